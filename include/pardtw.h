@@ -1,0 +1,158 @@
+/*
+ * pardtw.h — C-ABI of the GB300-native exact DTW (ParDTW) library.
+ *
+ * The library aligns two feature sequences A (La x D) and B (Lb x D) with
+ * exact dynamic time warping:
+ *
+ *   C[i][j] = 1 - cos(a_i, b_j)                       cosine cost (Sec. IV)
+ *   D[0][0] = C[0][0]
+ *   D[i][j] = min( D[i-1][j-1] + 2 C[i][j],           step (1,1)
+ *                  D[i-1][j-2] + 3 C[i][j],           step (1,2)
+ *                  D[i-2][j-1] + 3 C[i][j] )          step (2,1)
+ *
+ * with the step set and multiplicative weights of the DTW baseline of
+ * Sec. V ((di, dj) = (advance in A, advance in B)); ParDTW computes exactly
+ * this alignment with the cost formed on the fly, the cumulative cost kept
+ * only in a few live buffers, and a 2-bit backtrace matrix (Sec. II-D,
+ * Sec. III-B, Sec. VI-D).  Ties between candidates are broken in the order
+ * (1,1), (1,2), (2,1): a later candidate wins only when strictly smaller.
+ * A zero frame has cosine cost 1 against every frame.
+ *
+ * Arithmetic: FP32 cost and FP32 cumulative cost on the GPU; no FP64 and no
+ * CPU fallback.  Every call runs on the CUDA stream bound to the handle.
+ *
+ * Pointers.  Feature, path and result pointers may point to device memory
+ * or to host memory; the library detects which (cudaPointerGetAttributes).
+ * Host inputs are copied into the handle's workspace and host outputs are
+ * copied back; a call with any host output synchronises the stream before
+ * it returns.  With device-only arguments a call is asynchronous: it
+ * returns DTW_OK once the work is enqueued, and device-side failures are
+ * reported through the outputs (path_len < 0, see dtw_align).
+ *
+ * Layouts.  Features are row-major float32, frame k at X + k*D.  A path is
+ * an array of int32 (i, j) pairs, ascending from (0, 0) to (La-1, Lb-1):
+ * path[2k] = i_k, path[2k+1] = j_k.
+ *
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef PARDTW_H
+#define PARDTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define DTW_OK 0
+#define DTW_ERR_INVALID 1      /* null pointer, length < 1, D < 1, cap too small */
+#define DTW_ERR_UNREACHABLE 2  /* (La-1, Lb-1) cannot be reached: Lb-1 > 2(La-1) or La-1 > 2(Lb-1) */
+#define DTW_ERR_OOM 3          /* device allocation of the workspace failed */
+#define DTW_ERR_CUDA 4         /* a CUDA runtime call failed */
+#define DTW_ERR_TIMEOUT 5      /* a bounded device-side wait expired (the result is void) */
+#define DTW_ERR_UNSUPPORTED 6  /* option or size outside what this build supports */
+
+/* ---- options -------------------------------------------------------------- */
+#define DTW_COST_FP32 0        /* cost from FP32 features with FP32 accumulation */
+
+typedef struct dtw_options {
+    int cost_precision;    /* DTW_COST_FP32 */
+    /* The DP runs on C - cost_shift and adds cost_shift * (La + Lb - 2) to the
+     * total at the end.  Every path weighs exactly (La-1) + (Lb-1) (Sec. V),
+     * so the optimal path is unchanged in exact arithmetic; a shift near the
+     * per-step cost along the path keeps FP32 partial sums small and cuts
+     * their rounding.  0 = no shift. */
+    float cost_shift;
+    /* Upper bound on polling iterations of a device-side wait for a
+     * neighbouring tile's border (each iteration backs off ~0.1-1 us);
+     * 0 = library default (about 2 s).  On expiry the call fails with
+     * DTW_ERR_TIMEOUT. */
+    int wait_limit;
+    /* Fault injection for tests, -1 = off: the strip group with this index
+     * never publishes its bottom border, so the group below it waits until
+     * wait_limit and the call reports DTW_ERR_TIMEOUT. */
+    int debug_skip_publish;
+} dtw_options;
+
+/* Fill *opt with the defaults: FP32 cost, no shift, default wait limit,
+ * no fault injection. */
+void dtw_default_options(dtw_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* dtw_status_string(int status);
+
+/* ---- handle --------------------------------------------------------------- */
+typedef struct dtw_handle dtw_handle;
+
+/* Create a handle on CUDA device `device`, bound to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The handle owns a
+ * device workspace that grows on demand and is freed by dtw_destroy.
+ * Errors: DTW_ERR_INVALID (h == NULL, bad device), DTW_ERR_CUDA. */
+int dtw_create(dtw_handle** h, int device, void* cuda_stream);
+
+/* Synchronise the handle's stream, free its workspace and the handle. */
+int dtw_destroy(dtw_handle* h);
+
+/* Rebind the handle to another stream (later calls are ordered on it). */
+int dtw_set_stream(dtw_handle* h, void* cuda_stream);
+
+/* Bytes of device workspace dtw_align needs for (La, Lb, D) (Sec. VI-D's
+ * memory model: the 2-bit backtrace matrix dominates, La*Lb/4 bytes plus
+ * padding to 32 rows x 16 columns, plus O((La+Lb)*D) for normalised
+ * features and border buffers).  Errors: DTW_ERR_INVALID. */
+int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes);
+
+/* ---- cost matrix (Sec. IV cosine distance; Sec. VI-B explicit matrix) ---- */
+/* Write the La x Lb row-major FP32 cost matrix C[i*Lb + j] = 1 - cos(a_i, b_j).
+ * A, B: La x D and Lb x D float32 (device or host).  C: La*Lb float32,
+ * caller-owned (device or host).  The exact aligner never materialises
+ * this matrix (Sec. II-D); this entry point exists for inspection and tests.
+ * Errors: DTW_ERR_INVALID, DTW_ERR_OOM, DTW_ERR_CUDA. */
+int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, float* C);
+
+/* ---- exact alignment of one pair (Sec. II-D ParDTW, Sec. III-B) ----------- */
+/* Align A (La x D) with B (Lb x D).
+ *   opt         options, or NULL for the defaults
+ *   path        caller-owned int32 buffer of 2*cap entries (device or host)
+ *   cap         capacity in (i, j) pairs; must be >= min(La, Lb)
+ *   path_len    receives the number of pairs written (device or host int)
+ *   total_cost  receives D[La-1][Lb-1] in FP32 (device or host float); may be NULL
+ * Returns DTW_OK, DTW_ERR_INVALID, DTW_ERR_UNREACHABLE (checked on the host
+ * before any launch), DTW_ERR_OOM, DTW_ERR_CUDA, or, when the call
+ * synchronises (any host output), DTW_ERR_TIMEOUT.  When the call runs
+ * asynchronously, a device-side failure sets *path_len to -status
+ * (e.g. -DTW_ERR_TIMEOUT) and leaves path undefined. */
+int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+              const dtw_options* opt, int32_t* path, int cap, int* path_len,
+              float* total_cost);
+
+/* ---- batch of independent pairs ------------------------------------------- */
+/* Align n independent pairs (A[k], B[k]) of a common dimension D.
+ *   A, B, La, Lb, path_off : HOST arrays of n entries; A[k], B[k] point to
+ *                            device or host features
+ *   paths      one int32 buffer (device or host); pair k writes its path at
+ *              paths + 2*path_off[k], with room for min(La[k], Lb[k]) pairs
+ *   path_len, cost, status : arrays of n entries (device or host)
+ * A pair that fails (unreachable, timeout) gets its own status and
+ * path_len = -status; the other pairs are still aligned.  Returns the first
+ * argument or runtime error that prevented the batch from running. */
+int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
+                   const float* const* B, const int* Lb, int D, const dtw_options* opt,
+                   int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
+                   int* status);
+
+/* ---- profiling ------------------------------------------------------------ */
+/* Device time in ms of the stages of the last dtw_align on this handle,
+ * measured with CUDA events on the handle's stream: ms[0] normalise,
+ * ms[1] DP, ms[2] backtrace.  n = entries available in ms (<= 3).
+ * Synchronises on the last call's events.  Returns DTW_ERR_INVALID if no
+ * call has been timed (timing is enabled by dtw_enable_timing). */
+int dtw_enable_timing(dtw_handle* h, int on);
+int dtw_stage_times(dtw_handle* h, float* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARDTW_H */

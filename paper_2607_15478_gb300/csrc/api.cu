@@ -1,0 +1,482 @@
+// C-ABI of libpardtw (declarations and contracts in include/pardtw.h).
+//
+// Host-side work only: argument checks, the reachability test, workspace
+// management, pointer-kind detection, and the launch sequence
+//   normalise -> column-sweep DP (cost on the fly) -> backtrace
+// on the handle's stream.  Every step of the alignment runs in the kernels;
+// there is no CPU fallback.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "pardtw_common.cuh"
+
+using namespace pardtw;
+
+struct dtw_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    char* ws = nullptr;          // main workspace
+    size_t ws_cap = 0;
+    unsigned long long* border = nullptr;  // tagged border entries (own allocation, zeroed)
+    size_t border_cap = 0;                 // bytes
+    unsigned epoch = 0;
+    bool timing = false;
+    bool timed = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int* h_small = nullptr;      // pinned host: [0] path_len, [1] total bits
+};
+
+namespace {
+
+constexpr long long kDefaultTimeoutNs = 2000000000LL;  // 2 s
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CU(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) {                  \
+            (void)cudaGetLastError();             \
+            return DTW_ERR_CUDA;                  \
+        }                                         \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool reachable(int La, int Lb) {
+    long long i = La - 1, j = Lb - 1;
+    return La >= 1 && Lb >= 1 && j <= 2 * i && i <= 2 * j;
+}
+
+struct Layout {
+    int dp, nstrips, nchunk, ngroups, La_pad, cap;
+    size_t off_ctl, off_ahat, off_bhat, off_bp, off_scratch, off_stage_a, off_stage_b,
+        off_stage_path, total;
+    size_t border_bytes;
+};
+
+Layout make_layout(int La, int Lb, int D) {
+    Layout L;
+    L.dp = padded_dim(D);
+    L.nstrips = (La + kRowsPerStrip - 1) / kRowsPerStrip;
+    L.nchunk = (Lb + kColsPerWord - 1) / kColsPerWord;
+    L.ngroups = (L.nstrips + kWarpsPerGroup - 1) / kWarpsPerGroup;
+    L.La_pad = L.nstrips * kRowsPerStrip;
+    L.cap = std::min(La, Lb);
+    size_t o = 0;
+    L.off_ctl = o;  // DevCtl, e_final, total, path_len
+    o += 256;
+    L.off_ahat = o;
+    o = align256(o + (size_t)L.La_pad * L.dp * sizeof(float));
+    L.off_bhat = o;
+    o = align256(o + (size_t)Lb * L.dp * sizeof(float));
+    L.off_bp = o;
+    o = align256(o + (size_t)L.nstrips * L.nchunk * 32 * sizeof(uint32_t));
+    L.off_scratch = o;
+    o = align256(o + (size_t)2 * L.cap * sizeof(int32_t));
+    L.off_stage_a = o;
+    o = align256(o + (size_t)La * D * sizeof(float));
+    L.off_stage_b = o;
+    o = align256(o + (size_t)Lb * D * sizeof(float));
+    L.off_stage_path = o;
+    o = align256(o + (size_t)2 * L.cap * sizeof(int32_t));
+    L.total = o;
+    L.border_bytes = (size_t)L.ngroups * Lb * 2 * sizeof(unsigned long long);
+    return L;
+}
+
+int ensure_workspace(dtw_handle* h, size_t bytes, size_t border_bytes) {
+    if (bytes > h->ws_cap) {
+        CU(cudaStreamSynchronize(h->stream));
+        if (h->ws) cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_cap = 0;
+        size_t want = bytes + bytes / 8;
+        if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                h->ws = nullptr;
+                return DTW_ERR_OOM;
+            }
+            want = bytes;
+        }
+        h->ws_cap = want;
+    }
+    if (border_bytes > h->border_cap) {
+        CU(cudaStreamSynchronize(h->stream));
+        if (h->border) cudaFree(h->border);
+        h->border = nullptr;
+        h->border_cap = 0;
+        size_t want = border_bytes + border_bytes / 8;
+        if (cudaMalloc(&h->border, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->border = nullptr;
+            return DTW_ERR_OOM;
+        }
+        // Entries are tagged with the call's epoch, which only grows; zeroed
+        // memory can never carry the tag of a live call.
+        CU(cudaMemsetAsync(h->border, 0, want, h->stream));
+        h->border_cap = want;
+    }
+    return DTW_OK;
+}
+
+dtw_options defaults() {
+    dtw_options o;
+    o.cost_precision = DTW_COST_FP32;
+    o.cost_shift = 0.0f;
+    o.wait_limit = 0;
+    o.debug_skip_publish = -1;
+    return o;
+}
+
+// One pair, all the way to device-resident outputs.  `out_path`,
+// `out_len`, `out_total` are device pointers (out_total may be null).
+int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                 const dtw_options& o, int32_t* out_path, int* out_len, float* out_total) {
+    const Layout L = make_layout(La, Lb, D);
+    int rc = ensure_workspace(h, L.total, L.border_bytes);
+    if (rc != DTW_OK) return rc;
+    cudaStream_t s = h->stream;
+    char* ws = h->ws;
+    DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + L.off_ctl);
+    float* e_final = reinterpret_cast<float*>(ws + L.off_ctl + 16);
+    float* Ahat = reinterpret_cast<float*>(ws + L.off_ahat);
+    float* Bhat = reinterpret_cast<float*>(ws + L.off_bhat);
+    uint32_t* bp = reinterpret_cast<uint32_t*>(ws + L.off_bp);
+    int32_t* scratch = reinterpret_cast<int32_t*>(ws + L.off_scratch);
+
+    const float* dA = A;
+    const float* dB = B;
+    if (!is_device_ptr(A)) {
+        float* st = reinterpret_cast<float*>(ws + L.off_stage_a);
+        CU(cudaMemcpyAsync(st, A, (size_t)La * D * sizeof(float), cudaMemcpyHostToDevice, s));
+        dA = st;
+    }
+    if (!is_device_ptr(B)) {
+        float* st = reinterpret_cast<float*>(ws + L.off_stage_b);
+        CU(cudaMemcpyAsync(st, B, (size_t)Lb * D * sizeof(float), cudaMemcpyHostToDevice, s));
+        dB = st;
+    }
+    if (h->timing) CU(cudaEventRecord(h->ev[0], s));
+    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, D, L.dp, Ahat, Bhat, ctl, s));
+    if (h->timing) CU(cudaEventRecord(h->ev[1], s));
+
+    DpArgs a;
+    a.Ahat = Ahat;
+    a.Bhat = Bhat;
+    a.bp = bp;
+    a.gborder = h->border;
+    a.ctl = ctl;
+    a.e_final = e_final;
+    a.La = La;
+    a.Lb = Lb;
+    a.nstrips = L.nstrips;
+    a.nchunk = L.nchunk;
+    a.ngroups = L.ngroups;
+    a.mu = o.cost_shift;
+    a.kcost = 1.0f - o.cost_shift;
+    a.epoch = ++h->epoch;
+    if (a.epoch == 0) a.epoch = ++h->epoch;
+    a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
+    a.skip_publish = o.debug_skip_publish;
+    CU(launch_dp(a, L.dp, h->num_sms, s));
+    if (h->timing) CU(cudaEventRecord(h->ev[2], s));
+    CU(launch_backtrace(bp, La, Lb, L.nchunk, ctl, e_final, o.cost_shift, out_path, scratch,
+                        out_len, out_total, s));
+    if (h->timing) {
+        CU(cudaEventRecord(h->ev[3], s));
+        h->timed = true;
+    }
+    return DTW_OK;
+}
+
+int validate(const float* A, int La, const float* B, int Lb, int D) {
+    if (!A || !B || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
+    if (!reachable(La, Lb)) return DTW_ERR_UNREACHABLE;
+    if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
+    return DTW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dtw_default_options(dtw_options* opt) {
+    if (opt) *opt = defaults();
+}
+
+const char* dtw_status_string(int status) {
+    switch (status) {
+        case DTW_OK: return "ok";
+        case DTW_ERR_INVALID: return "invalid argument";
+        case DTW_ERR_UNREACHABLE: return "end cell unreachable with steps (1,1),(1,2),(2,1)";
+        case DTW_ERR_OOM: return "device workspace allocation failed";
+        case DTW_ERR_CUDA: return "CUDA runtime error";
+        case DTW_ERR_TIMEOUT: return "bounded device wait expired";
+        case DTW_ERR_UNSUPPORTED: return "unsupported option or size";
+        default: return "unknown status";
+    }
+}
+
+int dtw_create(dtw_handle** out, int device, void* cuda_stream) {
+    if (!out) return DTW_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DTW_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return DTW_ERR_INVALID;
+    DeviceGuard g(device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    dtw_handle* h = new (std::nothrow) dtw_handle();
+    if (!h) return DTW_ERR_OOM;
+    h->device = device;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess ||
+        cudaMallocHost(&h->h_small, 64) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete h;
+        return DTW_ERR_CUDA;
+    }
+    for (auto& e : h->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            (void)cudaGetLastError();
+            dtw_destroy(h);
+            return DTW_ERR_CUDA;
+        }
+    *out = h;
+    return DTW_OK;
+}
+
+int dtw_destroy(dtw_handle* h) {
+    if (!h) return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->border) cudaFree(h->border);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->h_small) cudaFreeHost(h->h_small);
+    (void)cudaGetLastError();
+    delete h;
+    return DTW_OK;
+}
+
+int dtw_set_stream(dtw_handle* h, void* cuda_stream) {
+    if (!h) return DTW_ERR_INVALID;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return DTW_OK;
+}
+
+int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes) {
+    (void)opt;
+    if (!bytes || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
+    if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
+    const Layout L = make_layout(La, Lb, D);
+    *bytes = L.total + L.border_bytes;
+    return DTW_OK;
+}
+
+int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, float* C) {
+    if (!h || !A || !B || !C || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
+    const int dp = padded_dim(D);
+    if (dp == 0) return DTW_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    const Layout L = make_layout(La, Lb, D);
+    const bool c_dev = is_device_ptr(C);
+    const size_t cbytes = (size_t)La * Lb * sizeof(float);
+    const size_t need = L.total + (c_dev ? 0 : align256(cbytes));
+    int rc = ensure_workspace(h, need, 0);
+    if (rc != DTW_OK) return rc;
+    cudaStream_t s = h->stream;
+    char* ws = h->ws;
+    const float* dA = A;
+    const float* dB = B;
+    if (!is_device_ptr(A)) {
+        float* st = reinterpret_cast<float*>(ws + L.off_stage_a);
+        CU(cudaMemcpyAsync(st, A, (size_t)La * D * sizeof(float), cudaMemcpyHostToDevice, s));
+        dA = st;
+    }
+    if (!is_device_ptr(B)) {
+        float* st = reinterpret_cast<float*>(ws + L.off_stage_b);
+        CU(cudaMemcpyAsync(st, B, (size_t)Lb * D * sizeof(float), cudaMemcpyHostToDevice, s));
+        dB = st;
+    }
+    DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + L.off_ctl);
+    float* Ahat = reinterpret_cast<float*>(ws + L.off_ahat);
+    float* Bhat = reinterpret_cast<float*>(ws + L.off_bhat);
+    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, D, dp, Ahat, Bhat, ctl, s));
+    float* dC = c_dev ? C : reinterpret_cast<float*>(ws + L.total);
+    CU(launch_cost(Ahat, La, Bhat, Lb, dp, dC, s));
+    if (!c_dev) {
+        CU(cudaMemcpyAsync(C, dC, cbytes, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return DTW_OK;
+}
+
+int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+              const dtw_options* opt, int32_t* path, int cap, int* path_len,
+              float* total_cost) {
+    if (!h || !path || !path_len) return DTW_ERR_INVALID;
+    int rc = validate(A, La, B, Lb, D);
+    if (rc != DTW_OK) return rc;
+    if (cap < std::min(La, Lb)) return DTW_ERR_INVALID;
+    const dtw_options o = opt ? *opt : defaults();
+    if (o.cost_precision != DTW_COST_FP32) return DTW_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+
+    const Layout L = make_layout(La, Lb, D);
+    rc = ensure_workspace(h, L.total, L.border_bytes);
+    if (rc != DTW_OK) return rc;
+    const bool path_dev = is_device_ptr(path);
+    const bool len_dev = is_device_ptr(path_len);
+    const bool tot_dev = total_cost ? is_device_ptr(total_cost) : true;
+    char* ws = h->ws;
+    int32_t* dpath = path_dev ? path : reinterpret_cast<int32_t*>(ws + L.off_stage_path);
+    int* dlen = len_dev ? path_len : reinterpret_cast<int*>(ws + L.off_ctl + 24);
+    float* dtot = total_cost ? (tot_dev ? total_cost : reinterpret_cast<float*>(ws + L.off_ctl + 20))
+                             : nullptr;
+    rc = align_device(h, A, La, B, Lb, D, o, dpath, dlen, dtot);
+    if (rc != DTW_OK) return rc;
+    cudaStream_t s = h->stream;
+    const bool host_out = !path_dev || !len_dev || !tot_dev;
+    if (!host_out) return DTW_OK;
+
+    // host outputs: bring back length and total, then the path
+    CU(cudaMemcpyAsync(h->h_small, ws + L.off_ctl + 20, 8, cudaMemcpyDeviceToHost, s));
+    if (len_dev) CU(cudaMemcpyAsync(h->h_small + 1, path_len, 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int n = h->h_small[1];
+    if (!len_dev) *path_len = n;
+    if (total_cost && !tot_dev) memcpy(total_cost, &h->h_small[0], sizeof(float));
+    if (n < 0) return -n;
+    if (!path_dev) {
+        CU(cudaMemcpyAsync(path, dpath, (size_t)2 * n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return DTW_OK;
+}
+
+int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
+                   const float* const* B, const int* Lb, int D, const dtw_options* opt,
+                   int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
+                   int* status) {
+    if (!h || n < 0 || (n > 0 && (!A || !La || !B || !Lb || !paths || !path_off || !path_len ||
+                                  !status)))
+        return DTW_ERR_INVALID;
+    if (n == 0) return DTW_OK;
+    const dtw_options o = opt ? *opt : defaults();
+    if (o.cost_precision != DTW_COST_FP32) return DTW_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    const bool paths_dev = is_device_ptr(paths);
+    const bool len_dev = is_device_ptr(path_len);
+    const bool cost_dev = cost ? is_device_ptr(cost) : true;
+    const bool st_dev = is_device_ptr(status);
+    std::vector<int> hst(n, DTW_OK);
+    std::vector<int> hlen(n, 0);
+    std::vector<float> hcost(n, NAN);
+    for (int k = 0; k < n; ++k) {
+        int rc = validate(A[k], La[k], B[k], Lb[k], D);
+        if (rc != DTW_OK) {
+            hst[k] = rc;
+            hlen[k] = -rc;
+            continue;
+        }
+        int32_t* pk = paths + 2 * path_off[k];
+        if (paths_dev && len_dev && cost_dev) {
+            rc = align_device(h, A[k], La[k], B[k], Lb[k], D, o, pk, path_len + k,
+                              cost ? cost + k : nullptr);
+        } else {
+            rc = dtw_align(h, A[k], La[k], B[k], Lb[k], D, &o, pk, std::min(La[k], Lb[k]),
+                           len_dev ? path_len + k : &hlen[k],
+                           cost ? (cost_dev ? cost + k : &hcost[k]) : nullptr);
+            if (rc == DTW_ERR_TIMEOUT) {
+                hst[k] = rc;
+                hlen[k] = -rc;
+                continue;
+            }
+        }
+        if (rc != DTW_OK) return rc;
+    }
+    cudaStream_t s = h->stream;
+    // host-side failures into device outputs
+    for (int k = 0; k < n; ++k) {
+        if (hst[k] == DTW_OK) continue;
+        if (len_dev) CU(cudaMemcpyAsync(path_len + k, &hlen[k], 4, cudaMemcpyHostToDevice, s));
+        if (cost && cost_dev) CU(cudaMemcpyAsync(cost + k, &hcost[k], 4, cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaStreamSynchronize(s));
+    if (!len_dev)
+        for (int k = 0; k < n; ++k)
+            if (hst[k] != DTW_OK) path_len[k] = hlen[k];
+    if (cost && !cost_dev)
+        for (int k = 0; k < n; ++k)
+            if (hst[k] != DTW_OK) cost[k] = hcost[k];
+    // statuses: host-side ones, or the sign of the device-side lengths
+    std::vector<int> lens(n);
+    if (len_dev)
+        CU(cudaMemcpy(lens.data(), path_len, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    else
+        memcpy(lens.data(), path_len, sizeof(int) * n);
+    for (int k = 0; k < n; ++k)
+        if (hst[k] == DTW_OK && lens[k] < 0) hst[k] = -lens[k];
+    if (st_dev)
+        CU(cudaMemcpy(status, hst.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    else
+        memcpy(status, hst.data(), sizeof(int) * n);
+    return DTW_OK;
+}
+
+int dtw_enable_timing(dtw_handle* h, int on) {
+    if (!h) return DTW_ERR_INVALID;
+    h->timing = on != 0;
+    h->timed = false;
+    return DTW_OK;
+}
+
+int dtw_stage_times(dtw_handle* h, float* ms, int n) {
+    if (!h || !ms || n < 1 || !h->timed) return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    CU(cudaEventSynchronize(h->ev[3]));
+    float t[3];
+    for (int k = 0; k < 3; ++k) CU(cudaEventElapsedTime(&t[k], h->ev[k], h->ev[k + 1]));
+    for (int k = 0; k < n && k < 3; ++k) ms[k] = t[k];
+    return DTW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Per-frame L2 normalisation and the explicit cosine cost matrix.
+//
+// The cosine cost of Sec. IV is C[i][j] = 1 - (a_i . b_j) / (|a_i| |b_j|).
+// The kernels normalise every frame once (a zero frame stays zero, so its
+// cost against anything is 1) and then form 1 - a^_i . b^_j with one FP32
+// fused multiply-add per feature, in feature order.  The DP kernel computes
+// the cost of each cell the same way on the fly (Sec. II-D: the cost
+// matrix is never stored); dtw_cost materialises it for inspection.
+#include "pardtw_common.cuh"
+
+namespace pardtw {
+
+int padded_dim(int D) {
+    static const int sizes[] = {4, 8, 12, 16, 32, 64, 128};
+    for (int s : sizes)
+        if (D <= s) return s;
+    return 0;
+}
+
+// One thread per frame.  Frames of A beyond La (padding up to a multiple of
+// 32 rows) and feature slots beyond D are written as zeros.  Thread 0 also
+// clears the control words of the call.
+__global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
+                            const float* __restrict__ B, int Lb, int D, int dp,
+                            float* __restrict__ Ahat, float* __restrict__ Bhat, DevCtl* ctl) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        ctl->status = 0;
+        ctl->detail = 0;
+        ctl->ticket = 0;
+    }
+    const float* src;
+    float* dst;
+    bool valid;
+    if (t < La_pad) {
+        src = A + (size_t)t * D;
+        dst = Ahat + (size_t)t * dp;
+        valid = t < La;
+    } else if (t < La_pad + Lb) {
+        const int k = t - La_pad;
+        src = B + (size_t)k * D;
+        dst = Bhat + (size_t)k * dp;
+        valid = true;
+    } else {
+        return;
+    }
+    float ss = 0.f;
+    if (valid)
+        for (int d = 0; d < D; ++d) {
+            const float v = src[d];
+            ss = fmaf(v, v, ss);
+        }
+    const float r = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+    for (int d = 0; d < dp; ++d) dst[d] = (valid && d < D) ? src[d] * r : 0.f;
+}
+
+cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb, int D,
+                             int dp, float* Ahat, float* Bhat, DevCtl* ctl, cudaStream_t s) {
+    const int n = La_pad + Lb;
+    const int threads = 256;
+    k_normalise<<<(n + threads - 1) / threads, threads, 0, s>>>(A, La, La_pad, B, Lb, D, dp,
+                                                                Ahat, Bhat, ctl);
+    return cudaGetLastError();
+}
+
+// C[i][j] = 1 - sum_d a^_i[d] b^_j[d], accumulated as fma(-a, b, acc) from 1
+// in feature order -- bit-identical to the cost the DP kernel uses.
+// Block: 256 threads = 8 rows x 32 column lanes; each lane writes 4 columns
+// of its row per pass.
+__global__ void k_cost(const float* __restrict__ Ahat, int La, const float* __restrict__ Bhat,
+                       int Lb, int dp, float* __restrict__ C) {
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.y * 8 + (threadIdx.x >> 5); i < La; i += gridDim.y * 8) {
+        const float* a = Ahat + (size_t)i * dp;
+        for (int j0 = blockIdx.x * 128 + lane; j0 < Lb; j0 += gridDim.x * 128) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + 32 * q;
+                if (j >= Lb) break;
+                const float* b = Bhat + (size_t)j * dp;
+                float acc = 1.0f;
+                for (int d = 0; d < dp; ++d) acc = fmaf(-a[d], b[d], acc);
+                C[(size_t)i * Lb + j] = acc;
+            }
+        }
+    }
+}
+
+cudaError_t launch_cost(const float* Ahat, int La, const float* Bhat, int Lb, int dp, float* C,
+                        cudaStream_t s) {
+    const int gx = (Lb + 127) / 128 < 64 ? (Lb + 127) / 128 : 64;
+    const int gy = (La + 7) / 8 < 32768 ? (La + 7) / 8 : 32768;
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    k_cost<<<grid, 256, 0, s>>>(Ahat, La, Bhat, Lb, dp, C);
+    return cudaGetLastError();
+}
+
+}  // namespace pardtw

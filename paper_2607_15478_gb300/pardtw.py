@@ -1,0 +1,262 @@
+"""Python binding of libpardtw (C-ABI in include/pardtw.h).
+
+Argument marshalling only: every step of the alignment (normalisation, cost,
+DP, backtrace) runs in the library's CUDA kernels.  PyTorch provides device
+memory and streams.  If the shared library is missing or cannot be loaded
+the calls raise -- there is no CPU fallback.
+
+Low-level names follow the C-ABI (``dtw_cost``, ``dtw_align``,
+``dtw_align_many``); ``Aligner`` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libpardtw.so")
+
+DTW_OK = 0
+DTW_ERR_INVALID = 1
+DTW_ERR_UNREACHABLE = 2
+DTW_ERR_OOM = 3
+DTW_ERR_CUDA = 4
+DTW_ERR_TIMEOUT = 5
+DTW_ERR_UNSUPPORTED = 6
+DTW_COST_FP32 = 0
+
+# every entry point include/pardtw.h declares
+EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destroy",
+           "dtw_set_stream", "dtw_workspace_size", "dtw_cost", "dtw_align", "dtw_align_many",
+           "dtw_enable_timing", "dtw_stage_times")
+
+
+class PardtwError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})" if what else msg)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("cost_precision", ctypes.c_int), ("cost_shift", ctypes.c_float),
+                ("wait_limit", ctypes.c_int), ("debug_skip_publish", ctypes.c_int)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpardtw.so (built by ``paper_2607_15478_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libpardtw.so not built at {path}; run "
+                      "`python -m paper_2607_15478_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, ci, cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    ip = ctypes.POINTER(ci)
+    lib.dtw_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.dtw_default_options.restype = None
+    lib.dtw_status_string.argtypes = [ci]
+    lib.dtw_status_string.restype = ctypes.c_char_p
+    lib.dtw_create.argtypes = [ctypes.POINTER(vp), ci, vp]
+    lib.dtw_destroy.argtypes = [vp]
+    lib.dtw_set_stream.argtypes = [vp, vp]
+    lib.dtw_workspace_size.argtypes = [ci, ci, ci, ctypes.POINTER(Options),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+    lib.dtw_cost.argtypes = [vp, vp, ci, vp, ci, ci, vp]
+    lib.dtw_align.argtypes = [vp, vp, ci, vp, ci, ci, ctypes.POINTER(Options), vp, ci, vp, vp]
+    lib.dtw_align_many.argtypes = [vp, ci, vp, vp, vp, vp, ci, ctypes.POINTER(Options), vp, vp,
+                                   vp, vp, vp]
+    lib.dtw_enable_timing.argtypes = [vp, ci]
+    lib.dtw_stage_times.argtypes = [vp, ctypes.POINTER(cf), ci]
+    for name in EXPORTS:
+        if name not in ("dtw_default_options", "dtw_status_string"):
+            getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().dtw_status_string(int(status)).decode()
+
+
+def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
+                 debug_skip_publish: int = -1) -> Options:
+    o = Options()
+    load_library().dtw_default_options(ctypes.byref(o))
+    o.cost_shift = float(cost_shift)
+    o.wait_limit = int(wait_limit_us)
+    o.debug_skip_publish = int(debug_skip_publish)
+    return o
+
+
+def workspace_size(La: int, Lb: int, D: int) -> int:
+    n = ctypes.c_size_t(0)
+    rc = load_library().dtw_workspace_size(La, Lb, D, None, ctypes.byref(n))
+    if rc != DTW_OK:
+        raise PardtwError(rc, "dtw_workspace_size")
+    return n.value
+
+
+def _check(rc: int, what: str):
+    if rc != DTW_OK:
+        raise PardtwError(rc, what)
+
+
+def _features(X):
+    import torch
+    if not isinstance(X, torch.Tensor):
+        X = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32))
+    if X.dtype != torch.float32 or X.dim() != 2:
+        raise ValueError("features must be a 2-D float32 tensor (L x D)")
+    return X.contiguous()
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C-ABI mirrors ------------------------------------------------------------------
+
+def dtw_create(device: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().dtw_create(ctypes.byref(h), int(device), _stream_ptr(stream)),
+           "dtw_create")
+    return h.value
+
+
+def dtw_destroy(h: int) -> None:
+    _check(load_library().dtw_destroy(h), "dtw_destroy")
+
+
+def dtw_cost(h: int, A, B, C) -> None:
+    """C[i, j] = 1 - cos(a_i, b_j) into the La x Lb float32 tensor C."""
+    A, B = _features(A), _features(B)
+    _check(load_library().dtw_cost(h, A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0],
+                                   A.shape[1], C.data_ptr()), "dtw_cost")
+
+
+def dtw_align(h: int, A, B, path, path_len, total=None, options: Options | None = None) -> None:
+    """Exact DTW of A and B into caller buffers (path: cap x 2 int32; path_len: int32[1];
+    total: float32[1] or None).  Asynchronous when every buffer is on the device."""
+    A, B = _features(A), _features(B)
+    cap = path.shape[0]
+    _check(load_library().dtw_align(h, A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0],
+                                    A.shape[1], ctypes.byref(options) if options else None,
+                                    path.data_ptr(), cap, path_len.data_ptr(),
+                                    total.data_ptr() if total is not None else None),
+           "dtw_align")
+
+
+def dtw_align_many(h: int, As: Sequence, Bs: Sequence, paths, path_off, path_len, cost, status,
+                   options: Options | None = None) -> None:
+    """Batched exact DTW; per-pair outputs as in include/pardtw.h."""
+    n = len(As)
+    As = [_features(a) for a in As]
+    Bs = [_features(b) for b in Bs]
+    D = As[0].shape[1] if n else 1
+    Ap = (ctypes.c_void_p * n)(*[a.data_ptr() for a in As])
+    Bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in Bs])
+    La = (ctypes.c_int * n)(*[a.shape[0] for a in As])
+    Lb = (ctypes.c_int * n)(*[b.shape[0] for b in Bs])
+    off = (ctypes.c_int64 * n)(*[int(x) for x in path_off])
+    _check(load_library().dtw_align_many(
+        h, n, ctypes.cast(Ap, ctypes.c_void_p), ctypes.cast(La, ctypes.c_void_p),
+        ctypes.cast(Bp, ctypes.c_void_p), ctypes.cast(Lb, ctypes.c_void_p), D,
+        ctypes.byref(options) if options else None, paths.data_ptr(),
+        ctypes.cast(off, ctypes.c_void_p), path_len.data_ptr(),
+        cost.data_ptr() if cost is not None else None, status.data_ptr()), "dtw_align_many")
+
+
+# ---- convenience wrapper --------------------------------------------------------------
+
+class Aligner:
+    """A library handle bound to a device and a stream, with tensor-level calls."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = torch.device("cuda", device)
+        self._stream = stream
+        self.h = dtw_create(device, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dtw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def enable_timing(self, on: bool = True):
+        _check(load_library().dtw_enable_timing(self.h, int(on)), "dtw_enable_timing")
+
+    def stage_times(self) -> Tuple[float, float, float]:
+        ms = (ctypes.c_float * 3)()
+        _check(load_library().dtw_stage_times(self.h, ms, 3), "dtw_stage_times")
+        return tuple(ms)
+
+    def cost(self, A, B):
+        import torch
+        A, B = _features(A), _features(B)
+        C = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32,
+                        device=A.device if A.is_cuda else self.device)
+        dtw_cost(self.h, A, B, C)
+        return C
+
+    def align_into(self, A, B, path, path_len, total, **opts):
+        """Asynchronous form: all outputs are caller-owned device tensors."""
+        dtw_align(self.h, A, B, path, path_len, total, make_options(**opts) if opts else None)
+
+    def align(self, A, B, **opts):
+        """Return (path as an (n, 2) int32 tensor on the device, total cost as float)."""
+        import torch
+        A, B = _features(A), _features(B)
+        cap = min(A.shape[0], B.shape[0])
+        dev = A.device if A.is_cuda else self.device
+        path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+        plen = torch.zeros(1, dtype=torch.int32, device=dev)
+        tot = torch.zeros(1, dtype=torch.float32, device=dev)
+        dtw_align(self.h, A, B, path, plen, tot, make_options(**opts) if opts else None)
+        n = int(plen.item())
+        if n < 0:
+            raise PardtwError(-n, "dtw_align (device)")
+        return path[:n], float(tot.item())
+
+    def align_many(self, As: List, Bs: List, **opts):
+        """Align independent pairs; returns (list of paths or None, costs, statuses)."""
+        import torch
+        n = len(As)
+        caps = [min(a.shape[0], b.shape[0]) for a, b in zip(As, Bs)]
+        off = np.concatenate([[0], np.cumsum(caps)[:-1]]).astype(np.int64) if n else []
+        paths = torch.empty((int(sum(caps)), 2), dtype=torch.int32, device=self.device)
+        plen = torch.zeros(n, dtype=torch.int32, device=self.device)
+        cost = torch.zeros(n, dtype=torch.float32, device=self.device)
+        status = torch.zeros(n, dtype=torch.int32, device=self.device)
+        dtw_align_many(self.h, As, Bs, paths, off, plen, cost, status,
+                       make_options(**opts) if opts else None)
+        plen_h = plen.cpu().numpy()
+        st = status.cpu().numpy()
+        out = []
+        for k in range(n):
+            out.append(paths[off[k]:off[k] + plen_h[k]] if st[k] == 0 else None)
+        return out, cost.cpu().numpy(), st

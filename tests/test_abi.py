@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads without a GPU and exports what include/*.h declares."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2607_15478_gb300 import build as pbuild
+from paper_2607_15478_gb300 import pardtw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(?:int|void|const char\s*\*)\s+(dtw_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return pardtw.load_library()
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == set(pardtw.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert pardtw.status_string(s)
+    assert "unreachable" in pardtw.status_string(pardtw.DTW_ERR_UNREACHABLE)
+
+
+def test_default_options(lib):
+    o = pardtw.make_options()
+    assert o.cost_precision == pardtw.DTW_COST_FP32
+    assert o.cost_shift == 0.0 and o.debug_skip_publish == -1
+
+
+def test_workspace_size_follows_memory_model(lib):
+    # Sec. VI-D: the 2-bit backtrace matrix (L^2 / 4 bytes) plus O(L) buffers;
+    # here also the tagged border rows between strip groups (16 B per column
+    # per group of 128 rows, i.e. La*Lb/8 bytes)
+    for La, Lb in [(1000, 1200), (20000, 25000), (100000, 130000)]:
+        n = pardtw.workspace_size(La, Lb, 12)
+        bp = -(-La // 32) * 32 * -(-Lb // 16) * 16 / 4
+        border = -(-La // 128) * Lb * 16
+        assert bp + border <= n <= (bp + border) * 1.01 + 64 * (La + Lb) * 12
+    with pytest.raises(pardtw.PardtwError):
+        pardtw.workspace_size(0, 10, 12)
+
+
+def test_workspace_size_rejects_unsupported_dim(lib):
+    with pytest.raises(pardtw.PardtwError) as e:
+        pardtw.workspace_size(10, 10, 4096)
+    assert e.value.status == pardtw.DTW_ERR_UNSUPPORTED
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    h = ctypes.c_void_p()
+    rc = lib.dtw_create(ctypes.byref(h), 0, None)
+    assert rc in (pardtw.DTW_ERR_CUDA, pardtw.DTW_ERR_INVALID)
+    assert h.value is None

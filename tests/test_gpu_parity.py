@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Acceptance, per result:
+  * the GPU path is a valid DTW path (endpoints, step set, length bounds);
+  * it equals the oracle's path index for index, or -- where FP32 rounding
+    resolves a near-tie differently -- its FP64-recomputed cost equals the
+    oracle's optimum within 1e-6 relative;
+  * the GPU's FP32 total is within 1e-5 relative of the oracle's FP64 total,
+    with an absolute floor of 2e-6 * (La + Lb) for totals near zero (each
+    FP32 cell cost carries an absolute error of order D * 2^-24 <= 1e-6, and
+    a path weighs (La-1)+(Lb-1)).
+Where every cost is a small integer (one-hot features) the FP32 arithmetic
+is exact, and paths and totals must match exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_15478_gb300 import synth
+from tests._pins import check_path_valid, constant_cost_path
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aligner():
+    from paper_2607_15478_gb300 import build, pardtw
+    build.build()
+    a = pardtw.Aligner(0)
+    yield a
+    a.close()
+
+
+def cost_tol(total, La, Lb):
+    return max(1e-5 * abs(total), 2e-6 * (La + Lb))
+
+
+def assert_parity(A, B, path, total):
+    La, Lb = A.shape[0], B.shape[0]
+    p = path.cpu().numpy() if hasattr(path, "cpu") else np.asarray(path)
+    check_path_valid(p, La, Lb)
+    po, to = oracle.dtw(A, B)
+    assert abs(total - to) <= cost_tol(to, La, Lb), (total, to)
+    if not (p.shape == po.shape and np.array_equal(p, po)):
+        tg = oracle.path_cost(A, B, p)
+        assert abs(tg - to) <= 1e-6 * max(abs(to), 1e-300), (tg, to)
+    return po, to
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+SHAPES = [(1, 1), (2, 2), (2, 3), (3, 2), (5, 9), (31, 33), (32, 32), (33, 31), (33, 64),
+          (64, 33), (100, 150), (127, 129), (128, 128), (129, 130), (130, 257), (257, 300),
+          (300, 257), (500, 400), (513, 1000), (1000, 513), (700, 900)]
+
+
+@pytest.mark.parametrize("La,Lb", SHAPES)
+def test_parity_small_shapes(aligner, La, Lb):
+    wp = synth.warped_pair(synth.rng_for(50, La * 1000 + Lb), La, Lb, 12, knots=4,
+                           tmin=0.5, tmax=2.0)
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    assert_parity(wp.A, wp.B, path, total)
+
+
+@pytest.mark.parametrize("D", [1, 3, 4, 7, 12, 13, 16, 20, 32, 33, 64, 100, 128])
+def test_parity_feature_dims(aligner, D):
+    La, Lb = 200, 230
+    rng = synth.rng_for(51, D)
+    wp = synth.warped_pair(rng, La, Lb, D, kind="gaussian" if D > 12 else "chroma", knots=4)
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    assert_parity(wp.A, wp.B, path, total)
+
+
+@pytest.mark.parametrize("La,Lb,K", [(40, 50, 3), (129, 170, 4), (300, 260, 2), (700, 999, 5)])
+def test_exact_ties_onehot(aligner, La, Lb, K):
+    # one-hot frames: cosine cost is exactly 0 or 1, FP32 arithmetic is exact,
+    # many paths tie; the tie order must give the oracle's path exactly
+    rng = np.random.default_rng(La + Lb)
+    A = np.eye(K, dtype=np.float32)[rng.integers(0, K, La)]
+    B = np.eye(K, dtype=np.float32)[rng.integers(0, K, Lb)]
+    path, total = aligner.align(dev(A), dev(B))
+    po, to = oracle.dtw(A, B)
+    assert total == to
+    np.testing.assert_array_equal(path.cpu().numpy(), po)
+
+
+@pytest.mark.parametrize("La,Lb", [(1, 1), (3, 4), (40, 70), (70, 40), (300, 599), (599, 300),
+                                   (1000, 1000)])
+def test_all_paths_tie(aligner, La, Lb):
+    A = np.tile(np.array([[0.25, 0.5, 1.0, 0.0]], np.float32), (La, 1))
+    B = A[:1].repeat(Lb, axis=0)
+    path, total = aligner.align(dev(A), dev(B))
+    np.testing.assert_array_equal(path.cpu().numpy(), constant_cost_path(La, Lb))
+    assert abs(total) <= 2e-6 * (La + Lb)
+
+
+def test_identical_sequences_diagonal(aligner):
+    A = synth.chroma_frames(synth.rng_for(52, 0), 777).astype(np.float32)
+    path, total = aligner.align(dev(A), dev(A))
+    np.testing.assert_array_equal(path.cpu().numpy(), np.stack([np.arange(777)] * 2, 1))
+    assert abs(total) <= 2e-6 * 2 * 777
+
+
+def test_zero_frames(aligner):
+    wp = synth.warped_pair(synth.rng_for(53, 0), 90, 100, 12, knots=3)
+    A, B = wp.A.copy(), wp.B.copy()
+    A[::7] = 0.0
+    B[::5] = 0.0
+    path, total = aligner.align(dev(A), dev(B))
+    assert_parity(A, B, path, total)
+
+
+def test_parity_config0_full(aligner):
+    wp = synth.config_pair(0)
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    assert_parity(wp.A, wp.B, path, total)
+
+
+def test_parity_config1_full(aligner):
+    # the benchmark workload, in the launch configuration bench.py times
+    wp = synth.config_pair(1)
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    assert_parity(wp.A, wp.B, path, total)
+
+
+def test_cost_shift_keeps_path(aligner):
+    wp = synth.config_pair(1, La=3000, Lb=3700)
+    p0, t0 = aligner.align(dev(wp.A), dev(wp.B))
+    p1, t1 = aligner.align(dev(wp.A), dev(wp.B), cost_shift=0.05)
+    po, to = assert_parity(wp.A, wp.B, p1, t1)
+    assert abs(t1 - to) <= abs(t0 - to) + 1e-5 * to
+
+
+def test_deterministic(aligner):
+    wp = synth.config_pair(1, La=2000, Lb=2500)
+    A, B = dev(wp.A), dev(wp.B)
+    p0, t0 = aligner.align(A, B)
+    for _ in range(3):
+        p1, t1 = aligner.align(A, B)
+        assert t1 == t0
+        assert torch.equal(p0, p1)
+
+
+def test_host_buffers_roundtrip(aligner):
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.config_pair(0, La=400, Lb=480)
+    A = torch.from_numpy(wp.A).pin_memory()
+    B = torch.from_numpy(wp.B).pin_memory()
+    cap = 400
+    path = torch.zeros((cap, 2), dtype=torch.int32).pin_memory()
+    plen = torch.zeros(1, dtype=torch.int32)
+    tot = torch.zeros(1, dtype=torch.float32)
+    pardtw.dtw_align(aligner.h, A, B, path, plen, tot)
+    n = int(plen[0])
+    assert_parity(wp.A, wp.B, path[:n].numpy(), float(tot[0]))
+
+
+def test_cost_matrix(aligner):
+    wp = synth.warped_pair(synth.rng_for(54, 0), 150, 170, 12, knots=3)
+    C = aligner.cost(dev(wp.A), dev(wp.B)).cpu().numpy()
+    Co = oracle.cost_matrix(wp.A, wp.B)
+    assert np.max(np.abs(C - Co)) < 2e-6
+
+
+def test_unreachable_and_invalid(aligner):
+    from paper_2607_15478_gb300 import pardtw
+    A = dev(np.ones((3, 4), np.float32))
+    B = dev(np.ones((10, 4), np.float32))
+    with pytest.raises(pardtw.PardtwError) as e:
+        aligner.align(A, B)
+    assert e.value.status == pardtw.DTW_ERR_UNREACHABLE
+    path = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    plen = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(pardtw.PardtwError) as e:
+        pardtw.dtw_align(aligner.h, A, dev(np.ones((4, 4), np.float32)), path, plen)
+    assert e.value.status == pardtw.DTW_ERR_INVALID
+
+
+def test_timeout_is_reported_and_handle_survives(aligner):
+    # the first strip group never publishes its bottom border; the group below
+    # waits for ~20 ms, records DTW_ERR_TIMEOUT and every CTA leaves
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.config_pair(0, La=600, Lb=700)
+    with pytest.raises(pardtw.PardtwError) as e:
+        aligner.align(dev(wp.A), dev(wp.B), wait_limit_us=20000, debug_skip_publish=0)
+    assert e.value.status == pardtw.DTW_ERR_TIMEOUT
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    assert_parity(wp.A, wp.B, path, total)
+
+
+def test_align_many_matches_single(aligner):
+    pairs = synth.config_batch(2, n_pairs=6, La_range=(100, 900))
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    # one unreachable pair in the middle must not stop the others
+    As.insert(3, dev(np.ones((3, 12), np.float32)))
+    Bs.insert(3, dev(np.ones((20, 12), np.float32)))
+    paths, costs, st = aligner.align_many(As, Bs)
+    assert st[3] == 2 and paths[3] is None
+    k = 0
+    for idx in range(len(As)):
+        if idx == 3:
+            continue
+        p = pairs[k]
+        k += 1
+        assert st[idx] == 0
+        assert_parity(p.A, p.B, paths[idx], float(costs[idx]))
