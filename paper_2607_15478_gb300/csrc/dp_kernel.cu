@@ -60,13 +60,18 @@ __device__ __forceinline__ void sts2(unsigned long long* p, unsigned long long a
                      (unsigned)__cvta_generic_to_shared(p)),
                  "l"(a), "l"(b));
 }
+// Border entries in global memory are two 64-bit words, each (value, tag);
+// every word is read and written as one relaxed gpu-scope 64-bit access,
+// which is single-copy atomic, so a reader can trust a word whose tag matches.
 __device__ __forceinline__ void ldg2(const unsigned long long* p, unsigned long long& a,
                                      unsigned long long& b) {
-    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p));
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p + 1));
 }
 __device__ __forceinline__ void stg2(unsigned long long* p, unsigned long long a,
                                      unsigned long long b) {
-    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b));
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a));
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p + 1), "l"(b));
 }
 __device__ __forceinline__ long long global_ns() {
     long long t;
@@ -92,9 +97,11 @@ struct Entry {
     int ok;
 };
 
-// Slow path of a ring read: poll the slot until its tags match, the call
-// fails elsewhere, or the deadline passes.  Warp-uniform (all lanes read the
-// same shared address; the deadline is taken from lane 0).
+// Slow path of a ring read: poll the slot until its tags match in every
+// lane, the call fails elsewhere, or the deadline passes.  Every decision is
+// a warp vote or comes from lane 0: lanes of a warp are not guaranteed to
+// execute a load together, so two lanes may see different tags, and a
+// per-lane branch in front of the warp-wide shuffles would be unsafe.
 __device__ __noinline__ Entry wait_ring_slot(const unsigned long long* slot, unsigned tag,
                                              DevCtl* ctl, long long timeout_ns, int where) {
     Entry r;
@@ -102,7 +109,7 @@ __device__ __noinline__ Entry wait_ring_slot(const unsigned long long* slot, uns
     for (;;) {
         __nanosleep(40);
         lds2(slot, r.e0, r.e1);
-        if (tag_of(r.e0) == tag && tag_of(r.e1) == tag) {
+        if (__all_sync(kFull, tag_of(r.e0) == tag && tag_of(r.e1) == tag)) {
             r.ok = 1;
             return r;
         }
@@ -290,7 +297,8 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
                 const unsigned long long* slot = myring + ((j - 1) & kRingMask) * 2;
                 Entry e;
                 lds2(slot, e.e0, e.e1);
-                if (tag_of(e.e0) != (unsigned)j || tag_of(e.e1) != (unsigned)j) {
+                if (!__all_sync(kFull, tag_of(e.e0) == (unsigned)j &&
+                                           tag_of(e.e1) == (unsigned)j)) {
                     e = wait_ring_slot(slot, (unsigned)j, p.ctl, p.timeout_ns, 1);
                     if (!e.ok) return;
                 }
