@@ -14,16 +14,26 @@
 // every sweep step at full width (no fill and drain of diagonals) and makes
 // the column of B a warp-uniform broadcast.
 //
-//   - A warp owns a strip of 32 consecutive rows of A, one row per lane, and
-//     sweeps all Lb columns; each lane keeps its row's two live cumulative
-//     values in registers and the normalised frame a_i in registers.
-//   - Rows i-1 and i-2 of column j-1 come from the lanes above through warp
-//     shuffles; lanes 0 and 1 take the two bottom rows of the strip above
-//     from a tagged ring in shared memory (strip above in the same CTA) or
-//     from a tagged border buffer in global memory (strip above in another
-//     CTA).  Ring and border entries carry a tag in the same 64-bit word as
-//     the value, so a reader never needs a fence: a matching tag proves the
-//     value is the one it waits for.
+//   - A warp owns a strip of 30 consecutive rows of A, one row per lane
+//     0..29, and sweeps all Lb columns; each lane keeps its row's two live
+//     cumulative values and the normalised frame a_i in registers.
+//   - Lanes 30 and 31 are "ghost" rows: they reproduce the two bottom rows of
+//     the strip above.  A ghost lane runs the same step as a real one, but
+//     its cost is 1e30 and the weight of its (1,2) candidate is 0, so that
+//     candidate -- fed with the border value -- is always the minimum.  Rows
+//     i-1 and i-2 of column j-1 then arrive for every lane by two rotating
+//     shuffles (lane 0 reads lanes 31 and 30), with no per-lane fix-up.
+//     Values >= 1e30 stand for unreachable cells and never reach a
+//     reachable end cell, whose cost is far below.
+//   - The border values come from a ring in shared memory.  Within a CTA the
+//     warp above fills it and publishes its progress every kSub columns with
+//     a release store that the reader acquires.  Across CTAs the bottom rows travel through
+//     a border buffer in global memory whose 64-bit entries carry the call's
+//     tag next to the value, so a matching tag proves the value is current;
+//     warp 0 loads them kWin columns ahead and checks them kSub at a time.
+//   - Per chunk of 16 columns the 16 cosine costs are formed first, as 16
+//     independent FMA chains, then the 16 DP steps run without branches; the
+//     only dependency chain left per step is shuffle -> FMA -> 3-input min.
 //   - A CTA owns kWarpsPerGroup consecutive strips (a "strip group");
 //     persistent CTAs take groups in order from an atomic ticket, so every
 //     group a CTA waits on was taken earlier by a running CTA.
@@ -38,8 +48,12 @@
 namespace pardtw {
 namespace {
 
-constexpr int kRing = 64;  // ring slots (columns) per warp
-constexpr int kRingMask = kRing - 1;
+constexpr int kRing = 64;  // ring capacity (columns) per warp
+constexpr int kSub = 8;    // columns between two progress synchronisations
+constexpr int kRingBlk = kRing / kSub;  // ring blocks of kSub columns
+constexpr int kGhost0 = kRowsPerStrip;  // first ghost lane (30)
+constexpr float kGhostCost = 1e30f;
+constexpr int kWin = 32;   // global border columns warp 0 keeps in flight
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ unsigned long long pack(float v, unsigned tag) {
@@ -48,17 +62,17 @@ __device__ __forceinline__ unsigned long long pack(float v, unsigned tag) {
 __device__ __forceinline__ float val_of(unsigned long long e) { return __uint_as_float((unsigned)e); }
 __device__ __forceinline__ unsigned tag_of(unsigned long long e) { return (unsigned)(e >> 32); }
 
-__device__ __forceinline__ void lds2(const unsigned long long* p, unsigned long long& a,
-                                     unsigned long long& b) {
-    asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];"
-                 : "=l"(a), "=l"(b)
-                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+// Shared-memory accessors.  The progress counters are accessed with
+// acquire/release semantics; their asm carries a memory clobber, so the
+// compiler keeps the plain ring loads and stores of a synchronisation step
+// after the acquire and before the release.
+__device__ __forceinline__ int ld_acquire_s(unsigned addr) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
 }
-__device__ __forceinline__ void sts2(unsigned long long* p, unsigned long long a,
-                                     unsigned long long b) {
-    asm volatile("st.volatile.shared.v2.u64 [%0], {%1, %2};" ::"r"(
-                     (unsigned)__cvta_generic_to_shared(p)),
-                 "l"(a), "l"(b));
+__device__ __forceinline__ void st_release_s(unsigned addr, int v) {
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 // Border entries in global memory are two 64-bit words, each (value, tag);
 // every word is read and written as one relaxed gpu-scope 64-bit access,
@@ -68,10 +82,8 @@ __device__ __forceinline__ void ldg2(const unsigned long long* p, unsigned long 
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p));
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p + 1));
 }
-__device__ __forceinline__ void stg2(unsigned long long* p, unsigned long long a,
-                                     unsigned long long b) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a));
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p + 1), "l"(b));
+__device__ __forceinline__ void stg1(unsigned long long* p, unsigned long long a) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
 __device__ __forceinline__ long long global_ns() {
     long long t;
@@ -92,154 +104,252 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return m;
 }
 
-struct Entry {
-    unsigned long long e0, e1;
-    int ok;
-};
+// Polls between two checks of the call's failure flag and of the deadline.
+constexpr int kFastPolls = 128;
 
-// Slow path of a ring read: poll the slot until its tags match in every
-// lane, the call fails elsewhere, or the deadline passes.  Every decision is
-// a warp vote or comes from lane 0: lanes of a warp are not guaranteed to
-// execute a load together, so two lanes may see different tags, and a
-// per-lane branch in front of the warp-wide shuffles would be unsafe.
-__device__ __noinline__ Entry wait_ring_slot(const unsigned long long* slot, unsigned tag,
-                                             DevCtl* ctl, long long timeout_ns, int where) {
-    Entry r;
-    const long long t0 = __shfl_sync(kFull, global_ns(), 0);
-    for (;;) {
-        __nanosleep(40);
-        lds2(slot, r.e0, r.e1);
-        if (__all_sync(kFull, tag_of(r.e0) == tag && tag_of(r.e1) == tag)) {
-            r.ok = 1;
-            return r;
-        }
-        const int st = __shfl_sync(kFull, read_status(ctl), 0);
-        if (st != 0) break;
+// Wait until the shared counter at `addr` reaches `need` (acquire loads in
+// every lane; the decision is a warp vote, so the warp never splits in front
+// of its shuffles).  Bounded: gives up when the call fails elsewhere or the
+// deadline passes.
+__device__ __noinline__ int wait_counter(unsigned addr, int need, DevCtl* ctl,
+                                         long long timeout_ns, int where) {
+    long long t0 = 0;
+    for (int round = 0;; ++round) {
+        for (int k = 0; k < kFastPolls; ++k)
+            if (__all_sync(kFull, ld_acquire_s(addr) >= need)) return 1;
         const long long now = __shfl_sync(kFull, global_ns(), 0);
+        if (round == 0) t0 = now;
+        if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
         if (now - t0 > timeout_ns) {
             if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, where);
-            break;
-        }
-    }
-    r.ok = 0;
-    return r;
-}
-
-// Producer side of a ring: wait until the consumer warp has read far enough
-// that the slots about to be overwritten are free.
-__device__ __noinline__ int wait_consumer(const volatile int* cons, int need, DevCtl* ctl,
-                                          long long timeout_ns) {
-    const long long t0 = __shfl_sync(kFull, global_ns(), 0);
-    for (;;) {
-        __nanosleep(40);
-        if (__shfl_sync(kFull, *cons, 0) >= need) return 1;
-        if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
-        const long long now = __shfl_sync(kFull, global_ns(), 0);
-        if (now - t0 > timeout_ns) {
-            if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 2);
             return 0;
         }
+        if (round >= 8) __nanosleep(256);
     }
 }
+__device__ __forceinline__ int wait_counter_fast(unsigned addr, int need, DevCtl* ctl,
+                                                 long long timeout_ns, int where) {
+    if (__all_sync(kFull, ld_acquire_s(addr) >= need)) return 1;
+    return wait_counter(addr, need, ctl, timeout_ns, where);
+}
 
-// Warp 0 of a group: move the next 32 columns of the top border into its
-// ring.  For group 0 the border is +inf (no rows above row 0).  Otherwise
-// (g0, g1) hold the entries of columns [j0, j0+32) loaded one block earlier
-// from the group above; they are validated by tag (re-polled if stale), then
-// the loads of the following block are issued.
-__device__ __forceinline__ int refill_top(unsigned long long* myring, int j0, int lane, int Lb,
-                                          int g, const unsigned long long* gin, unsigned epoch,
+// Warp 0 of a group g > 0: columns [js, js+kSub) of the border above, held
+// in the lanes l with (l - js) mod 32 < kSub (lane l holds the column
+// congruent to l mod 32 of the current kWin window), are validated by tag
+// (re-polled from L2 while stale), copied into the warp's own ring block,
+// and replaced by the loads of the columns kWin further on.
+__device__ __forceinline__ int refill_top(float (*blk)[kSub], int js, int lane, int Lb,
+                                          const unsigned long long* gin, unsigned epoch,
                                           unsigned long long& g0, unsigned long long& g1,
                                           DevCtl* ctl, long long timeout_ns) {
-    const int col = j0 + lane;
-    if (g == 0) {
-        if (col < Lb)
-            sts2(myring + (col & kRingMask) * 2, pack(INFINITY, col + 1), pack(INFINITY, col + 1));
-        __syncwarp();
-        return 1;
-    }
-    if (j0 == 0 && col < Lb) ldg2(gin + (size_t)col * 2, g0, g1);
-    int ok = col >= Lb || (tag_of(g0) == epoch && tag_of(g1) == epoch);
+    const int off = (lane - js) & (kWin - 1);
+    const int col = js + off;
+    const bool act = off < kSub && col < Lb;
+    int ok = !act || (tag_of(g0) == epoch && tag_of(g1) == epoch);
     if (!__all_sync(kFull, ok)) {
+        // each poll is a round trip to L2; status and deadline every 16 polls
         const long long t0 = __shfl_sync(kFull, global_ns(), 0);
-        for (;;) {
-            __nanosleep(200);
+        for (int poll = 1;; ++poll) {
             if (!ok) {
                 ldg2(gin + (size_t)col * 2, g0, g1);
                 ok = tag_of(g0) == epoch && tag_of(g1) == epoch;
             }
             if (__all_sync(kFull, ok)) break;
-            if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
-            const long long now = __shfl_sync(kFull, global_ns(), 0);
-            if (now - t0 > timeout_ns) {
-                if (lane == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 3);
-                return 0;
+            if ((poll & 15) == 0) {
+                if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > timeout_ns) {
+                    if (lane == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 3);
+                    return 0;
+                }
+                if (poll >= 256) __nanosleep(256);
             }
         }
     }
-    if (col < Lb)
-        sts2(myring + (col & kRingMask) * 2, pack(val_of(g0), col + 1), pack(val_of(g1), col + 1));
-    if (col + 32 < Lb) ldg2(gin + (size_t)(col + 32) * 2, g0, g1);
+    if (act) {
+        blk[0][off] = val_of(g0);
+        blk[1][off] = val_of(g1);
+        if (col + kWin < Lb) ldg2(gin + (size_t)(col + kWin) * 2, g0, g1);
+    }
     __syncwarp();
     return 1;
 }
 
-// The B frame of one column.  Small frames (DP <= 16) are loaded one step
-// ahead into registers; larger ones are streamed from L1 inside the dot
-// product to keep the register count bounded.
-template <int DP, bool kHold = (DP <= 16)>
-struct BFrame {
-    float4 v[DP / 4];
-    __device__ __forceinline__ void load(const float* Bhat, int j) {
-        const float4* s = reinterpret_cast<const float4*>(Bhat + (size_t)j * DP);
-#pragma unroll
-        for (int q = 0; q < DP / 4; ++q) v[q] = __ldg(s + q);
-    }
-    __device__ __forceinline__ float dot_from(const float* na, float acc, const float*, int) const {
-#pragma unroll
-        for (int q = 0; q < DP / 4; ++q) {
-            acc = fmaf(na[4 * q], v[q].x, acc);
-            acc = fmaf(na[4 * q + 1], v[q].y, acc);
-            acc = fmaf(na[4 * q + 2], v[q].z, acc);
-            acc = fmaf(na[4 * q + 3], v[q].w, acc);
-        }
-        return acc;
-    }
-};
+// B frames reach the cost computation through a per-warp ring of kSlots
+// blocks in shared memory, filled by TMA bulk copies (cp.async.bulk) with
+// one mbarrier per slot.  Block t of a warp's lifetime sits in slot
+// t % kSlots; its mbarrier phase parity is (t / kSlots) & 1.  A copy is
+// issued three blocks ahead of use, so the L2 latency never meets the
+// sweep.  Only lane 0 issues; all lanes wait on the barrier.
 template <int DP>
-struct BFrame<DP, false> {
-    __device__ __forceinline__ void load(const float*, int) {}
-    __device__ __forceinline__ float dot_from(const float* na, float acc, const float* Bhat,
-                                              int j) const {
-        const float4* s = reinterpret_cast<const float4*>(Bhat + (size_t)j * DP);
-#pragma unroll
-        for (int q = 0; q < DP / 4; ++q) {
-            const float4 b = __ldg(s + q);
-            acc = fmaf(na[4 * q], b.x, acc);
-            acc = fmaf(na[4 * q + 1], b.y, acc);
-            acc = fmaf(na[4 * q + 2], b.z, acc);
-            acc = fmaf(na[4 * q + 3], b.w, acc);
+struct BStage {
+    static constexpr int kBlk = DP <= 16 ? 64 : (DP <= 32 ? 32 : 16);  // frames per copy
+    static constexpr int kSlots = 4;
+    static constexpr int kAhead = kSlots - 1;
+    static constexpr int kWarpBytes = kSlots * kBlk * DP * 4;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ int mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return (int)done;
+}
+// Lane 0: copy `bytes` from global `src` into shared `dst`, completing on `bar`.
+__device__ __forceinline__ void tma_load(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+    // earlier generic-proxy reads of this slot are ordered before the
+    // async-proxy write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+template <int DP>
+struct BRing {
+    using S = BStage<DP>;
+    const float* stage;   // this warp's kSlots * kBlk frames
+    unsigned stage_s;     // its shared address
+    unsigned bar_s;       // shared address of this warp's kSlots mbarriers
+    unsigned base;        // lifetime block number of block 0 of the current strip
+    int nblk;             // blocks in the current strip (ceil(Lb / kBlk))
+    int issued;           // blocks of this strip issued so far
+    int waited;           // blocks of this strip known complete
+
+    __device__ __forceinline__ void issue(int q, const float* Bhat, int Lb, int lane) {
+        if (lane == 0) {
+            const unsigned t = base + (unsigned)q;
+            const int f0 = q * S::kBlk;
+            const int nf = min(S::kBlk, Lb - f0);
+            tma_load(stage_s + (t % S::kSlots) * (S::kBlk * DP * 4), Bhat + (size_t)f0 * DP,
+                     (unsigned)(nf * DP * 4), bar_s + (t % S::kSlots) * 8);
         }
-        return acc;
+    }
+    // Issue the blocks that fit ahead of block `q` (the one about to be read).
+    __device__ __forceinline__ void top_up(int q, const float* Bhat, int Lb, int lane) {
+        while (issued < nblk && issued <= q + S::kAhead) {
+            issue(issued, Bhat, Lb, lane);
+            ++issued;
+        }
+    }
+    // Wait until block q is in shared memory (bounded); warp-uniform.
+    __device__ __forceinline__ int wait(int q, DevCtl* ctl, long long timeout_ns) {
+        const unsigned t = base + (unsigned)q;
+        const unsigned bar = bar_s + (t % S::kSlots) * 8;
+        const unsigned par = (t / S::kSlots) & 1u;
+        if (__all_sync(kFull, mbar_try_wait(bar, par))) {
+            waited = q + 1;
+            return 1;
+        }
+        const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+        for (int poll = 1;; ++poll) {
+            if (__all_sync(kFull, mbar_try_wait(bar, par))) {
+                waited = q + 1;
+                return 1;
+            }
+            if ((poll & 63) == 0) {
+                if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > timeout_ns) {
+                    if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 4);
+                    return 0;
+                }
+            }
+        }
+    }
+    // Before leaving a strip early: let every issued copy land (bounded), so
+    // no bulk copy is still writing this CTA's shared memory.
+    __device__ __forceinline__ void drain() {
+        for (int q = waited; q < issued; ++q) {
+            const unsigned t = base + (unsigned)q;
+            const unsigned bar = bar_s + (t % S::kSlots) * 8;
+            const unsigned par = (t / S::kSlots) & 1u;
+            const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+            while (!__all_sync(kFull, mbar_try_wait(bar, par))) {
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > 1000000000LL) break;  // 1 s: give up on this copy
+            }
+        }
+        waited = issued;
+    }
+    // Frame f of the strip (its block must be complete).
+    __device__ __forceinline__ const float4* frame(int f) const {
+        const unsigned t = base + (unsigned)(f / S::kBlk);
+        return reinterpret_cast<const float4*>(stage + ((size_t)(t % S::kSlots) * S::kBlk +
+                                                        (size_t)(f % S::kBlk)) * DP);
     }
 };
 
-// One warp sweeps its 32-row strip over all columns.
+// C' = (1 - mu) - a^_i . b^_j: one FMA per feature, in feature order, from
+// the negated row a^_i held in registers and the frame b^_j in shared memory
+// (broadcast reads: every lane reads the same address).
+template <int DP>
+__device__ __forceinline__ float cost_of(const float* na, float kcost, const float4* b) {
+    float acc = kcost;
+#pragma unroll
+    for (int q = 0; q < DP / 4; ++q) {
+        const float4 v = b[q];
+        acc = fmaf(na[4 * q], v.x, acc);
+        acc = fmaf(na[4 * q + 1], v.y, acc);
+        acc = fmaf(na[4 * q + 2], v.z, acc);
+        acc = fmaf(na[4 * q + 3], v.w, acc);
+    }
+    return acc;
+}
+
+// One DP step of column j for the warp's 32 lanes: no memory access and no
+// branch.  Lane sources srcA = lane-1, srcB = lane-2 (mod 32) give rows i-1
+// and i-2 of column j-1; x1p holds row i-1 of column j-2 (for a ghost lane:
+// its own border value of column j).
+__device__ __forceinline__ void dp_step(float cost, unsigned bit, int srcA, int srcB, float w12,
+                                        bool origin_here, float mu, float& cur, float& x1p,
+                                        float& x1, uint32_t& word, float& out) {
+    x1 = __shfl_sync(kFull, cur, srcA);        // E[i-1][j-1]
+    const float x2 = __shfl_sync(kFull, cur, srcB);  // E[i-2][j-1]
+    const float c0 = fmaf(2.0f, cost, x1);  // from (i-1, j-1)
+    const float c1 = fmaf(w12, cost, x1p);  // from (i-1, j-2)
+    const float c2 = fmaf(3.0f, cost, x2);  // from (i-2, j-1)
+    float m = min3f(c0, c1, c2);
+    const uint32_t code = (c0 == m) ? 0u : ((c1 == m) ? 1u : 2u);
+    m = origin_here ? cost + mu : m;  // E[0][0] = C[0][0]
+    word |= code << bit;
+    out = m;
+    cur = m;
+}
+
+// One warp sweeps its strip (30 rows + 2 ghost lanes) over all columns.
 template <int DP, int NW>
 __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lane,
-                                          unsigned long long (*ring)[kRing][2],
-                                          volatile int* cons) {
+                                          float (*ring)[kRingBlk][2][kSub], int* prod, int* cons,
+                                          BRing<DP>& br) {
+    using S = BStage<DP>;
     const int strip = g * NW + w;
     if (strip >= p.nstrips) return;
-    const int i = strip * kRowsPerStrip + lane;
+    const bool ghost = lane >= kGhost0;
+    const int i = strip * kRowsPerStrip + lane;  // row of a real lane
     const int Lb = p.Lb;
 
-    float na[DP];  // -a^_i
+    float na[DP];  // -a^_i (0 in ghost lanes)
     {
         const float4* s = reinterpret_cast<const float4*>(p.Ahat + (size_t)i * DP);
 #pragma unroll
         for (int q = 0; q < DP / 4; ++q) {
-            const float4 v = __ldg(s + q);
+            const float4 v = ghost ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(s + q);
             na[4 * q] = -v.x;
             na[4 * q + 1] = -v.y;
             na[4 * q + 2] = -v.z;
@@ -248,139 +358,205 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
     }
     const bool to_ring = (w + 1 < NW) && (strip + 1 < p.nstrips);
     const bool to_global = (w == NW - 1) && (g + 1 < p.ngroups) && (g != p.skip_publish);
-    unsigned long long* myring = &ring[w][0][0];
-    unsigned long long* nextring = &ring[(w + 1) % NW][0][0];
+    const bool out_lane = (lane == kGhost0 - 2) || (lane == kGhost0 - 1);  // rows 28, 29
+    const int out_comp = lane - (kGhost0 - 2);                             // 0 or 1
+    float (*myring)[2][kSub] = ring[w];
+    float (*nextring)[2][kSub] = ring[(w + 1) % NW];
+    const int in_comp = (lane == 31) ? 1 : 0;  // lane 30: row top-2, lane 31: row top-1
+    const unsigned prod_in = smem_u32(&prod[w]);
+    const unsigned prod_out = smem_u32(&prod[(w + 1) % NW]);
+    const unsigned cons_mine = smem_u32(&cons[w]);
+    const unsigned cons_next = smem_u32(&cons[(w + 1) % NW]);
     unsigned long long* gout = p.gborder + (size_t)g * Lb * 2;
     const unsigned long long* gin = p.gborder + (size_t)(g > 0 ? g - 1 : 0) * Lb * 2;
-    const float kcost = p.kcost;
+    const float kcost = ghost ? kGhostCost : p.kcost;
+    const float mu = p.mu;
+    const float w12 = ghost ? 0.0f : 3.0f;
+    const int srcA = (lane + 31) & 31, srcB = (lane + 30) & 31;
+    const unsigned epoch = p.epoch;
     const bool is_origin = (i == 0);
+    const bool from_global = (w == 0) && (g > 0);
+
+    // B pipeline and, for warp 0 below another group, the border window
+    br.base += (unsigned)br.nblk;  // continue the lifetime block numbering
+    br.nblk = (Lb + S::kBlk - 1) / S::kBlk;
+    br.issued = 0;
+    br.waited = 0;
+    br.top_up(0, p.Bhat, Lb, lane);
+    unsigned long long g0 = 0, g1 = 0;
+    if (from_global && lane < Lb) ldg2(gin + (size_t)lane * 2, g0, g1);
 
     float cur = INFINITY;  // E[i][j-1]
-    float x1p = INFINITY;  // E[i-1][j-2]
-    unsigned long long g0 = 0, g1 = 0;
-    BFrame<DP> bcur;
-    bcur.load(p.Bhat, 0);
-
+    float x1p = INFINITY;  // E[i-1][j-2]; a ghost lane: its border value of column j
+    float x1 = INFINITY;
     // The failure flag is loaded one chunk ahead of its test, so the load's
     // latency never stalls the sweep.
     int status_seen = 0;
     for (int j0 = 0; j0 < Lb; j0 += kColsPerWord) {
-        if (__shfl_sync(kFull, status_seen, 0) != 0) return;
+        if (__shfl_sync(kFull, status_seen, 0) != 0) {
+            br.drain();
+            return;
+        }
         status_seen = read_status(p.ctl);
-        if (w > 0 && lane == 0) {
-            __threadfence_block();
-            cons[w] = j0;
-        }
-        if (to_ring) {
-            const int need = j0 + kColsPerWord + 2 - kRing;
-            if (need > 0 && __shfl_sync(kFull, cons[w + 1], 0) < need)
-                if (!wait_consumer(&cons[w + 1], need, p.ctl, p.timeout_ns)) return;
-        }
-        if (w == 0 && (j0 & 31) == 0)
-            if (!refill_top(myring, j0, lane, Lb, g, gin, p.epoch, g0, g1, p.ctl, p.timeout_ns))
+        if ((j0 % S::kBlk) == 0) {
+            const int q = j0 / S::kBlk;
+            if (!br.wait(q, p.ctl, p.timeout_ns)) {
+                br.drain();
                 return;
-
+            }
+            br.top_up(q, p.Bhat, Lb, lane);
+        }
+        // the chunk's costs C' = (1 - mu) - a^_i . b^_j (1e30 in ghost lanes)
+        float c[kColsPerWord];
+        {
+            const float4* fb = br.frame(j0);
+            if (j0 + kColsPerWord <= Lb) {
+#pragma unroll
+                for (int u = 0; u < kColsPerWord; ++u)
+                    c[u] = cost_of<DP>(na, kcost, fb + u * (DP / 4));
+            } else {
+#pragma unroll
+                for (int u = 0; u < kColsPerWord; ++u)
+                    c[u] = (j0 + u < Lb) ? cost_of<DP>(na, kcost, fb + u * (DP / 4)) : 0.f;
+            }
+        }
         uint32_t word = 0;
 #pragma unroll
-        for (int u = 0; u < kColsPerWord; ++u) {
-            const int j = j0 + u;
-            if (j >= Lb) break;
-            BFrame<DP> bnext;
-            if (j + 1 < Lb) bnext.load(p.Bhat, j + 1);
-
-            // C' = (1 - mu) - a^_i . b^_j, one FMA per feature in order
-            const float acc = bcur.dot_from(na, kcost, p.Bhat, j);
-
-            // the strip above: E[top-2][j-1], E[top-1][j-1]
-            float t30 = INFINITY, t31 = INFINITY;
-            if (j > 0) {
-                const unsigned long long* slot = myring + ((j - 1) & kRingMask) * 2;
-                Entry e;
-                lds2(slot, e.e0, e.e1);
-                if (!__all_sync(kFull, tag_of(e.e0) == (unsigned)j &&
-                                           tag_of(e.e1) == (unsigned)j)) {
-                    e = wait_ring_slot(slot, (unsigned)j, p.ctl, p.timeout_ns, 1);
-                    if (!e.ok) return;
+        for (int h = 0; h < kColsPerWord / kSub; ++h) {
+            const int js = j0 + h * kSub;
+            if (js >= Lb) break;
+            const int nsteps = min(kSub, Lb - js);
+            const int b = (js / kSub) % kRingBlk;
+            // border values of columns js .. js+nsteps-1
+            if (from_global) {
+                if (!refill_top(myring[b], js, lane, Lb, gin, epoch, g0, g1, p.ctl,
+                                p.timeout_ns)) {
+                    br.drain();
+                    return;
                 }
-                t30 = val_of(e.e0);
-                t31 = val_of(e.e1);
+            } else if (w > 0) {
+                if (!wait_counter_fast(prod_in, js + nsteps, p.ctl, p.timeout_ns, 1)) {
+                    br.drain();
+                    return;
+                }
             }
-            float x1 = __shfl_up_sync(kFull, cur, 1);  // E[i-1][j-1]
-            float x2 = __shfl_up_sync(kFull, cur, 2);  // E[i-2][j-1]
-            if (lane == 0) {
-                x1 = t31;
-                x2 = t30;
+            if (w > 0 && lane == 0) st_release_s(cons_mine, js);  // windows < js are read
+            if (to_ring) {
+                // the ring block about to be written must have been read below
+                const int need = js + 2 * kSub - kRing;
+                if (need > 0 && !wait_counter_fast(cons_next, need, p.ctl, p.timeout_ns, 2)) {
+                    br.drain();
+                    return;
+                }
             }
-            if (lane == 1) x2 = t31;
-
-            const float c0 = fmaf(2.0f, acc, x1);   // from (i-1, j-1)
-            const float c1 = fmaf(3.0f, acc, x1p);  // from (i-1, j-2)
-            const float c2 = fmaf(3.0f, acc, x2);   // from (i-2, j-1)
-            float m = min3f(c0, c1, c2);
-            const uint32_t code = (c0 == m) ? 0u : ((c1 == m) ? 1u : 2u);
-            if (j == 0 && is_origin) m = acc + p.mu;  // E[0][0] = C[0][0]
-            word |= code << (2 * u);
-
-            // bottom two rows of this strip, column j-1, to the strip below
-            if (lane == 31 && j > 0) {
-                if (to_ring)
-                    sts2(nextring + ((j - 1) & kRingMask) * 2, pack(x1, j), pack(cur, j));
-                else if (to_global)
-                    stg2(gout + (size_t)(j - 1) * 2, pack(x1, p.epoch), pack(cur, p.epoch));
+            float gv[kSub];  // ghost lanes: border value of columns js .. js+kSub-1
+            {
+                const float4* src = reinterpret_cast<const float4*>(&myring[b][in_comp][0]);
+                const float4 v0 = src[0], v1 = src[1];
+                gv[0] = v0.x; gv[1] = v0.y; gv[2] = v0.z; gv[3] = v0.w;
+                gv[4] = v1.x; gv[5] = v1.y; gv[6] = v1.z; gv[7] = v1.w;
             }
-            x1p = x1;
-            cur = m;
-            bcur = bnext;
+            x1p = ghost ? gv[0] : x1p;
+            float o[kSub];  // rows 28, 29: own values of columns js .. js+kSub-1
+            if (nsteps == kSub) {
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    const int uu = h * kSub + u;
+                    dp_step(c[uu], 2u * uu, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
+                            mu, cur, x1p, x1, word, o[u]);
+                    x1p = (u + 1 < kSub && ghost) ? gv[u + 1 < kSub ? u + 1 : 0] : x1;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    const int uu = h * kSub + u;
+                    if (u >= nsteps) break;
+                    dp_step(c[uu], 2u * uu, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
+                            mu, cur, x1p, x1, word, o[u]);
+                    x1p = (u + 1 < kSub && ghost) ? gv[u + 1 < kSub ? u + 1 : 0] : x1;
+                }
+            }
+            if (to_ring) {
+                if (out_lane) {
+                    float4* dst = reinterpret_cast<float4*>(&nextring[b][out_comp][0]);
+                    dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+                    dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+                }
+                __syncwarp();
+                // columns < js+nsteps of the bottom rows are in the ring below
+                if (lane == kGhost0 - 1) st_release_s(prod_out, js + nsteps);
+            } else if (to_global && out_lane) {
+#pragma unroll
+                for (int u = 0; u < kSub; ++u)
+                    if (u < nsteps)
+                        stg1(gout + (size_t)(js + u) * 2 + out_comp, pack(o[u], epoch));
+            }
         }
         p.bp[((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * 32 + lane] = word;
     }
-    // column Lb-1 of the bottom rows
-    const float xl = __shfl_up_sync(kFull, cur, 1);
-    if (lane == 31) {
-        if (to_ring)
-            sts2(nextring + ((Lb - 1) & kRingMask) * 2, pack(xl, Lb), pack(cur, Lb));
-        else if (to_global)
-            stg2(gout + (size_t)(Lb - 1) * 2, pack(xl, p.epoch), pack(cur, p.epoch));
-    }
-    if (i == p.La - 1) *p.e_final = cur;
+    if (!ghost && i == p.La - 1) *p.e_final = cur;
 }
 
 template <int DP, int NW>
-__global__ void __launch_bounds__(NW * 32, DP <= 32 ? 4 : 1) k_dp(const DpArgs p) {
-    __shared__ __align__(16) unsigned long long ring[NW][kRing][2];
-    __shared__ volatile int cons[NW];
+__global__ void __launch_bounds__(NW * 32, DP <= 32 ? 2 : 1) k_dp(const DpArgs p) {
+    using S = BStage<DP>;
+    __shared__ __align__(16) float ring[NW][kRingBlk][2][kSub];
+    __shared__ __align__(8) unsigned long long bars[NW][S::kSlots];
+    __shared__ int prod[NW];
+    __shared__ int cons[NW];
     __shared__ int s_group;
+    extern __shared__ __align__(128) unsigned char bstage[];  // NW * S::kWarpBytes
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+
+    BRing<DP> br;
+    br.stage = reinterpret_cast<const float*>(bstage + (size_t)w * S::kWarpBytes);
+    br.stage_s = smem_u32(bstage + (size_t)w * S::kWarpBytes);
+    br.bar_s = smem_u32(&bars[w][0]);
+    br.base = 0;
+    br.nblk = 0;
+    br.issued = br.waited = 0;
+    if (lane == 0) {
+        for (int k = 0; k < S::kSlots; ++k) mbar_init(br.bar_s + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
     for (;;) {
         __syncthreads();  // every warp finished the previous group
         if (threadIdx.x == 0) {
             s_group = read_status(p.ctl) != 0 ? p.ngroups : atomicAdd(&p.ctl->ticket, 1);
         }
-        for (int k = threadIdx.x; k < NW * kRing; k += blockDim.x) {
-            ring[k / kRing][k % kRing][0] = 0ull;
-            ring[k / kRing][k % kRing][1] = 0ull;
+        // +inf border: group 0's top rows, and nothing is read before it is written
+        float* rf = &ring[0][0][0][0];
+        for (int k = threadIdx.x; k < NW * kRing * 2; k += blockDim.x) rf[k] = INFINITY;
+        if (threadIdx.x < NW) {
+            prod[threadIdx.x] = 0;
+            cons[threadIdx.x] = 0;
         }
-        if (threadIdx.x < NW) cons[threadIdx.x] = 0;
         __syncthreads();
         const int g = s_group;
         if (g >= p.ngroups) return;
-        run_strip<DP, NW>(p, g, w, lane, ring, cons);
+        run_strip<DP, NW>(p, g, w, lane, ring, prod, cons, br);
     }
 }
 
 template <int DP>
 cudaError_t launch_dp_t(const DpArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NW = kWarpsPerGroup;
+    const int smem = NW * BStage<DP>::kWarpBytes;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dp<DP, NW>, NW * 32, 0);
+        cudaError_t e = cudaFuncSetAttribute(k_dp<DP, NW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dp<DP, NW>, NW * 32,
+                                                          smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int grid = blocks_per_sm * num_sms;
     if (grid > a.ngroups) grid = a.ngroups;
-    k_dp<DP, NW><<<grid, NW * 32, 0, s>>>(a);
+    k_dp<DP, NW><<<grid, NW * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@
 namespace pardtw {
 
 constexpr int kWarp = 32;
-constexpr int kRowsPerStrip = 32;   // one warp lane per row of A
+constexpr int kRowsPerStrip = 30;   // rows of A per warp: lanes 0..29 (lanes 30, 31 carry
+                                    // the two bottom rows of the strip above)
 constexpr int kColsPerWord = 16;    // 2-bit codes per uint32 backpointer word
 constexpr int kWarpsPerGroup = 4;   // strips per CTA ("strip group")
 
@@ -25,9 +26,9 @@ struct DevCtl {
 
 // Arguments of the column-sweep DP kernel.
 struct DpArgs {
-    const float* Ahat;              // nstrips*32 x dp, row-normalised, rows >= La are zero
+    const float* Ahat;              // nstrips*30 x dp, row-normalised, rows >= La are zero
     const float* Bhat;              // Lb x dp, row-normalised
-    uint32_t* bp;                   // nstrips * nchunk * 32 words (strip, chunk, lane)
+    uint32_t* bp;                   // nstrips * nchunk * 32 words (strip, chunk, row in strip)
     unsigned long long* gborder;    // ngroups * Lb * 2 tagged values (group bottom rows)
     DevCtl* ctl;
     float* e_final;                 // shifted cumulative cost at (La-1, Lb-1)
@@ -41,9 +42,12 @@ struct DpArgs {
 };
 
 // Backpointer word address of cell (i, j): strip-major, then 16-column chunk,
-// then row within the strip.  One warp store covers 32 consecutive words.
+// then row within the strip (32 words per strip and chunk, of which the
+// first 30 hold rows).  One warp store covers 32 consecutive words (128 B).
 __host__ __device__ inline size_t bp_word_index(int i, int j, int nchunk) {
-    return ((size_t)(i >> 5) * (size_t)nchunk + (size_t)(j >> 4)) * 32u + (size_t)(i & 31);
+    const int strip = i / kRowsPerStrip;
+    return ((size_t)strip * (size_t)nchunk + (size_t)(j >> 4)) * 32u +
+           (size_t)(i - strip * kRowsPerStrip);
 }
 
 // Launchers (each returns a cudaError_t from the launch).
