@@ -65,15 +65,18 @@ typedef struct dtw_options {
      * per-step cost along the path keeps FP32 partial sums small and cuts
      * their rounding.  0 = no shift. */
     float cost_shift;
-    /* Upper bound on polling iterations of a device-side wait for a
-     * neighbouring tile's border (each iteration backs off ~0.1-1 us);
-     * 0 = library default (about 2 s).  On expiry the call fails with
-     * DTW_ERR_TIMEOUT. */
+    /* Deadline, in microseconds, of every device-side wait (for the border
+     * of the strip above, or for a staged block of B); 0 = library default
+     * (2 s).  On expiry the call fails with DTW_ERR_TIMEOUT. */
     int wait_limit;
     /* Fault injection for tests, -1 = off: the strip group with this index
      * never publishes its bottom border, so the group below it waits until
      * wait_limit and the call reports DTW_ERR_TIMEOUT. */
     int debug_skip_publish;
+    /* Rows of A each GPU lane sweeps (1, 2 or 4); 0 = chosen from La, D and
+     * the SM count.  Results do not depend on it (it only changes the work
+     * decomposition); D > 32 runs with 1. */
+    int rows_per_lane;
 } dtw_options;
 
 /* Fill *opt with the defaults: FP32 cost, no shift, default wait limit,
@@ -98,10 +101,11 @@ int dtw_destroy(dtw_handle* h);
 /* Rebind the handle to another stream (later calls are ordered on it). */
 int dtw_set_stream(dtw_handle* h, void* cuda_stream);
 
-/* Bytes of device workspace dtw_align needs for (La, Lb, D) (Sec. VI-D's
- * memory model: the 2-bit backtrace matrix dominates, La*Lb/4 bytes plus
- * padding to 32 rows x 16 columns, plus O((La+Lb)*D) for normalised
- * features and border buffers).  Errors: DTW_ERR_INVALID. */
+/* Upper bound on the bytes of device workspace dtw_align needs for
+ * (La, Lb, D) (Sec. VI-D's memory model: the 2-bit backtrace matrix
+ * dominates, La*Lb/4 bytes plus at most 7% padding, plus border rows
+ * between strip groups, La*Lb/8 bytes at most, plus O((La+Lb)*D)).
+ * Errors: DTW_ERR_INVALID. */
 int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes);
 
 /* ---- cost matrix (Sec. IV cosine distance; Sec. VI-B explicit matrix) ---- */

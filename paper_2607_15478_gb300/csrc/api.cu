@@ -76,19 +76,33 @@ bool reachable(int La, int Lb) {
 }
 
 struct Layout {
-    int dp, nstrips, nchunk, ngroups, La_pad, cap;
+    int dp, R, rps, wpb, nstrips, nchunk, ngroups, La_pad, cap;
     size_t off_ctl, off_ahat, off_bhat, off_bp, off_scratch, off_stage_a, off_stage_b,
         off_stage_path, total;
     size_t border_bytes;
 };
 
-Layout make_layout(int La, int Lb, int D) {
+// Rows per lane: the requested value if the fused DP supports it for this
+// dimension, else 2, or 4 when La leaves more than ~5 warps of 62 rows per SM.
+int choose_rows(int La, int dp, int requested, int num_sms) {
+    if (requested == 1) return 1;
+    if (requested == 2 || requested == 4) return multirow_supported(dp, requested) ? requested : 1;
+    if (!multirow_supported(dp, 2)) return 1;
+    const long long warps2 = (La + strip_rows(2) - 1) / strip_rows(2);
+    if (warps2 > 5LL * num_sms && multirow_supported(dp, 4)) return 4;
+    return 2;
+}
+
+Layout make_layout(int La, int Lb, int D, int R) {
     Layout L;
     L.dp = padded_dim(D);
-    L.nstrips = (La + kRowsPerStrip - 1) / kRowsPerStrip;
+    L.R = R;
+    L.rps = strip_rows(R);
+    L.wpb = strip_words(R);
+    L.nstrips = (La + L.rps - 1) / L.rps;
     L.nchunk = (Lb + kColsPerWord - 1) / kColsPerWord;
     L.ngroups = (L.nstrips + kWarpsPerGroup - 1) / kWarpsPerGroup;
-    L.La_pad = L.nstrips * kRowsPerStrip;
+    L.La_pad = L.nstrips * L.rps;
     L.cap = std::min(La, Lb);
     size_t o = 0;
     L.off_ctl = o;  // DevCtl, e_final, total, path_len
@@ -96,9 +110,9 @@ Layout make_layout(int La, int Lb, int D) {
     L.off_ahat = o;
     o = align256(o + (size_t)L.La_pad * L.dp * sizeof(float));
     L.off_bhat = o;
-    o = align256(o + (size_t)Lb * L.dp * sizeof(float));
+    o = align256(o + (size_t)L.nchunk * kColsPerWord * L.dp * sizeof(float));
     L.off_bp = o;
-    o = align256(o + (size_t)L.nstrips * L.nchunk * 32 * sizeof(uint32_t));
+    o = align256(o + (size_t)L.nstrips * L.nchunk * L.wpb * sizeof(uint32_t));
     L.off_scratch = o;
     o = align256(o + (size_t)2 * L.cap * sizeof(int32_t));
     L.off_stage_a = o;
@@ -155,6 +169,7 @@ dtw_options defaults() {
     o.cost_shift = 0.0f;
     o.wait_limit = 0;
     o.debug_skip_publish = -1;
+    o.rows_per_lane = 0;
     return o;
 }
 
@@ -162,7 +177,8 @@ dtw_options defaults() {
 // `out_len`, `out_total` are device pointers (out_total may be null).
 int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
                  const dtw_options& o, int32_t* out_path, int* out_len, float* out_total) {
-    const Layout L = make_layout(La, Lb, D);
+    const Layout L =
+        make_layout(La, Lb, D, choose_rows(La, padded_dim(D), o.rows_per_lane, h->num_sms));
     int rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     cudaStream_t s = h->stream;
@@ -187,7 +203,8 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
         dB = st;
     }
     if (h->timing) CU(cudaEventRecord(h->ev[0], s));
-    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, D, L.dp, Ahat, Bhat, ctl, s));
+    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, L.nchunk * kColsPerWord, D, L.dp, Ahat, Bhat,
+                        ctl, s));
     if (h->timing) CU(cudaEventRecord(h->ev[1], s));
 
     DpArgs a;
@@ -202,15 +219,21 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     a.nstrips = L.nstrips;
     a.nchunk = L.nchunk;
     a.ngroups = L.ngroups;
+    a.rps = L.rps;
+    a.wpb = L.wpb;
     a.mu = o.cost_shift;
     a.kcost = 1.0f - o.cost_shift;
     a.epoch = ++h->epoch;
     if (a.epoch == 0) a.epoch = ++h->epoch;
     a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
     a.skip_publish = o.debug_skip_publish;
-    CU(launch_dp(a, L.dp, h->num_sms, s));
+    if (L.R == 1)
+        CU(launch_dp(a, L.dp, h->num_sms, s));
+    else
+        CU(launch_dp_multirow(a, L.dp, L.R, h->num_sms, s));
     if (h->timing) CU(cudaEventRecord(h->ev[2], s));
-    CU(launch_backtrace(bp, La, Lb, L.nchunk, ctl, e_final, o.cost_shift, out_path, scratch,
+    CU(launch_backtrace(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift, out_path,
+                        scratch,
                         out_len, out_total, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
@@ -303,8 +326,12 @@ int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* by
     (void)opt;
     if (!bytes || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
     if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
-    const Layout L = make_layout(La, Lb, D);
-    *bytes = L.total + L.border_bytes;
+    size_t most = 0;
+    for (int R : {1, 2, 4}) {
+        const Layout L = make_layout(La, Lb, D, R);
+        most = std::max(most, L.total + L.border_bytes);
+    }
+    *bytes = most;
     return DTW_OK;
 }
 
@@ -314,7 +341,7 @@ int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int 
     if (dp == 0) return DTW_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
-    const Layout L = make_layout(La, Lb, D);
+    const Layout L = make_layout(La, Lb, D, 1);
     const bool c_dev = is_device_ptr(C);
     const size_t cbytes = (size_t)La * Lb * sizeof(float);
     const size_t need = L.total + (c_dev ? 0 : align256(cbytes));
@@ -337,7 +364,8 @@ int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int 
     DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + L.off_ctl);
     float* Ahat = reinterpret_cast<float*>(ws + L.off_ahat);
     float* Bhat = reinterpret_cast<float*>(ws + L.off_bhat);
-    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, D, dp, Ahat, Bhat, ctl, s));
+    CU(launch_normalise(dA, La, L.La_pad, dB, Lb, L.nchunk * kColsPerWord, D, dp, Ahat, Bhat,
+                        ctl, s));
     float* dC = c_dev ? C : reinterpret_cast<float*>(ws + L.total);
     CU(launch_cost(Ahat, La, Bhat, Lb, dp, dC, s));
     if (!c_dev) {
@@ -359,7 +387,8 @@ int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
 
-    const Layout L = make_layout(La, Lb, D);
+    const Layout L = make_layout(La, Lb, D, choose_rows(La, padded_dim(D), o.rows_per_lane,
+                                                        h->num_sms));
     rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     const bool path_dev = is_device_ptr(path);

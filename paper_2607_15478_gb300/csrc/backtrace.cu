@@ -12,8 +12,8 @@
 
 namespace pardtw {
 
-__global__ void k_backtrace(const uint32_t* __restrict__ bp, int La, int Lb, int nchunk,
-                            const DevCtl* __restrict__ ctl, const float* __restrict__ e_final,
+__global__ void k_backtrace(const uint32_t* __restrict__ bp, int La, int Lb, int nchunk, int rps,
+                            int wpb, const DevCtl* __restrict__ ctl, const float* __restrict__ e_final,
                             float mu, int32_t* __restrict__ path, int32_t* __restrict__ scratch,
                             int* __restrict__ path_len, float* __restrict__ total) {
     __shared__ int s_len;
@@ -34,7 +34,7 @@ __global__ void k_backtrace(const uint32_t* __restrict__ bp, int La, int Lb, int
                 scratch[2 * (cap - 1 - n) + 1] = j;
                 ++n;
                 if (i == 0 && j == 0) break;
-                const uint32_t word = __ldg(bp + bp_word_index(i, j, nchunk));
+                const uint32_t word = __ldg(bp + bp_word_index(i, j, nchunk, rps, wpb));
                 const int code = (int)((word >> (2 * (j & 15))) & 3u);
                 if (code == 0) {
                     i -= 1;
@@ -69,11 +69,11 @@ __global__ void k_backtrace(const uint32_t* __restrict__ bp, int La, int Lb, int
     for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) path[k] = src[k];
 }
 
-cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, const DevCtl* ctl,
-                             const float* e_final, float mu, int32_t* path, int32_t* scratch,
-                             int* path_len, float* total, cudaStream_t s) {
-    k_backtrace<<<1, 256, 0, s>>>(bp, La, Lb, nchunk, ctl, e_final, mu, path, scratch, path_len,
-                                  total);
+cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int rps, int wpb,
+                             const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
+                             int32_t* scratch, int* path_len, float* total, cudaStream_t s) {
+    k_backtrace<<<1, 256, 0, s>>>(bp, La, Lb, nchunk, rps, wpb, ctl, e_final, mu, path, scratch,
+                                  path_len, total);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,264 @@
+// Device-side building blocks shared by the DP kernels: tagged border
+// entries, acquire/release progress counters, bounded waits, the top-border
+// refill from global memory, and the TMA-fed ring of B frames.
+// Internal to libpardtw; every translation unit gets its own copy.
+#pragma once
+
+#include <math.h>
+
+#include "pardtw_common.cuh"
+
+namespace pardtw {
+namespace {
+
+
+constexpr int kRing = 64;  // ring capacity (columns) per warp
+constexpr int kSub = 8;    // columns between two progress synchronisations
+constexpr int kRingBlk = kRing / kSub;  // ring blocks of kSub columns
+constexpr float kGhostCost = 1e30f;
+constexpr int kWin = 32;   // global border columns warp 0 keeps in flight
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long pack(float v, unsigned tag) {
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+__device__ __forceinline__ float val_of(unsigned long long e) { return __uint_as_float((unsigned)e); }
+__device__ __forceinline__ unsigned tag_of(unsigned long long e) { return (unsigned)(e >> 32); }
+
+// Shared-memory accessors.  The progress counters are accessed with
+// acquire/release semantics; their asm carries a memory clobber, so the
+// compiler keeps the plain ring loads and stores of a synchronisation step
+// after the acquire and before the release.
+__device__ __forceinline__ int ld_acquire_s(unsigned addr) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s(unsigned addr, int v) {
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Border entries in global memory are two 64-bit words, each (value, tag);
+// every word is read and written as one relaxed gpu-scope 64-bit access,
+// which is single-copy atomic, so a reader can trust a word whose tag matches.
+__device__ __forceinline__ void ldg2(const unsigned long long* p, unsigned long long& a,
+                                     unsigned long long& b) {
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p));
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p + 1));
+}
+__device__ __forceinline__ void stg1(unsigned long long* p, unsigned long long a) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int read_status(const DevCtl* c) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(&c->status));
+    return v;
+}
+__device__ __forceinline__ void raise_status(DevCtl* c, int code, int detail) {
+    if (atomicCAS(&c->status, 0, code) == 0) atomicExch(&c->detail, detail);
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float m;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    return m;
+}
+
+// Polls between two checks of the call's failure flag and of the deadline.
+constexpr int kFastPolls = 128;
+
+// Wait until the shared counter at `addr` reaches `need` (acquire loads in
+// every lane; the decision is a warp vote, so the warp never splits in front
+// of its shuffles).  Bounded: gives up when the call fails elsewhere or the
+// deadline passes.
+__device__ __noinline__ int wait_counter(unsigned addr, int need, DevCtl* ctl,
+                                         long long timeout_ns, int where) {
+    long long t0 = 0;
+    for (int round = 0;; ++round) {
+        for (int k = 0; k < kFastPolls; ++k)
+            if (__all_sync(kFull, ld_acquire_s(addr) >= need)) return 1;
+        const long long now = __shfl_sync(kFull, global_ns(), 0);
+        if (round == 0) t0 = now;
+        if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+        if (now - t0 > timeout_ns) {
+            if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, where);
+            return 0;
+        }
+        if (round >= 8) __nanosleep(256);
+    }
+}
+__device__ __forceinline__ int wait_counter_fast(unsigned addr, int need, DevCtl* ctl,
+                                                 long long timeout_ns, int where) {
+    if (__all_sync(kFull, ld_acquire_s(addr) >= need)) return 1;
+    return wait_counter(addr, need, ctl, timeout_ns, where);
+}
+
+// Warp 0 of a group g > 0: columns [js, js+kSub) of the border above, held
+// in the lanes l with (l - js) mod 32 < kSub (lane l holds the column
+// congruent to l mod 32 of the current kWin window), are validated by tag
+// (re-polled from L2 while stale), copied into the warp's own ring block,
+// and replaced by the loads of the columns kWin further on.
+__device__ __forceinline__ int refill_top(float (*blk)[kSub], int js, int lane, int Lb,
+                                          const unsigned long long* gin, unsigned epoch,
+                                          unsigned long long& g0, unsigned long long& g1,
+                                          DevCtl* ctl, long long timeout_ns) {
+    const int off = (lane - js) & (kWin - 1);
+    const int col = js + off;
+    const bool act = off < kSub && col < Lb;
+    int ok = !act || (tag_of(g0) == epoch && tag_of(g1) == epoch);
+    if (!__all_sync(kFull, ok)) {
+        // each poll is a round trip to L2; status and deadline every 16 polls
+        const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+        for (int poll = 1;; ++poll) {
+            if (!ok) {
+                ldg2(gin + (size_t)col * 2, g0, g1);
+                ok = tag_of(g0) == epoch && tag_of(g1) == epoch;
+            }
+            if (__all_sync(kFull, ok)) break;
+            if ((poll & 15) == 0) {
+                if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > timeout_ns) {
+                    if (lane == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 3);
+                    return 0;
+                }
+                if (poll >= 256) __nanosleep(256);
+            }
+        }
+    }
+    if (act) {
+        blk[0][off] = val_of(g0);
+        blk[1][off] = val_of(g1);
+        if (col + kWin < Lb) ldg2(gin + (size_t)(col + kWin) * 2, g0, g1);
+    }
+    __syncwarp();
+    return 1;
+}
+
+// B frames (chunk-transposed, see bt_index) reach the cost computation
+// through a per-warp ring of kSlots blocks in shared memory, filled by TMA
+// bulk copies (cp.async.bulk) with one mbarrier per slot.  Block t of a warp's lifetime sits in slot
+// t % kSlots; its mbarrier phase parity is (t / kSlots) & 1.  A copy is
+// issued three blocks ahead of use, so the L2 latency never meets the
+// sweep.  Only lane 0 issues; all lanes wait on the barrier.
+template <int DP>
+struct BStage {
+    static constexpr int kBlk = DP <= 16 ? 64 : (DP <= 32 ? 32 : 16);  // frames per copy
+    static constexpr int kSlots = 4;
+    static constexpr int kAhead = kSlots - 1;
+    static constexpr int kWarpBytes = kSlots * kBlk * DP * 4;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ int mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return (int)done;
+}
+// Lane 0: copy `bytes` from global `src` into shared `dst`, completing on `bar`.
+__device__ __forceinline__ void tma_load(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+    // earlier generic-proxy reads of this slot are ordered before the
+    // async-proxy write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+template <int DP>
+struct BRing {
+    using S = BStage<DP>;
+    const float* stage;   // this warp's kSlots * kBlk frames
+    unsigned stage_s;     // its shared address
+    unsigned bar_s;       // shared address of this warp's kSlots mbarriers
+    unsigned base;        // lifetime block number of block 0 of the current strip
+    int nblk;             // blocks in the current strip (ceil(Lb / kBlk))
+    int issued;           // blocks of this strip issued so far
+    int waited;           // blocks of this strip known complete
+
+    // Copy block q (frames q*kBlk .., whole 16-frame chunks) of the
+    // chunk-transposed B (Lb_pad frames) into its slot.
+    __device__ __forceinline__ void issue(int q, const float* Bt, int Lb_pad, int lane) {
+        if (lane == 0) {
+            const unsigned t = base + (unsigned)q;
+            const int f0 = q * S::kBlk;
+            const int nf = min(S::kBlk, Lb_pad - f0);
+            tma_load(stage_s + (t % S::kSlots) * (S::kBlk * DP * 4), Bt + (size_t)f0 * DP,
+                     (unsigned)(nf * DP * 4), bar_s + (t % S::kSlots) * 8);
+        }
+    }
+    // Issue the blocks that fit ahead of block `q` (the one about to be read).
+    __device__ __forceinline__ void top_up(int q, const float* Bt, int Lb_pad, int lane) {
+        while (issued < nblk && issued <= q + S::kAhead) {
+            issue(issued, Bt, Lb_pad, lane);
+            ++issued;
+        }
+    }
+    // Wait until block q is in shared memory (bounded); warp-uniform.
+    __device__ __forceinline__ int wait(int q, DevCtl* ctl, long long timeout_ns) {
+        const unsigned t = base + (unsigned)q;
+        const unsigned bar = bar_s + (t % S::kSlots) * 8;
+        const unsigned par = (t / S::kSlots) & 1u;
+        if (__all_sync(kFull, mbar_try_wait(bar, par))) {
+            waited = q + 1;
+            return 1;
+        }
+        const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+        for (int poll = 1;; ++poll) {
+            if (__all_sync(kFull, mbar_try_wait(bar, par))) {
+                waited = q + 1;
+                return 1;
+            }
+            if ((poll & 63) == 0) {
+                if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > timeout_ns) {
+                    if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, 4);
+                    return 0;
+                }
+            }
+        }
+    }
+    // Before leaving a strip early: let every issued copy land (bounded), so
+    // no bulk copy is still writing this CTA's shared memory.
+    __device__ __forceinline__ void drain() {
+        for (int q = waited; q < issued; ++q) {
+            const unsigned t = base + (unsigned)q;
+            const unsigned bar = bar_s + (t % S::kSlots) * 8;
+            const unsigned par = (t / S::kSlots) & 1u;
+            const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+            while (!__all_sync(kFull, mbar_try_wait(bar, par))) {
+                const long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (now - t0 > 1000000000LL) break;  // 1 s: give up on this copy
+            }
+        }
+        waited = issued;
+    }
+    // The 16 x DP feature-major values of chunk k (its block must be complete).
+    __device__ __forceinline__ const float* chunk(int k) const {
+        const int f = k * kColsPerWord;
+        const unsigned t = base + (unsigned)(f / S::kBlk);
+        return stage + ((size_t)(t % S::kSlots) * S::kBlk + (size_t)(f % S::kBlk)) * DP;
+    }
+};
+
+}  // namespace
+}  // namespace pardtw

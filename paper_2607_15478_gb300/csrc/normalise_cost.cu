@@ -17,12 +17,13 @@ int padded_dim(int D) {
     return 0;
 }
 
-// One thread per frame.  Frames of A beyond La (padding up to a multiple of
-// 32 rows) and feature slots beyond D are written as zeros.  Thread 0 also
-// clears the control words of the call.
+// One thread per frame.  A is written row-major (La_pad x dp), B
+// chunk-transposed (bt_index, Lb_pad frames).  Frames of A beyond La, frames
+// of B beyond Lb and feature slots beyond D are zero.  Thread 0 also clears
+// the control words of the call.
 __global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
-                            const float* __restrict__ B, int Lb, int D, int dp,
-                            float* __restrict__ Ahat, float* __restrict__ Bhat, DevCtl* ctl) {
+                            const float* __restrict__ B, int Lb, int Lb_pad, int D, int dp,
+                            float* __restrict__ Ahat, float* __restrict__ Bt, DevCtl* ctl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         ctl->status = 0;
@@ -30,17 +31,18 @@ __global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
         ctl->ticket = 0;
     }
     const float* src;
-    float* dst;
-    bool valid;
+    bool valid, is_a;
+    int k;
     if (t < La_pad) {
+        k = t;
         src = A + (size_t)t * D;
-        dst = Ahat + (size_t)t * dp;
         valid = t < La;
-    } else if (t < La_pad + Lb) {
-        const int k = t - La_pad;
+        is_a = true;
+    } else if (t < La_pad + Lb_pad) {
+        k = t - La_pad;
         src = B + (size_t)k * D;
-        dst = Bhat + (size_t)k * dp;
-        valid = true;
+        valid = k < Lb;
+        is_a = false;
     } else {
         return;
     }
@@ -51,15 +53,22 @@ __global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
             ss = fmaf(v, v, ss);
         }
     const float r = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
-    for (int d = 0; d < dp; ++d) dst[d] = (valid && d < D) ? src[d] * r : 0.f;
+    for (int d = 0; d < dp; ++d) {
+        const float v = (valid && d < D) ? src[d] * r : 0.f;
+        if (is_a)
+            Ahat[(size_t)k * dp + d] = v;
+        else
+            Bt[bt_index(k, d, dp)] = v;
+    }
 }
 
-cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb, int D,
-                             int dp, float* Ahat, float* Bhat, DevCtl* ctl, cudaStream_t s) {
-    const int n = La_pad + Lb;
+cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb,
+                             int Lb_pad, int D, int dp, float* Ahat, float* Bt, DevCtl* ctl,
+                             cudaStream_t s) {
+    const int n = La_pad + Lb_pad;
     const int threads = 256;
-    k_normalise<<<(n + threads - 1) / threads, threads, 0, s>>>(A, La, La_pad, B, Lb, D, dp,
-                                                                Ahat, Bhat, ctl);
+    k_normalise<<<(n + threads - 1) / threads, threads, 0, s>>>(A, La, La_pad, B, Lb, Lb_pad, D,
+                                                                dp, Ahat, Bt, ctl);
     return cudaGetLastError();
 }
 
@@ -67,7 +76,7 @@ cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B,
 // in feature order -- bit-identical to the cost the DP kernel uses.
 // Block: 256 threads = 8 rows x 32 column lanes; each lane writes 4 columns
 // of its row per pass.
-__global__ void k_cost(const float* __restrict__ Ahat, int La, const float* __restrict__ Bhat,
+__global__ void k_cost(const float* __restrict__ Ahat, int La, const float* __restrict__ Bt,
                        int Lb, int dp, float* __restrict__ C) {
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.y * 8 + (threadIdx.x >> 5); i < La; i += gridDim.y * 8) {
@@ -77,21 +86,20 @@ __global__ void k_cost(const float* __restrict__ Ahat, int La, const float* __re
             for (int q = 0; q < 4; ++q) {
                 const int j = j0 + 32 * q;
                 if (j >= Lb) break;
-                const float* b = Bhat + (size_t)j * dp;
                 float acc = 1.0f;
-                for (int d = 0; d < dp; ++d) acc = fmaf(-a[d], b[d], acc);
+                for (int d = 0; d < dp; ++d) acc = fmaf(-a[d], Bt[bt_index(j, d, dp)], acc);
                 C[(size_t)i * Lb + j] = acc;
             }
         }
     }
 }
 
-cudaError_t launch_cost(const float* Ahat, int La, const float* Bhat, int Lb, int dp, float* C,
+cudaError_t launch_cost(const float* Ahat, int La, const float* Bt, int Lb, int dp, float* C,
                         cudaStream_t s) {
     const int gx = (Lb + 127) / 128 < 64 ? (Lb + 127) / 128 : 64;
     const int gy = (La + 7) / 8 < 32768 ? (La + 7) / 8 : 32768;
     dim3 grid((unsigned)gx, (unsigned)gy);
-    k_cost<<<grid, 256, 0, s>>>(Ahat, La, Bhat, Lb, dp, C);
+    k_cost<<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C);
     return cudaGetLastError();
 }
 

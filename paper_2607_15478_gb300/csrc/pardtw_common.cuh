@@ -27,13 +27,15 @@ struct DevCtl {
 // Arguments of the column-sweep DP kernel.
 struct DpArgs {
     const float* Ahat;              // nstrips*30 x dp, row-normalised, rows >= La are zero
-    const float* Bhat;              // Lb x dp, row-normalised
+    const float* Bhat;              // row-normalised B, chunk-transposed (see bt_index)
     uint32_t* bp;                   // nstrips * nchunk * 32 words (strip, chunk, row in strip)
     unsigned long long* gborder;    // ngroups * Lb * 2 tagged values (group bottom rows)
     DevCtl* ctl;
     float* e_final;                 // shifted cumulative cost at (La-1, Lb-1)
     int La, Lb;
     int nstrips, nchunk, ngroups;
+    int rps;                        // rows of A per strip (warp)
+    int wpb;                        // backpointer words per (strip, 16 columns)
     float kcost;                    // 1 - cost_shift
     float mu;                       // cost_shift
     unsigned epoch;                 // call tag for global border entries
@@ -42,23 +44,44 @@ struct DpArgs {
 };
 
 // Backpointer word address of cell (i, j): strip-major, then 16-column chunk,
-// then row within the strip (32 words per strip and chunk, of which the
-// first 30 hold rows).  One warp store covers 32 consecutive words (128 B).
-__host__ __device__ inline size_t bp_word_index(int i, int j, int nchunk) {
-    const int strip = i / kRowsPerStrip;
-    return ((size_t)strip * (size_t)nchunk + (size_t)(j >> 4)) * 32u +
-           (size_t)(i - strip * kRowsPerStrip);
+// then row within the strip.  A strip of rps rows stores wpb >= rps words
+// per chunk (32 per warp and row of a lane: the ghost lane's words are
+// unused), so one warp store covers wpb consecutive words.
+__host__ __device__ inline size_t bp_word_index(int i, int j, int nchunk, int rps, int wpb) {
+    const int strip = i / rps;
+    return ((size_t)strip * (size_t)nchunk + (size_t)(j >> 4)) * (size_t)wpb +
+           (size_t)(i - strip * rps);
+}
+
+// Strip geometry of the DP kernels: R rows per lane.  R = 1: lanes 0..29
+// are rows, lanes 30, 31 carry the strip above (30 rows, 32 words).  R >= 2:
+// lanes 0..30 hold R rows each, lane 31 carries the strip above (31 R rows,
+// 32 R words).
+__host__ __device__ inline int strip_rows(int R) { return R == 1 ? 30 : 31 * R; }
+__host__ __device__ inline int strip_words(int R) { return 32 * R; }
+
+// Normalised frames of B are stored chunk-transposed: 16 consecutive frames
+// (one backpointer chunk) form a feature-major block of 16 * dp floats, so
+// value d of frame f sits at ((f / 16) * dp + d) * 16 + f % 16.  A partial
+// last chunk is zero-padded.  The DP kernel reads these blocks feature by
+// feature to spread the 16 cost computations of a chunk over its steps.
+__host__ __device__ inline size_t bt_index(int f, int d, int dp) {
+    return ((size_t)(f >> 4) * (size_t)dp + (size_t)d) * 16u + (size_t)(f & 15);
 }
 
 // Launchers (each returns a cudaError_t from the launch).
-cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb, int D,
-                             int dp, float* Ahat, float* Bhat, DevCtl* ctl, cudaStream_t s);
-cudaError_t launch_cost(const float* Ahat, int La, const float* Bhat, int Lb, int dp,
-                        float* C, cudaStream_t s);
-cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);
-cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, const DevCtl* ctl,
-                             const float* e_final, float mu, int32_t* path, int32_t* scratch,
-                             int* path_len, float* total, cudaStream_t s);
+cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb,
+                             int Lb_pad, int D, int dp, float* Ahat, float* Bt, DevCtl* ctl,
+                             cudaStream_t s);
+cudaError_t launch_cost(const float* Ahat, int La, const float* Bt, int Lb, int dp, float* C,
+                        cudaStream_t s);
+cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);           // R = 1
+cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
+// Rows per lane the fused DP supports for a padded dimension (0 = none).
+bool multirow_supported(int dp, int R);
+cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int rps, int wpb,
+                             const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
+                             int32_t* scratch, int* path_len, float* total, cudaStream_t s);
 
 // Padded feature width used by the kernels for a given D (0 = unsupported).
 int padded_dim(int D);
