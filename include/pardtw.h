@@ -53,6 +53,7 @@ extern "C" {
 #define DTW_ERR_CUDA 4         /* a CUDA runtime call failed */
 #define DTW_ERR_TIMEOUT 5      /* a bounded device-side wait expired (the result is void) */
 #define DTW_ERR_UNSUPPORTED 6  /* option or size outside what this build supports */
+#define DTW_ERR_SCRATCH_LIMIT 7 /* dtw_align_static: the problem needs more than its fixed scratch */
 
 /* ---- options -------------------------------------------------------------- */
 #define DTW_COST_FP32 0        /* cost from FP32 features with FP32 accumulation */
@@ -146,6 +147,36 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
                    const float* const* B, const int* Lb, int D, const dtw_options* opt,
                    int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
                    int* status);
+
+/* ---- alignment without device allocation ---------------------------------- */
+/* The paper has no counterpart of this entry point; it is a service of this
+ * library.  Some callers cannot allocate device memory while they align: a
+ * real-time loop (live score following) that must not block in the driver's
+ * allocator, or a process whose device memory is already reserved by
+ * another allocator (a framework's caching allocator, a plugin host with a
+ * fixed budget).  dtw_align_static computes exactly what dtw_align computes
+ * (same kernels, same result) but allocates nothing: all of its scratch
+ * lives in one fixed device array of dtw_static_scratch_bytes() bytes
+ * (64 MiB) that every GPU loading the library holds until the process exits.
+ *
+ *   A, B, path, path_len, total_cost : device pointers (total_cost may be
+ *       NULL); a host pointer is rejected with DTW_ERR_INVALID
+ *   cuda_stream : stream the work is ordered on (NULL = legacy default)
+ *   other arguments as in dtw_align; the call is asynchronous and reports
+ *       device-side failures through *path_len < 0
+ * Sizes whose scratch (backpointers La*Lb/4 bytes plus padding, border rows,
+ * normalised features) exceeds the array return DTW_ERR_SCRATCH_LIMIT before
+ * any work is queued; about 1.5e8 cells fit (e.g. 10000 x 15000 at D = 12).
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device, made with that device current); make that first call
+ * before any stream capture.  Every call shares the array and leaves its
+ * contents behind: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller. */
+int dtw_align_static(const float* A, int La, const float* B, int Lb, int D,
+                     const dtw_options* opt, void* cuda_stream, int32_t* path, int cap,
+                     int* path_len, float* total_cost);
+/* Size in bytes of the fixed scratch array used by dtw_align_static. */
+size_t dtw_static_scratch_bytes(void);
 
 /* ---- profiling ------------------------------------------------------------ */
 /* Device time in ms of the stages of the last dtw_align on this handle,

@@ -266,6 +266,7 @@ const char* dtw_status_string(int status) {
         case DTW_ERR_CUDA: return "CUDA runtime error";
         case DTW_ERR_TIMEOUT: return "bounded device wait expired";
         case DTW_ERR_UNSUPPORTED: return "unsupported option or size";
+        case DTW_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of dtw_align_static";
         default: return "unknown status";
     }
 }

@@ -26,12 +26,14 @@ DTW_ERR_OOM = 3
 DTW_ERR_CUDA = 4
 DTW_ERR_TIMEOUT = 5
 DTW_ERR_UNSUPPORTED = 6
+DTW_ERR_SCRATCH_LIMIT = 7
 DTW_COST_FP32 = 0
 
 # every entry point include/pardtw.h declares
 EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destroy",
            "dtw_set_stream", "dtw_workspace_size", "dtw_cost", "dtw_align", "dtw_align_many",
-           "dtw_enable_timing", "dtw_stage_times")
+           "dtw_enable_timing", "dtw_stage_times", "dtw_align_static",
+           "dtw_static_scratch_bytes")
 
 
 class PardtwError(RuntimeError):
@@ -76,8 +78,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                    vp, vp, vp]
     lib.dtw_enable_timing.argtypes = [vp, ci]
     lib.dtw_stage_times.argtypes = [vp, ctypes.POINTER(cf), ci]
+    lib.dtw_align_static.argtypes = [vp, ci, vp, ci, ci, ctypes.POINTER(Options), vp, vp, ci, vp,
+                                     vp]
+    lib.dtw_static_scratch_bytes.argtypes = []
+    lib.dtw_static_scratch_bytes.restype = ctypes.c_size_t
     for name in EXPORTS:
-        if name not in ("dtw_default_options", "dtw_status_string"):
+        if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes"):
             getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -179,6 +185,29 @@ def dtw_align_many(h: int, As: Sequence, Bs: Sequence, paths, path_off, path_len
         ctypes.byref(options) if options else None, paths.data_ptr(),
         ctypes.cast(off, ctypes.c_void_p), path_len.data_ptr(),
         cost.data_ptr() if cost is not None else None, status.data_ptr()), "dtw_align_many")
+
+
+def dtw_align_static(A, B, path, path_len, total=None, options: Options | None = None,
+                     stream=None) -> None:
+    """Exact DTW into caller device buffers without any device allocation.
+
+    For callers that cannot allocate device memory while they align (a
+    real-time loop that must not block in the allocator, or a process whose
+    device memory is reserved by another allocator).  The library keeps all
+    scratch in one fixed device array (``dtw_static_scratch_bytes()``); too
+    large a problem raises ``PardtwError`` with ``DTW_ERR_SCRATCH_LIMIT``.
+    All tensors must be on the device; calls overlapping on the GPU race.
+    """
+    A, B = _features(A), _features(B)
+    _check(load_library().dtw_align_static(
+        A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1],
+        ctypes.byref(options) if options else None, _stream_ptr(stream), path.data_ptr(),
+        path.shape[0], path_len.data_ptr(), total.data_ptr() if total is not None else None),
+        "dtw_align_static")
+
+
+def dtw_static_scratch_bytes() -> int:
+    return int(load_library().dtw_static_scratch_bytes())
 
 
 # ---- convenience wrapper --------------------------------------------------------------
