@@ -2,7 +2,7 @@
 //
 // Host-side work only: argument checks, the reachability test, workspace
 // management, pointer-kind detection, and the launch sequence
-//   normalise -> column-sweep DP (cost on the fly) -> backtrace
+//   normalise -> column-sweep DP (cost on the fly) -> band map -> backtrace
 // on the handle's stream.  Every step of the alignment runs in the kernels;
 // there is no CPU fallback.
 #include <cuda_runtime.h>
@@ -77,7 +77,7 @@ bool reachable(int La, int Lb) {
 
 struct Layout {
     int dp, R, rps, wpb, nstrips, nchunk, ngroups, La_pad, cap;
-    size_t off_ctl, off_ahat, off_bhat, off_bp, off_scratch, off_stage_a, off_stage_b,
+    size_t off_ctl, off_ahat, off_bhat, off_bp, off_bt, off_stage_a, off_stage_b,
         off_stage_path, total;
     size_t border_bytes;
 };
@@ -113,8 +113,8 @@ Layout make_layout(int La, int Lb, int D, int R) {
     o = align256(o + (size_t)L.nchunk * kColsPerWord * L.dp * sizeof(float));
     L.off_bp = o;
     o = align256(o + (size_t)L.nstrips * L.nchunk * L.wpb * sizeof(uint32_t));
-    L.off_scratch = o;
-    o = align256(o + (size_t)2 * L.cap * sizeof(int32_t));
+    L.off_bt = o;
+    o = align256(o + bandmap_scratch_bytes(La, Lb));
     L.off_stage_a = o;
     o = align256(o + (size_t)La * D * sizeof(float));
     L.off_stage_b = o;
@@ -188,7 +188,6 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     float* Ahat = reinterpret_cast<float*>(ws + L.off_ahat);
     float* Bhat = reinterpret_cast<float*>(ws + L.off_bhat);
     uint32_t* bp = reinterpret_cast<uint32_t*>(ws + L.off_bp);
-    int32_t* scratch = reinterpret_cast<int32_t*>(ws + L.off_scratch);
 
     const float* dA = A;
     const float* dB = B;
@@ -232,9 +231,8 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     else
         CU(launch_dp_multirow(a, L.dp, L.R, h->num_sms, s));
     if (h->timing) CU(cudaEventRecord(h->ev[2], s));
-    CU(launch_backtrace(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift, out_path,
-                        scratch,
-                        out_len, out_total, s));
+CU(launch_backtrace_bands(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift,
+                              out_path, out_len, out_total, ws + L.off_bt, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
         h->timed = true;

@@ -1,0 +1,340 @@
+// Parallel backtrace (Sec. II-D keeps the backtrace matrix and follows it
+// back from the end cell; Sec. VI-C notes that this stage is sequential).
+//
+// A serial walk costs one dependent memory access per path cell (~2e4 for
+// a 20000 x 25000 pair).  This file splits it:
+//
+//   1. k_bandmap: rows are cut into bands of 256 rows.  For every cell of
+//      a band, "entry" = the cell of the band above where the optimal path
+//      to this cell last sat before entering the band, encoded as
+//      2 * column + (1 if that cell is in the band above's last row, 0 if in
+//      its second-to-last; every step advances at most 2 rows).  It is
+//      propagated forward row by row from the step codes:
+//        entry(i, j) = entry(predecessor)       predecessor inside the band
+//                    = encode(predecessor)      predecessor in the band above
+//      All columns of a row are independent (the inputs are rows i-1, i-2),
+//      so bands and column segments run in parallel.  A segment recomputes
+//      2 * 256 columns to its left (dependencies move at most 2 columns
+//      left per row, so those halo values are exact when they are used).
+//      Only the entries of each band's last two rows are stored, and the
+//      end cell's entry.
+//   2. k_bt_chain (one thread): from the end cell, the entries give the
+//      path's last cell in each band, band by band up to band 0.
+//   3. k_bt_walk (one warp per band): each band's piece of the path is
+//      walked back from that cell to the band's top, in parallel.
+//   4. k_bt_emit: the pieces are concatenated in ascending order.
+//
+// Entry codes: -1 = the origin (0, 0); -2 = no path (unreachable cell).
+#include "pardtw_common.cuh"
+
+namespace pardtw {
+
+namespace {
+
+constexpr int kSegThreads = 512;
+constexpr int kSegCols = kSegThreads * kColsPerWord;  // 8192 columns computed per CTA
+constexpr int kNoPath = -2;
+constexpr int kOrigin = -1;
+
+
+}  // namespace
+
+// Grid: (column segments, bands).  Block: kSegThreads threads; thread t owns
+// the 16 columns s0 + 16 t .. + 15 of the segment's computed range, where
+// s0 = c0 - halo; the segment stores columns c0 .. c0 + width - 1 with
+// width = kSegCols - 2 * band (segments are width apart).  Two row buffers of entries per thread live in registers;
+// the two left-neighbour columns a thread needs come through shared memory.
+// One row of the band map for a thread's 16 columns.  kTop: the row is one
+// of the band's first two rows, whose predecessors may lie in the band above.
+template <bool kTop>
+__device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int Lb, int jb, int c0,
+                                            int width, int b, uint32_t word, int t,
+                                            int (*s_x)[kSegThreads][3], int* e1, int* e2,
+                                            int2* __restrict__ exits, int* __restrict__ end_entry) {
+    const int par = i & 1;
+    s_x[par][t][0] = e1[kColsPerWord - 2];
+    s_x[par][t][1] = e1[kColsPerWord - 1];
+    s_x[par][t][2] = e2[kColsPerWord - 1];
+    __syncthreads();
+    // (i-1, jb-2), (i-1, jb-1), (i-2, jb-1) from the left neighbour
+    const int l1m2 = t > 0 ? s_x[par][t - 1][0] : kNoPath;
+    const int l1m1 = t > 0 ? s_x[par][t - 1][1] : kNoPath;
+    const int l2m1 = t > 0 ? s_x[par][t - 1][2] : kNoPath;
+    int en[kColsPerWord];
+#pragma unroll
+    for (int q = 0; q < kColsPerWord; ++q) {
+        const uint32_t code = (word >> (2 * q)) & 3u;
+        int p11 = (q >= 1) ? e1[q - 1] : l1m1;                    // (i-1, j-1)
+        int p12 = (q >= 2) ? e1[q - 2] : (q == 1 ? l1m1 : l1m2);  // (i-1, j-2)
+        int p21 = (q >= 1) ? e2[q - 1] : l2m1;                    // (i-2, j-1)
+        if (kTop) {
+            // predecessors in the band above are named 2 * column + (1 if in
+            // its last row)
+            const int j = jb + q;
+            if (i == r0) {
+                p11 = (i >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
+                p12 = (i >= 1 && j >= 2) ? 2 * (j - 2) + 1 : kNoPath;
+                p21 = (i >= 2 && j >= 1) ? 2 * (j - 1) : kNoPath;
+            } else {  // i == r0 + 1: only (i-2, j-1) is above
+                p21 = (r0 >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
+            }
+        }
+        int v = code == 0u ? p11 : (code == 1u ? p12 : p21);
+        if (kTop && i == 0 && jb + q == 0) v = kOrigin;
+        en[q] = v;
+    }
+    // the band's last two rows are kept for the band below
+    if (i >= r1 - 2 && r1 < La) {
+        const int which = (i == r1 - 1) ? 1 : 0;
+#pragma unroll
+        for (int q = 0; q < kColsPerWord; ++q) {
+            const int j = jb + q;
+            if (j >= c0 && j < c0 + width && j < Lb)
+                reinterpret_cast<int*>(exits + (size_t)b * Lb + j)[which] = en[q];
+        }
+    }
+    if (i == La - 1) {
+        const int q = (Lb - 1) - jb;
+        if (q >= 0 && q < kColsPerWord && Lb - 1 >= c0 && Lb - 1 < c0 + width) {
+#pragma unroll
+            for (int u = 0; u < kColsPerWord; ++u)
+                if (u == q) *end_entry = en[u];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kColsPerWord; ++q) {
+        e2[q] = e1[q];
+        e1[q] = en[q];
+    }
+}
+
+constexpr int kRowsAhead = 8;  // backpointer rows loaded ahead of use
+
+__global__ void __launch_bounds__(kSegThreads) k_bandmap(const uint32_t* __restrict__ bp, int La,
+                                                         int Lb, int nchunk, int rps, int wpb,
+                                                         int band, int2* __restrict__ exits,
+                                                         int* __restrict__ end_entry) {
+    // left-neighbour exchange, double-buffered by row parity: columns 14, 15
+    // of row i-1 and column 15 of row i-2 of every thread
+    __shared__ int s_x[2][kSegThreads][3];
+    const int b = blockIdx.y;
+    const int r0 = b * band;
+    const int r1 = min(r0 + band, La);
+    const int width = kSegCols - 2 * band;
+    const int c0 = blockIdx.x * width;
+    const int halo = (c0 == 0) ? 0 : 2 * band;  // multiple of 16
+    const int s0 = c0 - halo;
+    const int t = threadIdx.x;
+    const int jb = s0 + kColsPerWord * t;  // first column of this thread
+    const bool have = jb < nchunk * kColsPerWord;
+    auto load = [&](int i) -> uint32_t {
+        return (have && i < r1) ? __ldg(bp + bp_word_index(i, jb, nchunk, rps, wpb)) : 0u;
+    };
+
+    int e1[kColsPerWord], e2[kColsPerWord];  // entries of rows i-1 and i-2
+#pragma unroll
+    for (int q = 0; q < kColsPerWord; ++q) e1[q] = e2[q] = kNoPath;
+
+    // the band's first two rows
+    const uint32_t top0 = load(r0), top1 = load(r0 + 1);
+    uint32_t wq[kRowsAhead];
+#pragma unroll
+    for (int u = 0; u < kRowsAhead; ++u) wq[u] = load(r0 + 2 + u);
+    bandmap_row<true>(r0, r0, r1, La, Lb, jb, c0, width, b, top0, t, s_x, e1, e2, exits,
+                      end_entry);
+    if (r0 + 1 < r1)
+        bandmap_row<true>(r0 + 1, r0, r1, La, Lb, jb, c0, width, b, top1, t, s_x, e1, e2, exits,
+                          end_entry);
+    // the rest, kRowsAhead at a time, loading the next group meanwhile
+    for (int i = r0 + 2; i < r1; i += kRowsAhead) {
+        uint32_t wn[kRowsAhead];
+#pragma unroll
+        for (int u = 0; u < kRowsAhead; ++u) wn[u] = load(i + kRowsAhead + u);
+#pragma unroll
+        for (int u = 0; u < kRowsAhead; ++u)
+            if (i + u < r1)
+                bandmap_row<false>(i + u, r0, r1, La, Lb, jb, c0, width, b, wq[u], t, s_x, e1, e2,
+                                   exits, end_entry);
+#pragma unroll
+        for (int u = 0; u < kRowsAhead; ++u) wq[u] = wn[u];
+    }
+}
+
+// One thread: the path's last cell in every band, from the end cell up.
+// cross[b] = (i, j) of that cell for b < last band; status on failure.
+__global__ void k_bt_chain(const int2* __restrict__ exits, const int* __restrict__ end_entry,
+                           int La, int Lb, int band, int nbands, int2* __restrict__ cross,
+                           DevCtl* ctl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (ctl->status != 0) return;
+    cross[nbands - 1] = make_int2(La - 1, Lb - 1);
+    int e = *end_entry;
+    for (int b = nbands - 1; b >= 1; --b) {
+        if (e < 0) {  // an entry must name a cell of the band above
+            atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
+            return;
+        }
+        const int r0 = b * band;
+        const int j = e >> 1;
+        const int i = (e & 1) ? r0 - 1 : r0 - 2;
+        if (i < (b - 1) * band || j < 0 || j >= Lb) {
+            atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
+            return;
+        }
+        cross[b - 1] = make_int2(i, j);
+        const int2 x = exits[(size_t)(b - 1) * Lb + j];
+        e = (i == r0 - 1) ? x.y : x.x;
+    }
+    if (e != kOrigin) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
+}
+
+// One warp per band: walk back from cross[b] while inside band b, writing
+// the cells (descending) into seg + b * band; count[b] = cells written.  The
+// warp holds the backpointer block (one strip of rps rows x 16 columns, wpb
+// words) that contains the current cell, lane l holding words l, l+32, ...;
+// a step reads its word with one shuffle, and a new block is one coalesced
+// load when the path leaves the current one.
+__global__ void k_bt_walk(const uint32_t* __restrict__ bp, int nchunk, int rps, int wpb,
+                          int band, int nbands, const int2* __restrict__ cross,
+                          int2* __restrict__ seg, int* __restrict__ count, DevCtl* ctl) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nbands) return;
+    if (ctl->status != 0) {
+        if (lane == 0) count[b] = 0;
+        return;
+    }
+    const int r0 = b * band;
+    int i = cross[b].x, j = cross[b].y;
+    int n = 0;
+    int2* out = seg + (size_t)b * band;
+    int blk = -1;      // (strip, chunk) block index held by the warp
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // words lane, lane+32, lane+64, lane+96
+    int bad = 0;
+    while (i >= r0) {
+        if (n >= band || j < 0) {
+            bad = 1;
+            break;
+        }
+        if (lane == 0) out[n] = make_int2(i, j);
+        ++n;
+        if (i == 0 && j == 0) break;
+        const int strip = i / rps, rr = i - strip * rps;
+        const int want = strip * nchunk + (j >> 4);
+        if (want != blk) {  // warp-uniform
+            blk = want;
+            const uint32_t* src = bp + (size_t)want * wpb;
+            w0 = lane < wpb ? __ldg(src + lane) : 0u;
+            w1 = lane + 32 < wpb ? __ldg(src + lane + 32) : 0u;
+            w2 = lane + 64 < wpb ? __ldg(src + lane + 64) : 0u;
+            w3 = lane + 96 < wpb ? __ldg(src + lane + 96) : 0u;
+        }
+        const int slot = rr >> 5;
+        const uint32_t mine = slot == 0 ? w0 : (slot == 1 ? w1 : (slot == 2 ? w2 : w3));
+        const uint32_t word = __shfl_sync(0xffffffffu, mine, rr & 31);
+        const int code = (int)((word >> (2 * (j & 15))) & 3u);
+        if (code == 0) {
+            i -= 1;
+            j -= 1;
+        } else if (code == 1) {
+            i -= 1;
+            j -= 2;
+        } else if (code == 2) {
+            i -= 2;
+            j -= 1;
+        } else {
+            bad = 1;
+            break;
+        }
+    }
+    // the walk must leave the band exactly at the path's cell of the band above
+    if (b > 0 && !bad && (i != cross[b - 1].x || j != cross[b - 1].y)) bad = 1;
+    if (lane == 0) {
+        if (bad) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
+        count[b] = n;
+    }
+}
+
+// One CTA: prefix sum of the counts, then the cells in ascending order.
+__global__ void k_bt_emit(const int2* __restrict__ seg, const int* __restrict__ count, int band,
+                          int nbands, int cap, const DevCtl* __restrict__ ctl,
+                          const float* __restrict__ e_final, float mu, int La, int Lb,
+                          int32_t* __restrict__ path, int* __restrict__ path_len,
+                          float* __restrict__ total) {
+    extern __shared__ int s_off[];  // nbands + 1
+    __shared__ int s_err;
+    if (threadIdx.x == 0) {
+        int err = ctl->status;
+        int acc = 0;
+        for (int b = 0; b < nbands; ++b) {
+            s_off[b] = acc;
+            acc += count[b];
+        }
+        s_off[nbands] = acc;
+        if (err == 0 && (acc < 1 || acc > cap)) err = DTW_ERR_CUDA;
+        s_err = err;
+        if (err != 0) {
+            *path_len = -err;
+            if (total) *total = NAN;
+        } else {
+            *path_len = acc;
+            if (total) *total = fmaf(mu, (float)(La + Lb - 2), *e_final);
+        }
+    }
+    __syncthreads();
+    if (s_err != 0) return;
+    // band b's cells are stored descending; they go to positions
+    // s_off[b] .. s_off[b+1]-1 reversed
+    for (int b = 0; b < nbands; ++b) {
+        const int n = count[b];
+        const int base = s_off[b];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int2 c = seg[(size_t)b * band + (n - 1 - k)];
+            path[2 * (base + k)] = c.x;
+            path[2 * (base + k) + 1] = c.y;
+        }
+    }
+}
+
+int bandmap_band_rows() { return 256; }
+
+size_t bandmap_scratch_bytes(int La, int Lb) {
+    const int band = bandmap_band_rows();
+    const int nbands = (La + band - 1) / band;
+    return (size_t)nbands * Lb * sizeof(int2)        // exits
+           + (size_t)nbands * sizeof(int2)            // cross
+           + (size_t)nbands * band * sizeof(int2)     // seg
+           + (size_t)nbands * sizeof(int) + 64;       // count, end entry
+}
+
+cudaError_t launch_backtrace_bands(const uint32_t* bp, int La, int Lb, int nchunk, int rps,
+                                   int wpb, DevCtl* ctl, const float* e_final, float mu,
+                                   int32_t* path, int* path_len, float* total, void* scratch,
+                                   cudaStream_t s) {
+    const int band = bandmap_band_rows();
+    const int nbands = (La + band - 1) / band;
+    char* p = static_cast<char*>(scratch);
+    int2* exits = reinterpret_cast<int2*>(p);
+    p += (size_t)nbands * Lb * sizeof(int2);
+    int2* cross = reinterpret_cast<int2*>(p);
+    p += (size_t)nbands * sizeof(int2);
+    int2* seg = reinterpret_cast<int2*>(p);
+    p += (size_t)nbands * band * sizeof(int2);
+    int* count = reinterpret_cast<int*>(p);
+    p += (size_t)nbands * sizeof(int);
+    int* end_entry = reinterpret_cast<int*>(p);
+
+    const int width = kSegCols - 2 * band;
+    dim3 grid((unsigned)((Lb + width - 1) / width), (unsigned)nbands);
+    k_bandmap<<<grid, kSegThreads, 0, s>>>(bp, La, Lb, nchunk, rps, wpb, band, exits, end_entry);
+    k_bt_chain<<<1, 32, 0, s>>>(exits, end_entry, La, Lb, band, nbands, cross, ctl);
+    k_bt_walk<<<(nbands + 3) / 4, 128, 0, s>>>(bp, nchunk, rps, wpb, band, nbands, cross, seg,
+                                               count, ctl);
+    const int cap = La < Lb ? La : Lb;
+    k_bt_emit<<<1, 256, (nbands + 1) * sizeof(int), s>>>(seg, count, band, nbands, cap, ctl,
+                                                         e_final, mu, La, Lb, path, path_len,
+                                                         total);
+    return cudaGetLastError();
+}
+
+}  // namespace pardtw

@@ -83,6 +83,14 @@ cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int
                              const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
                              int32_t* scratch, int* path_len, float* total, cudaStream_t s);
 
+// Parallel backtrace through per-band entry maps (bandmap.cu); scratch is
+// caller-provided device memory of bandmap_scratch_bytes(La, Lb) bytes.
+size_t bandmap_scratch_bytes(int La, int Lb);
+cudaError_t launch_backtrace_bands(const uint32_t* bp, int La, int Lb, int nchunk, int rps,
+                                   int wpb, DevCtl* ctl, const float* e_final, float mu,
+                                   int32_t* path, int* path_len, float* total, void* scratch,
+                                   cudaStream_t s);
+
 // Padded feature width used by the kernels for a given D (0 = unsupported).
 int padded_dim(int D);
 

@@ -56,7 +56,8 @@ def dev(x):
 
 SHAPES = [(1, 1), (2, 2), (2, 3), (3, 2), (5, 9), (31, 33), (32, 32), (33, 31), (33, 64),
           (64, 33), (100, 150), (127, 129), (128, 128), (129, 130), (130, 257), (257, 300),
-          (300, 257), (500, 400), (513, 1000), (1000, 513), (700, 900)]
+          (300, 257), (500, 400), (513, 1000), (1000, 513), (700, 900), (255, 500),
+          (256, 300), (257, 400), (384, 200), (1025, 900)]
 
 
 @pytest.mark.parametrize("La,Lb", SHAPES)
