@@ -2,8 +2,9 @@
 """Benchmark: exact DTW (ParDTW) throughput in GCUPS on GB300.
 
 One step = one exact alignment of the 20000x12 vs 25000x12 chroma-like pair
-(normalise + column-sweep DP with on-the-fly cosine cost + backtrace), with
-the inputs already resident in HBM.  GCUPS = La*Lb / t / 1e9.
+(normalise, column-sweep DP with on-the-fly cosine cost, band entry map,
+band chain, band walks, path emit: 6 kernels), with the inputs already
+resident in HBM.  GCUPS = La*Lb / t / 1e9.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,8 +34,15 @@ METRIC = "exact DTW GCUPS on 1 GB300; learned-band speedup at <=1-frame path err
 UNIT = "GCUPS"
 WORKLOAD = "pair-20000x12-vs-25000x12 chroma-like, warped (64 knots, tempo 0.7-1.4), cosine cost"
 L2_FLUSH_BYTES = 512 << 20
+KERNELS_PER_STEP = 6  # normalise, DP, band map, band chain, band walks, emit
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+
+
+def workload_name(La, Lb):
+    if (La, Lb) == (20000, 25000):
+        return WORKLOAD
+    return f"pair-{La}x12-vs-{Lb}x12 chroma-like, warped (64 knots, tempo 0.7-1.4), cosine cost"
 
 
 def dist_env():
@@ -68,7 +76,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -113,7 +121,7 @@ def dp_traffic_from_profiles():
     """DRAM bytes per DP launch from the committed ncu summary, if it matches the source."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "dp_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2607_15478_gb300", "csrc", "dp_kernel.cu")
+    src = os.path.join(ROOT, "paper_2607_15478_gb300", "csrc", "dp_multirow.cu")
     if not os.path.exists(p):
         return None
     try:
@@ -191,7 +199,7 @@ def run_ours(args):
         dist.barrier()
     from paper_2607_15478_gb300 import pardtw, synth
 
-    wp = synth.config_pair(1, pair=rank)
+    wp = synth.config_pair(1, pair=rank, La=args.La, Lb=args.Lb)
     La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
     cells = La * Lb
     stream = torch.cuda.Stream(device=dev)
@@ -290,20 +298,20 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "La": La, "Lb": Lb, "D": D,
+            "config": {"workload": workload_name(La, Lb), "La": La, "Lb": Lb, "D": D,
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": traffic,
-                         "kernel": "k_dp (column-sweep DP, cost on the fly)",
+                         "kernel": "k_dp_multirow (column-sweep DP, cost on the fly)",
                          "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{clock:.0f} MHz (sm_max_mhz, {src})"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -315,10 +323,13 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--La", type=int, default=None,
+                    help="override the pair's lengths (same recipe; for profiling smaller cases)")
+    ap.add_argument("--Lb", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
