@@ -74,11 +74,22 @@ typedef struct dtw_options {
      * never publishes its bottom border, so the group below it waits until
      * wait_limit and the call reports DTW_ERR_TIMEOUT. */
     int debug_skip_publish;
-    /* Rows of A each GPU lane sweeps (1, 2 or 4); 0 = chosen from La, D and
-     * the SM count.  Results do not depend on it (it only changes the work
-     * decomposition); D > 32 runs with 1. */
+    /* Rows of A each GPU lane sweeps (1, 2, 3 or 4); 0 = chosen from La, D
+     * and the SM count.  Results do not depend on it (it only changes the
+     * work decomposition); D > 32 runs with 1, and a value the chosen
+     * schedule does not support falls back to 1. */
     int rows_per_lane;
+    /* Division of labour of the DP for rows_per_lane >= 2: DTW_SCHEDULE_AUTO
+     * (0, the default: cost/DP warp pairs), DTW_SCHEDULE_FUSED (1: one warp
+     * per strip computes the costs and the recurrence; rows_per_lane 2 or 4)
+     * or DTW_SCHEDULE_SPLIT (2: a cost warp and a DP warp per strip;
+     * rows_per_lane 2, 3 or 4).  Results do not depend on it. */
+    int dp_schedule;
 } dtw_options;
+
+#define DTW_SCHEDULE_AUTO 0
+#define DTW_SCHEDULE_FUSED 1
+#define DTW_SCHEDULE_SPLIT 2
 
 /* Fill *opt with the defaults: FP32 cost, no shift, default wait limit,
  * no fault injection. */

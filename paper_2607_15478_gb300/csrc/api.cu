@@ -76,32 +76,57 @@ bool reachable(int La, int Lb) {
 }
 
 struct Layout {
+    DpPlan plan;
     int dp, R, rps, wpb, nstrips, nchunk, ngroups, La_pad, cap;
     size_t off_ctl, off_ahat, off_bhat, off_bp, off_bt, off_stage_a, off_stage_b,
         off_stage_path, total;
     size_t border_bytes;
 };
 
-// Rows per lane: the requested value if the fused DP supports it for this
-// dimension, else 2, or 4 when La leaves more than ~5 warps of 62 rows per SM.
-int choose_rows(int La, int dp, int requested, int num_sms) {
-    if (requested == 1) return 1;
-    if (requested == 2 || requested == 4) return multirow_supported(dp, requested) ? requested : 1;
-    if (!multirow_supported(dp, 2)) return 1;
-    const long long warps2 = (La + strip_rows(2) - 1) / strip_rows(2);
-    if (warps2 > 5LL * num_sms && multirow_supported(dp, 4)) return 4;
-    return 2;
+}  // namespace
+
+// The DP kernel for a problem.  Explicit requests are honoured where the
+// kernel supports them (else one row per lane); the default is the cost/DP
+// warp pair with 3 rows per lane for D <= 32, one row per lane above.
+DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
+    (void)La;
+    (void)num_sms;
+    const DpPlan one = {0, 1, kWarpsPerGroup};
+    const int req = o.rows_per_lane;
+    if (req == 1) return one;
+    if (o.dp_schedule == DTW_SCHEDULE_FUSED) {
+        const int R = req == 0 ? 2 : req;
+        if (multirow_supported(dp, R)) return {1, R, kWarpsPerGroup};
+        return one;
+    }
+    const int R = req == 0 ? 3 : req;
+    if (split_supported(dp, R)) return {2, R, kSplitStrips};
+    return one;
 }
 
-Layout make_layout(int La, int Lb, int D, int R) {
+cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
+                        cudaStream_t s) {
+    switch (plan.kind) {
+        case 0: return launch_dp(a, dp, num_sms, s);
+        case 1: return launch_dp_multirow(a, dp, plan.R, num_sms, s);
+        case 2: return launch_dp_split(a, dp, plan.R, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+namespace {
+
+Layout make_layout(int La, int Lb, int D, const DpPlan& plan) {
     Layout L;
+    L.plan = plan;
     L.dp = padded_dim(D);
+    const int R = plan.R;
     L.R = R;
     L.rps = strip_rows(R);
     L.wpb = strip_words(R);
     L.nstrips = (La + L.rps - 1) / L.rps;
     L.nchunk = (Lb + kColsPerWord - 1) / kColsPerWord;
-    L.ngroups = (L.nstrips + kWarpsPerGroup - 1) / kWarpsPerGroup;
+    L.ngroups = (L.nstrips + plan.spg - 1) / plan.spg;
     L.La_pad = L.nstrips * L.rps;
     L.cap = std::min(La, Lb);
     size_t o = 0;
@@ -170,6 +195,7 @@ dtw_options defaults() {
     o.wait_limit = 0;
     o.debug_skip_publish = -1;
     o.rows_per_lane = 0;
+    o.dp_schedule = DTW_SCHEDULE_AUTO;
     return o;
 }
 
@@ -177,8 +203,7 @@ dtw_options defaults() {
 // `out_len`, `out_total` are device pointers (out_total may be null).
 int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
                  const dtw_options& o, int32_t* out_path, int* out_len, float* out_total) {
-    const Layout L =
-        make_layout(La, Lb, D, choose_rows(La, padded_dim(D), o.rows_per_lane, h->num_sms));
+    const Layout L = make_layout(La, Lb, D, choose_plan(La, padded_dim(D), o, h->num_sms));
     int rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     cudaStream_t s = h->stream;
@@ -226,12 +251,9 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     if (a.epoch == 0) a.epoch = ++h->epoch;
     a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
     a.skip_publish = o.debug_skip_publish;
-    if (L.R == 1)
-        CU(launch_dp(a, L.dp, h->num_sms, s));
-    else
-        CU(launch_dp_multirow(a, L.dp, L.R, h->num_sms, s));
+    CU(launch_plan(L.plan, a, L.dp, h->num_sms, s));
     if (h->timing) CU(cudaEventRecord(h->ev[2], s));
-CU(launch_backtrace_bands(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift,
+    CU(launch_backtrace_bands(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift,
                               out_path, out_len, out_total, ws + L.off_bt, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
@@ -326,8 +348,11 @@ int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* by
     if (!bytes || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
     if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
     size_t most = 0;
-    for (int R : {1, 2, 4}) {
-        const Layout L = make_layout(La, Lb, D, R);
+    const DpPlan plans[] = {{0, 1, kWarpsPerGroup}, {1, 2, kWarpsPerGroup},
+                            {1, 4, kWarpsPerGroup}, {2, 2, kSplitStrips},
+                            {2, 3, kSplitStrips},   {2, 4, kSplitStrips}};
+    for (const DpPlan& plan : plans) {
+        const Layout L = make_layout(La, Lb, D, plan);
         most = std::max(most, L.total + L.border_bytes);
     }
     *bytes = most;
@@ -340,7 +365,7 @@ int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int 
     if (dp == 0) return DTW_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
-    const Layout L = make_layout(La, Lb, D, 1);
+    const Layout L = make_layout(La, Lb, D, DpPlan{0, 1, kWarpsPerGroup});
     const bool c_dev = is_device_ptr(C);
     const size_t cbytes = (size_t)La * Lb * sizeof(float);
     const size_t need = L.total + (c_dev ? 0 : align256(cbytes));
@@ -386,8 +411,7 @@ int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
 
-    const Layout L = make_layout(La, Lb, D, choose_rows(La, padded_dim(D), o.rows_per_lane,
-                                                        h->num_sms));
+    const Layout L = make_layout(La, Lb, D, choose_plan(La, padded_dim(D), o, h->num_sms));
     rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     const bool path_dev = is_device_ptr(path);

@@ -3,7 +3,7 @@
 // path; Sec. VI-C: this stage is sequential).
 //
 // One CTA.  Thread 0 walks from (La-1, Lb-1) to (0, 0), following the step
-// codes 0 = (1,1), 1 = (1,2), 2 = (2,1), and writes the cells into a scratch
+// of each cell's backpointer field (step_of_field), and writes the cells into a scratch
 // buffer from its end; then the whole CTA copies them in ascending order
 // into the caller's path buffer.  The walk is bounded by min(La, Lb) cells
 // and checks every index, so a damaged matrix yields an error, never an
@@ -35,19 +35,16 @@ __global__ void k_backtrace(const uint32_t* __restrict__ bp, int La, int Lb, int
                 ++n;
                 if (i == 0 && j == 0) break;
                 const uint32_t word = __ldg(bp + bp_word_index(i, j, nchunk, rps, wpb));
-                const int code = (int)((word >> (2 * (j & 15))) & 3u);
-                if (code == 0) {
+                const int step = step_of_field((word >> (2 * (j & 15))) & 3u);
+                if (step == 0) {
                     i -= 1;
                     j -= 1;
-                } else if (code == 1) {
+                } else if (step == 1) {
                     i -= 1;
                     j -= 2;
-                } else if (code == 2) {
+                } else {
                     i -= 2;
                     j -= 1;
-                } else {
-                    err = DTW_ERR_CUDA;
-                    break;
                 }
             }
         }

@@ -63,7 +63,7 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
     int en[kColsPerWord];
 #pragma unroll
     for (int q = 0; q < kColsPerWord; ++q) {
-        const uint32_t code = (word >> (2 * q)) & 3u;
+        const int step = step_of_field((word >> (2 * q)) & 3u);
         int p11 = (q >= 1) ? e1[q - 1] : l1m1;                    // (i-1, j-1)
         int p12 = (q >= 2) ? e1[q - 2] : (q == 1 ? l1m1 : l1m2);  // (i-1, j-2)
         int p21 = (q >= 1) ? e2[q - 1] : l2m1;                    // (i-2, j-1)
@@ -79,7 +79,7 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
                 p21 = (r0 >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
             }
         }
-        int v = code == 0u ? p11 : (code == 1u ? p12 : p21);
+        int v = step == 0 ? p11 : (step == 1 ? p12 : p21);
         if (kTop && i == 0 && jb + q == 0) v = kOrigin;
         en[q] = v;
     }
@@ -232,19 +232,16 @@ __global__ void k_bt_walk(const uint32_t* __restrict__ bp, int nchunk, int rps, 
         const int slot = rr >> 5;
         const uint32_t mine = slot == 0 ? w0 : (slot == 1 ? w1 : (slot == 2 ? w2 : w3));
         const uint32_t word = __shfl_sync(0xffffffffu, mine, rr & 31);
-        const int code = (int)((word >> (2 * (j & 15))) & 3u);
-        if (code == 0) {
+        const int step = step_of_field((word >> (2 * (j & 15))) & 3u);
+        if (step == 0) {
             i -= 1;
             j -= 1;
-        } else if (code == 1) {
+        } else if (step == 1) {
             i -= 1;
             j -= 2;
-        } else if (code == 2) {
+        } else {
             i -= 2;
             j -= 1;
-        } else {
-            bad = 1;
-            break;
         }
     }
     // the walk must leave the band exactly at the path's cell of the band above

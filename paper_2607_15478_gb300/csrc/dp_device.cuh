@@ -45,6 +45,11 @@ __device__ __forceinline__ void ldg2(const unsigned long long* p, unsigned long 
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p));
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p + 1));
 }
+__device__ __forceinline__ unsigned long long ldg1(const unsigned long long* p) {
+    unsigned long long a;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(a) : "l"(p));
+    return a;
+}
 __device__ __forceinline__ void stg1(unsigned long long* p, unsigned long long a) {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
@@ -183,6 +188,65 @@ __device__ __forceinline__ void tma_load(unsigned dst, const void* src, unsigned
         : "memory");
 }
 
+
+// Explicit shared-memory vector accesses (32-bit shared addresses).  Both
+// are compiler memory barriers, so they stay in program order with the
+// barrier waits and arrivals and with plain shared-memory accesses.
+__device__ __forceinline__ float4 lds128(unsigned addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts128(unsigned addr, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Non-blocking test of the same condition as mbar_try_wait (never suspends
+// the thread), for look-ahead checks placed between independent work.
+__device__ __forceinline__ int mbar_test_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return (int)done;
+}
+
+// mbarrier arrive (release at CTA scope) by the calling thread.
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Wait (warp-uniform) until the phase of parity `par` of `bar` has completed.
+// Bounded like every other wait: gives up when the call failed elsewhere or
+// the deadline passed (raising DTW_ERR_TIMEOUT with detail `where`).
+__device__ __noinline__ int mbar_wait_slow(unsigned bar, unsigned par, DevCtl* ctl,
+                                           long long timeout_ns, int where) {
+    const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+    for (int poll = 1;; ++poll) {
+        if (__all_sync(kFull, mbar_try_wait(bar, par))) return 1;
+        if ((poll & 63) == 0) {
+            if (__shfl_sync(kFull, read_status(ctl), 0) != 0) return 0;
+            const long long now = __shfl_sync(kFull, global_ns(), 0);
+            if (now - t0 > timeout_ns) {
+                if ((threadIdx.x & 31) == 0) raise_status(ctl, DTW_ERR_TIMEOUT, where);
+                return 0;
+            }
+        }
+    }
+}
+__device__ __forceinline__ int mbar_wait(unsigned bar, unsigned par, DevCtl* ctl,
+                                         long long timeout_ns, int where) {
+    if (__all_sync(kFull, mbar_try_wait(bar, par))) return 1;
+    return mbar_wait_slow(bar, par, ctl, timeout_ns, where);
+}
+
 template <int DP>
 struct BRing {
     using S = BStage<DP>;
@@ -252,6 +316,13 @@ struct BRing {
         }
         waited = issued;
     }
+    // Shared address of the 16 x DP feature-major values of chunk k.
+    __device__ __forceinline__ unsigned chunk_s(int k) const {
+        const int f = k * kColsPerWord;
+        const unsigned t = base + (unsigned)(f / S::kBlk);
+        return stage_s +
+               (unsigned)(((t % S::kSlots) * S::kBlk + (unsigned)(f % S::kBlk)) * DP * 4);
+    }
     // The 16 x DP feature-major values of chunk k (its block must be complete).
     __device__ __forceinline__ const float* chunk(int k) const {
         const int f = k * kColsPerWord;
@@ -259,6 +330,75 @@ struct BRing {
         return stage + ((size_t)(t % S::kSlots) * S::kBlk + (size_t)(f % S::kBlk)) * DP;
     }
 };
+
+// 1.0f if a == b, else 0.0f (one compare that yields a float).
+__device__ __forceinline__ float eq_as_float(float a, float b) {
+    float r;
+    asm("set.eq.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// One DP step of one column for the lane's R rows (no memory access, no
+// branch).  cur[k] = E[row k][j-1], prv[k] = E[row k][j-2], ylp = E[row
+// above][j-2]; g0, g1 = the ghost lane's border values of column j.  u is
+// the column's place in its 8-column sub-chunk: the cell's backpointer
+// field (see step_of_field) is added to fw[k] at bits 2u, 2u+1 by two FMAs
+// of exact powers of two, so the code costs two compares and no integer or
+// select instruction.
+template <int R>
+__device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, const float* w12,
+                                        bool ghost, float g0, float g1, bool origin_here,
+                                        float mu, float* cur, float* prv, float& ylp, float* fw,
+                                        float& o0, float& o1) {
+    const float y1 = __shfl_sync(kFull, cur[R - 1], srcA);  // E[i0-1][j-1]
+    const float y2 = __shfl_sync(kFull, cur[R - 2], srcA);  // E[i0-2][j-1]
+    const float bit0 = (float)(1u << (2 * u)), bit1 = (float)(2u << (2 * u));
+    float m[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float x1 = (k == 0) ? y1 : cur[k - 1];                       // E[i-1][j-1]
+        const float x2 = (k == 0) ? y2 : ((k == 1) ? y1 : cur[k - 2]);     // E[i-2][j-1]
+        float x1p = (k == 0) ? ylp : prv[k - 1];                           // E[i-1][j-2]
+        if (k == R - 2) x1p = ghost ? g0 : x1p;
+        if (k == R - 1) x1p = ghost ? g1 : x1p;
+        const float c0 = fmaf(2.0f, cost[k], x1);    // from (i-1, j-1)
+        const float c1 = fmaf(w12[k], cost[k], x1p);  // from (i-1, j-2)
+        const float c2 = fmaf(3.0f, cost[k], x2);    // from (i-2, j-1)
+        float mk = min3f(c0, c1, c2);
+        fw[k] = fmaf(eq_as_float(c0, mk), bit0, fw[k]);
+        fw[k] = fmaf(eq_as_float(c1, mk), bit1, fw[k]);
+        if (k == 0) mk = origin_here ? cost[0] + mu : mk;  // E[0][0] = C[0][0]
+        m[k] = mk;
+    }
+    o0 = m[R - 2];
+    o1 = m[R - 1];
+    ylp = y1;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        prv[k] = cur[k];
+        cur[k] = m[k];
+    }
+}
+
+// The 16 field bits a sub-chunk accumulated, as the low or high half of a
+// backpointer word (h = 0 or 1).
+__device__ __forceinline__ uint32_t field_bits(float fw, int h) {
+    return __float2uint_rz(fw) << (16 * h);
+}
+
+// A lane's R backpointer words of one chunk, at word offset lane * R of the
+// strip's block (vector stores where the offset is aligned for them).
+template <int R>
+__device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t* word) {
+    if constexpr (R == 2) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2(word[0], word[1]);
+    } else if constexpr (R == 4) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) dst[k] = word[k];
+    }
+}
 
 }  // namespace
 }  // namespace pardtw

@@ -70,18 +70,20 @@ __device__ __forceinline__ void next_cost_part(const float* nb, int uu, const fl
 // branch.  Lane sources srcA = lane-1, srcB = lane-2 (mod 32) give rows i-1
 // and i-2 of column j-1; x1p holds row i-1 of column j-2 (for a ghost lane:
 // its own border value of column j).
-__device__ __forceinline__ void dp_step(float cost, unsigned bit, int srcA, int srcB, float w12,
+__device__ __forceinline__ void dp_step(float cost, int u, int srcA, int srcB, float w12,
                                         bool origin_here, float mu, float& cur, float& x1p,
-                                        float& x1, uint32_t& word, float& out) {
+                                        float& x1, float& fw, float& out) {
     x1 = __shfl_sync(kFull, cur, srcA);        // E[i-1][j-1]
     const float x2 = __shfl_sync(kFull, cur, srcB);  // E[i-2][j-1]
     const float c0 = fmaf(2.0f, cost, x1);  // from (i-1, j-1)
     const float c1 = fmaf(w12, cost, x1p);  // from (i-1, j-2)
     const float c2 = fmaf(3.0f, cost, x2);  // from (i-2, j-1)
     float m = min3f(c0, c1, c2);
-    const uint32_t code = (c0 == m) ? 0u : ((c1 == m) ? 1u : 2u);
+    // backpointer field (step_of_field) at bits 2u, 2u+1 of the sub-chunk's
+    // accumulator
+    fw = fmaf(eq_as_float(c0, m), (float)(1u << (2 * u)), fw);
+    fw = fmaf(eq_as_float(c1, m), (float)(2u << (2 * u)), fw);
     m = origin_here ? cost + mu : m;  // E[0][0] = C[0][0]
-    word |= code << bit;
     out = m;
     cur = m;
 }
@@ -236,13 +238,14 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
             }
             x1p = ghost ? gv[0] : x1p;
             float o[kSub];  // rows 28, 29: own values of columns js .. js+kSub-1
+            float fw = 0.0f;  // backpointer fields of the sub-chunk, bits 2u, 2u+1
             if (nsteps == kSub) {
 #pragma unroll
                 for (int u = 0; u < kSub; ++u) {
                     const int uu = h * kSub + u;
                     next_cost_part<DP>(nb, uu, na, cn);
-                    dp_step(c[uu], 2u * uu, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
-                            mu, cur, x1p, x1, word, o[u]);
+                    dp_step(c[uu], u, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
+                            mu, cur, x1p, x1, fw, o[u]);
                     x1p = (u + 1 < kSub && ghost) ? gv[u + 1 < kSub ? u + 1 : 0] : x1;
                 }
             } else {
@@ -250,11 +253,12 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
                 for (int u = 0; u < kSub; ++u) {
                     const int uu = h * kSub + u;
                     if (u >= nsteps) break;
-                    dp_step(c[uu], 2u * uu, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
-                            mu, cur, x1p, x1, word, o[u]);
+                    dp_step(c[uu], u, srcA, srcB, w12, (uu == 0) && (j0 == 0) && is_origin,
+                            mu, cur, x1p, x1, fw, o[u]);
                     x1p = (u + 1 < kSub && ghost) ? gv[u + 1 < kSub ? u + 1 : 0] : x1;
                 }
             }
+            word |= field_bits(fw, h);
             if (to_ring) {
                 if (out_lane) {
                     float4* dst = reinterpret_cast<float4*>(&nextring[b][out_comp][0]);

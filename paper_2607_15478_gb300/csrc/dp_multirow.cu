@@ -49,52 +49,6 @@ __device__ __forceinline__ void next_cost_part(const float* nb, int u, const flo
     }
 }
 
-// One DP step of one column for the lane's R rows (no memory access, no
-// branch).  cur[k] = E[row k][j-1], prv[k] = E[row k][j-2], ylp = E[row
-// above][j-2]; g0, g1 = the ghost lane's border values of column j.
-template <int R>
-__device__ __forceinline__ void dp_step(const float* cost, unsigned bit, int srcA,
-                                        const float* w12, bool ghost, float g0, float g1,
-                                        bool origin_here, float mu, float* cur, float* prv,
-                                        float& ylp, uint32_t* word, float& o0, float& o1) {
-    const float y1 = __shfl_sync(kFull, cur[R - 1], srcA);  // E[i0-1][j-1]
-    const float y2 = __shfl_sync(kFull, cur[R - 2], srcA);  // E[i0-2][j-1]
-    float m[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const float x1 = (k == 0) ? y1 : cur[k - 1];                       // E[i-1][j-1]
-        const float x2 = (k == 0) ? y2 : ((k == 1) ? y1 : cur[k - 2]);     // E[i-2][j-1]
-        float x1p = (k == 0) ? ylp : prv[k - 1];                           // E[i-1][j-2]
-        if (k == R - 2) x1p = ghost ? g0 : x1p;
-        if (k == R - 1) x1p = ghost ? g1 : x1p;
-        const float c0 = fmaf(2.0f, cost[k], x1);    // from (i-1, j-1)
-        const float c1 = fmaf(w12[k], cost[k], x1p);  // from (i-1, j-2)
-        const float c2 = fmaf(3.0f, cost[k], x2);    // from (i-2, j-1)
-        float mk = min3f(c0, c1, c2);
-        const uint32_t code = (c0 == mk) ? 0u : ((c1 == mk) ? 1u : 2u);
-        if (k == 0) mk = origin_here ? cost[0] + mu : mk;  // E[0][0] = C[0][0]
-        word[k] |= code << bit;
-        m[k] = mk;
-    }
-    o0 = m[R - 2];
-    o1 = m[R - 1];
-    ylp = y1;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        prv[k] = cur[k];
-        cur[k] = m[k];
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void store_words(uint32_t* dst, const uint32_t* word) {
-    if constexpr (R == 2) {
-        *reinterpret_cast<uint2*>(dst) = make_uint2(word[0], word[1]);
-    } else {
-        *reinterpret_cast<uint4*>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
-    }
-}
-
 template <int DP, int R, int NW>
 __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lane,
                                           float (*ring)[kRingBlk][2][kSub], int* prod, int* cons,
@@ -253,6 +207,9 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
                 gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
             }
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
+            float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
+#pragma unroll
+            for (int k = 0; k < R; ++k) fw[k] = 0.0f;
             if (nsteps == kSub) {
 #pragma unroll
                 for (int u = 0; u < kSub; ++u) {
@@ -260,9 +217,9 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R>(cu, 2u * (h * kSub + u), srcA, w12, ghost, gv0[u], gv1[u],
+                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
                                (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
-                               ylp, word, o0[u], o1[u]);
+                               ylp, fw, o0[u], o1[u]);
                 }
             } else {
 #pragma unroll
@@ -271,11 +228,13 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R>(cu, 2u * (h * kSub + u), srcA, w12, ghost, gv0[u], gv1[u],
+                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
                                (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
-                               ylp, word, o0[u], o1[u]);
+                               ylp, fw, o0[u], o1[u]);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], h);
             if (lane == kOutLane) {
                 if (to_ring) {
                     float4* d0 = reinterpret_cast<float4*>(&nextring[b][0][0]);

@@ -1,0 +1,585 @@
+// Exact DTW dynamic programming, warp-specialised: every strip of A has a
+// DP warp and a cost warp, and every CTA of NS strips a reader and a writer
+// warp for the border it shares with the neighbouring CTAs.  Same
+// recurrence, step set, weights and tie order as the other DP kernels
+// (Sec. V, Sec. II-D); only the division of labour differs.
+//
+//   - The strip geometry is that of the multi-row kernel: 31 R rows, lane t
+//     (0..30) of the DP warp holds rows R t .. R t + R - 1 of the strip,
+//     lane 31 is the ghost lane that carries the two bottom rows of the strip
+//     above (cost 1e30, weight 0 on the (1,2) candidate fed the border value).
+//   - The cost warp of the strip computes C' = (1 - mu) - a^_i . b^_j for the
+//     same rows, 8 columns at a time (one FMA per feature, in feature order,
+//     so the values are bit-identical to the other kernels'), reading the
+//     frames of B from its TMA-fed ring, and hands them to the DP warp
+//     through a ring of kCostSlots sub-chunks in shared memory with one
+//     full and one empty mbarrier per slot.  The DP warp loads the costs of
+//     the next sub-chunk half-way through the current one.
+//   - The DP warp runs only the recurrence: per column two shuffles, three
+//     FMAs, a three-way minimum and two compares per cell.
+//   - Every DP warp takes its top border from a ring of kRingBlk sub-chunks
+//     in shared memory and writes its two bottom rows into the next ring,
+//     with a full and an empty mbarrier per block.  The first strip's ring
+//     is filled by the reader warp from the global border that the CTA
+//     above publishes; the last strip's ring is drained by the writer warp
+//     into this CTA's global border.  The L2 round trips of that exchange
+//     thus never sit in a DP warp, and all DP warps do the same work per
+//     sub-chunk (in a chain of strips the slowest one sets the pace).
+//   - Every wait is bounded (DTW_ERR_TIMEOUT) and gives up when the call has
+//     failed elsewhere.
+#include "dp_device.cuh"
+
+namespace pardtw {
+namespace {
+
+constexpr int kGhostLane = 31;
+constexpr int kOutLane = 30;    // holds the strip's two bottom rows
+constexpr int kCostSlots = 4;   // sub-chunks of costs in flight per strip
+
+// One slot holds the 8 costs of each of a lane's R rows: float4 q of lane l
+// (q = 2 k + half) at [q][l], so a warp's 16-byte accesses are contiguous.
+template <int R>
+struct CostRing {
+    static constexpr int kF4 = 2 * R;
+    static constexpr int kSlotBytes = kF4 * kWarp * 16;
+    static constexpr int kBytes = kCostSlots * kSlotBytes;
+};
+
+template <int DP, int R>
+struct SplitSmem {
+    // per strip slot: the cost warp's B stage, then the cost ring
+    static constexpr int kStripBytes = BStage<DP>::kWarpBytes + CostRing<R>::kBytes;
+};
+
+// Barrier `slot` of an array of 8-byte mbarriers, and the phase parity a
+// waiter for the t-th (lifetime) use of a ring of n slots expects.
+__device__ __forceinline__ unsigned bar_at(unsigned base, unsigned slot) { return base + 8 * slot; }
+__device__ __forceinline__ unsigned use_parity(unsigned t, unsigned n) { return (t / n) & 1u; }
+
+// Cost warp of `strip`: all sub-chunks of the sweep, in order.
+template <int DP, int R>
+__device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, unsigned cring,
+                                         unsigned cfull, unsigned cempty, unsigned csub,
+                                         BRing<DP>& br) {
+    using S = BStage<DP>;
+    using CR = CostRing<R>;
+    constexpr int kRows = 31 * R;
+    constexpr int kFG = 4;            // features per group of loads
+    constexpr int kNG = DP / kFG;     // DP is a multiple of 4
+    const bool ghost = lane == kGhostLane;
+    const int i0 = strip * kRows + lane * R;
+    float na[R][DP];  // -a^_i of the lane's rows (0 in the ghost lane)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4* s = reinterpret_cast<const float4*>(p.Ahat + (size_t)(i0 + k) * DP);
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+            const float4 v = ghost ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(s + q);
+            na[k][4 * q] = -v.x;
+            na[k][4 * q + 1] = -v.y;
+            na[k][4 * q + 2] = -v.z;
+            na[k][4 * q + 3] = -v.w;
+        }
+    }
+    const float kc = ghost ? kGhostCost : p.kcost;
+    const int Lb = p.Lb;
+    const int Lb_pad = p.nchunk * kColsPerWord;
+    const int nsub = (Lb + kSub - 1) / kSub;
+    br.base += (unsigned)br.nblk;
+    br.nblk = (Lb_pad + S::kBlk - 1) / S::kBlk;
+    br.issued = 0;
+    br.waited = 0;
+    br.top_up(0, p.Bhat, Lb_pad, lane);
+    for (int n = 0; n < nsub; ++n) {
+        const int js = n * kSub;
+        if (js % S::kBlk == 0) {
+            const int q = js / S::kBlk;
+            if (!br.wait(q, p.ctl, p.timeout_ns)) break;
+            br.top_up(q, p.Bhat, Lb_pad, lane);
+        }
+        const unsigned t = csub + (unsigned)n;
+        const unsigned slot = t % kCostSlots;
+        // the DP warp has read this slot's previous contents
+        if (!mbar_wait(bar_at(cempty, slot), use_parity(t, kCostSlots) ^ 1u, p.ctl, p.timeout_ns,
+                       6))
+            break;
+        // the 8 frames of the sub-chunk, feature-major (16 floats per feature)
+        const unsigned nb = br.chunk_s(js >> 4) + (unsigned)(js & kSub) * 4u;
+        float c[R][kSub];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int f = 0; f < kSub; ++f) c[k][f] = kc;
+        // loads of the next feature group are issued before the FMAs of the
+        // current one
+        float4 bv[2][2 * kFG];
+#pragma unroll
+        for (int e = 0; e < kFG; ++e) {
+            bv[0][2 * e] = lds128(nb + (unsigned)(e * kColsPerWord) * 4u);
+            bv[0][2 * e + 1] = lds128(nb + (unsigned)(e * kColsPerWord + 4) * 4u);
+        }
+#pragma unroll
+        for (int gi = 0; gi < kNG; ++gi) {
+            if (gi + 1 < kNG) {
+#pragma unroll
+                for (int e = 0; e < kFG; ++e) {
+                    const int d = (gi + 1) * kFG + e;
+                    bv[(gi + 1) & 1][2 * e] = lds128(nb + (unsigned)(d * kColsPerWord) * 4u);
+                    bv[(gi + 1) & 1][2 * e + 1] =
+                        lds128(nb + (unsigned)(d * kColsPerWord + 4) * 4u);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < kFG; ++e) {
+                const int d = gi * kFG + e;
+                const float4 b0 = bv[gi & 1][2 * e], b1 = bv[gi & 1][2 * e + 1];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    c[k][0] = fmaf(na[k][d], b0.x, c[k][0]);
+                    c[k][1] = fmaf(na[k][d], b0.y, c[k][1]);
+                    c[k][2] = fmaf(na[k][d], b0.z, c[k][2]);
+                    c[k][3] = fmaf(na[k][d], b0.w, c[k][3]);
+                    c[k][4] = fmaf(na[k][d], b1.x, c[k][4]);
+                    c[k][5] = fmaf(na[k][d], b1.y, c[k][5]);
+                    c[k][6] = fmaf(na[k][d], b1.z, c[k][6]);
+                    c[k][7] = fmaf(na[k][d], b1.w, c[k][7]);
+                }
+            }
+        }
+        const unsigned dst = cring + slot * CR::kSlotBytes + (unsigned)lane * 16u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            sts128(dst + (unsigned)(2 * k) * (kWarp * 16),
+                   make_float4(c[k][0], c[k][1], c[k][2], c[k][3]));
+            sts128(dst + (unsigned)(2 * k + 1) * (kWarp * 16),
+                   make_float4(c[k][4], c[k][5], c[k][6], c[k][7]));
+        }
+        mbar_arrive(bar_at(cfull, slot));
+    }
+    br.drain();
+}
+
+// The costs of lifetime sub-chunk t (its slot must be full) into c.
+template <int R>
+__device__ __forceinline__ void load_costs(unsigned cring, unsigned t, int lane,
+                                           float (*c)[kSub]) {
+    using CR = CostRing<R>;
+    const unsigned src = cring + (t % kCostSlots) * CR::kSlotBytes + (unsigned)lane * 16u;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4 v0 = lds128(src + (unsigned)(2 * k) * (kWarp * 16));
+        const float4 v1 = lds128(src + (unsigned)(2 * k + 1) * (kWarp * 16));
+        c[k][0] = v0.x;
+        c[k][1] = v0.y;
+        c[k][2] = v0.z;
+        c[k][3] = v0.w;
+        c[k][4] = v1.x;
+        c[k][5] = v1.y;
+        c[k][6] = v1.z;
+        c[k][7] = v1.w;
+    }
+}
+
+// Which rings of a CTA a strip group uses: ring w < NS feeds DP slot w (ring
+// 0 from the reader warp, which has nothing to read in group 0; ring w >= 1
+// from DP slot w-1, when strip w exists); ring NS takes the last DP slot's
+// bottom rows to the writer warp, when a group below needs them.  Producer
+// and consumer of a ring count its uses (in sub-chunks) the same way, which
+// keeps every barrier's phase in step across groups.
+struct GroupRoles {
+    int g, nstrips_here;
+    bool reader, writer;
+};
+template <int NS>
+__device__ __forceinline__ GroupRoles group_roles(const DpArgs& p, int g) {
+    GroupRoles r;
+    r.g = g;
+    r.nstrips_here = min(NS, p.nstrips - g * NS);
+    r.reader = g > 0;
+    r.writer = (g + 1 < p.ngroups) && (g != p.skip_publish);
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ bool ring_used(const GroupRoles& r, int w) {
+    if (w == 0) return r.reader;
+    if (w < NS) return w < r.nstrips_here;
+    return r.writer;
+}
+
+// DP warp of `strip` (slot w of group g).  ring: the NS + 1 border rings;
+// bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
+// sub-chunk counts of the input and output rings at the start of this
+// group; csub: that of the cost ring.
+template <int R, int NS>
+__device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
+                                       int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
+                                       unsigned bempty, unsigned rin, unsigned rout,
+                                       unsigned cring, unsigned cfull, unsigned cempty,
+                                       unsigned csub) {
+    constexpr int kRows = 31 * R;
+    const bool ghost = lane == kGhostLane;
+    const int i0 = strip * kRows + lane * R;
+    const int Lb = p.Lb;
+    const bool from_ring = ring_used<NS>(gr, w);
+    const bool to_ring = ring_used<NS>(gr, w + 1);
+    float (*myring)[2][kSub] = ring[w];
+    float (*nextring)[2][kSub] = ring[w + 1];
+    const unsigned bfull_in = bfull + 8 * kRingBlk * w;
+    const unsigned bempty_in = bempty + 8 * kRingBlk * w;
+    const unsigned bfull_out = bfull + 8 * kRingBlk * (w + 1);
+    const unsigned bempty_out = bempty + 8 * kRingBlk * (w + 1);
+    const float mu = p.mu;
+    float w12[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) w12[k] = (ghost && k >= R - 2) ? 0.0f : 3.0f;
+    const int srcA = (lane + 31) & 31;
+    const bool is_origin = (i0 == 0) && !ghost;
+
+    // costs of sub-chunk 0
+    float c[R][kSub];
+    if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
+                   p.timeout_ns, 7))
+        return;
+    load_costs<R>(cring, csub, lane, c);
+    mbar_arrive(bar_at(cempty, csub % kCostSlots));
+
+    float cur[R], prv[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) cur[k] = prv[k] = INFINITY;
+    float ylp = INFINITY;
+    int status_seen = 0;  // loaded one chunk ahead of its test
+    for (int j0 = 0; j0 < Lb; j0 += kColsPerWord) {
+        if (__shfl_sync(kFull, status_seen, 0) != 0) return;
+        status_seen = read_status(p.ctl);
+        uint32_t word[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) word[k] = 0;
+#pragma unroll
+        for (int h = 0; h < kColsPerWord / kSub; ++h) {
+            const int js = j0 + h * kSub;
+            if (js >= Lb) break;
+            const int n = js / kSub;
+            const int nsteps = min(kSub, Lb - js);
+            const unsigned ti = rin + (unsigned)n, to = rout + (unsigned)n;
+            const unsigned t = csub + (unsigned)n;
+
+            // border rows top-2, top-1 of columns js .. js+7 (the group's top
+            // border is +inf in group 0)
+            if (from_ring && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk),
+                                        p.ctl, p.timeout_ns, 1))
+                return;
+            float gv0[kSub], gv1[kSub];
+            {
+                const unsigned s0 = smem_u32(&myring[from_ring ? ti % kRingBlk : 0][0][0]);
+                const float4 a0 = lds128(s0), a1 = lds128(s0 + 16);
+                const float4 b0 = lds128(s0 + 32), b1 = lds128(s0 + 48);
+                gv0[0] = a0.x; gv0[1] = a0.y; gv0[2] = a0.z; gv0[3] = a0.w;
+                gv0[4] = a1.x; gv0[5] = a1.y; gv0[6] = a1.z; gv0[7] = a1.w;
+                gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
+                gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
+            }
+            if (from_ring) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+            // the output block must have been read below
+            if (to_ring && !mbar_wait(bar_at(bempty_out, to % kRingBlk),
+                                      use_parity(to, kRingBlk) ^ 1u, p.ctl, p.timeout_ns, 2))
+                return;
+
+            float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
+            float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
+#pragma unroll
+            for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+            const bool has_next = js + kSub < Lb;
+            float cn[R][kSub];
+            if (nsteps == kSub) {
+                unsigned ready = 1;
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    // the next sub-chunk's costs: test at step 2, load at step 4
+                    if (u == 2 && has_next)
+                        ready = mbar_test_wait(bar_at(cfull, (t + 1) % kCostSlots),
+                                               use_parity(t + 1, kCostSlots));
+                    if (u == 4 && has_next) {
+                        if (!__all_sync(kFull, ready) &&
+                            !mbar_wait_slow(bar_at(cfull, (t + 1) % kCostSlots),
+                                            use_parity(t + 1, kCostSlots), p.ctl, p.timeout_ns,
+                                            7))
+                            return;
+                        load_costs<R>(cring, t + 1, lane, cn);
+                        mbar_arrive(bar_at(cempty, (t + 1) % kCostSlots));
+                    }
+                    float cu[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                               (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
+                               ylp, fw, o0[u], o1[u]);
+                }
+            } else {
+                // the last, partial sub-chunk (has_next is false)
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    if (u >= nsteps) break;
+                    float cu[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                               (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
+                               ylp, fw, o0[u], o1[u]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], h);
+            if (to_ring && lane == kOutLane) {
+                const unsigned d0 = smem_u32(&nextring[to % kRingBlk][0][0]);
+                sts128(d0, make_float4(o0[0], o0[1], o0[2], o0[3]));
+                sts128(d0 + 16, make_float4(o0[4], o0[5], o0[6], o0[7]));
+                sts128(d0 + 32, make_float4(o1[0], o1[1], o1[2], o1[3]));
+                sts128(d0 + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
+                mbar_arrive(bar_at(bfull_out, to % kRingBlk));
+            }
+            if (has_next) {
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+#pragma unroll
+                    for (int f = 0; f < kSub; ++f) c[k][f] = cn[k][f];
+            }
+        }
+        store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
+                           (size_t)lane * R,
+                       word);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (!ghost && i0 + k == p.La - 1) *p.e_final = cur[k];
+}
+
+// Reader warp (groups g > 0): the bottom rows of group g-1 from the global
+// border into ring 0.  Lane v < 16 carries value v of every sub-chunk
+// (column v % 8, row v / 8); loads run kAheadSub sub-chunks ahead, and a
+// value whose tag is not yet this call's is re-polled (bounded).
+constexpr int kAheadSub = 4;
+__device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, float (*ring0)[2][kSub],
+                                           unsigned bfull0, unsigned bempty0, unsigned rbase) {
+    const int Lb = p.Lb;
+    const int nsub = (Lb + kSub - 1) / kSub;
+    const unsigned long long* gin = p.gborder + (size_t)(g - 1) * Lb * 2;
+    const unsigned epoch = p.epoch;
+    const bool act_lane = lane < 2 * kSub;
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    unsigned long long pend[kAheadSub];
+#pragma unroll
+    for (int q = 0; q < kAheadSub; ++q) {
+        const int col = q * kSub + cofs;
+        pend[q] = (act_lane && col < Lb) ? ldg1(gin + (size_t)col * 2 + row) : 0ull;
+    }
+    for (int n0 = 0; n0 < nsub; n0 += kAheadSub) {
+#pragma unroll
+        for (int q = 0; q < kAheadSub; ++q) {
+            const int n = n0 + q;
+            if (n >= nsub) break;
+            const int col = n * kSub + cofs;
+            const bool act = act_lane && col < Lb;
+            int ok = !act || tag_of(pend[q]) == epoch;
+            if (!__all_sync(kFull, ok)) {
+                // each poll is a round trip to L2; status and deadline every 16 polls
+                const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+                for (int poll = 1;; ++poll) {
+                    if (!ok) {
+                        pend[q] = ldg1(gin + (size_t)col * 2 + row);
+                        ok = tag_of(pend[q]) == epoch;
+                    }
+                    if (__all_sync(kFull, ok)) break;
+                    if ((poll & 15) == 0) {
+                        if (__shfl_sync(kFull, read_status(p.ctl), 0) != 0) return;
+                        const long long now = __shfl_sync(kFull, global_ns(), 0);
+                        if (now - t0 > p.timeout_ns) {
+                            if (lane == 0) raise_status(p.ctl, DTW_ERR_TIMEOUT, 3);
+                            return;
+                        }
+                    }
+                }
+            }
+            const unsigned t = rbase + (unsigned)n;
+            if (!mbar_wait(bar_at(bempty0, t % kRingBlk), use_parity(t, kRingBlk) ^ 1u, p.ctl,
+                           p.timeout_ns, 8))
+                return;
+            if (act) ring0[t % kRingBlk][row][cofs] = val_of(pend[q]);
+            mbar_arrive(bar_at(bfull0, t % kRingBlk));
+            const int ncol = col + kAheadSub * kSub;
+            if (act_lane && ncol < Lb) pend[q] = ldg1(gin + (size_t)ncol * 2 + row);
+        }
+    }
+}
+
+// Writer warp: the last DP slot's bottom rows from ring NS to the global
+// border of group g, as (value, epoch) words; lanes 0..15 store one
+// coalesced 128-byte line per sub-chunk.
+__device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
+                                           float (*ringo)[2][kSub], unsigned bfullo,
+                                           unsigned bemptyo, unsigned rbase) {
+    const int Lb = p.Lb;
+    const int nsub = (Lb + kSub - 1) / kSub;
+    unsigned long long* gout = p.gborder + (size_t)g * Lb * 2;
+    const unsigned epoch = p.epoch;
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    for (int n = 0; n < nsub; ++n) {
+        const unsigned t = rbase + (unsigned)n;
+        if (!mbar_wait(bar_at(bfullo, t % kRingBlk), use_parity(t, kRingBlk), p.ctl, p.timeout_ns,
+                       9))
+            return;
+        const float v = ringo[t % kRingBlk][row][cofs];
+        mbar_arrive(bar_at(bemptyo, t % kRingBlk));
+        const int col = n * kSub + cofs;
+        if (lane < 2 * kSub && col < Lb) stg1(gout + (size_t)col * 2 + row, pack(v, epoch));
+    }
+}
+
+// NS strips per CTA.  Warps 0..NS-1: the strips' cost warps; NS..2NS-1:
+// their DP warps; 2NS: the reader; 2NS+1: the writer.  Warp w runs on SM
+// sub-partition w % 4, so for NS = 2 each DP warp has a sub-partition of its
+// own and the helpers share those of the cost warps.  Persistent: a CTA
+// takes strip groups from the ticket counter until none are left, so a
+// group only ever waits on groups that started earlier.
+template <int DP, int R, int NS>
+__global__ void __launch_bounds__((2 * NS + 2) * 32, 1) k_dp_split(const DpArgs p) {
+    using S = BStage<DP>;
+    using M = SplitSmem<DP, R>;
+    __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
+    __shared__ __align__(8) unsigned long long bbar[NS][S::kSlots];
+    __shared__ __align__(8) unsigned long long cfull[NS][kCostSlots];
+    __shared__ __align__(8) unsigned long long cempty[NS][kCostSlots];
+    __shared__ __align__(8) unsigned long long bfull[NS + 1][kRingBlk];
+    __shared__ __align__(8) unsigned long long bempty[NS + 1][kRingBlk];
+    __shared__ int s_group;
+    extern __shared__ __align__(128) unsigned char dyn[];  // NS * M::kStripBytes
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
+    const int w = role == 0 ? wid : (role == 1 ? wid - NS : 0);  // strip slot
+    unsigned char* mine = dyn + (size_t)w * M::kStripBytes;
+    const unsigned cring_s = smem_u32(mine + S::kWarpBytes);
+    const unsigned cfull_s = smem_u32(&cfull[w][0]);
+    const unsigned cempty_s = smem_u32(&cempty[w][0]);
+
+    BRing<DP> br;
+    br.stage = reinterpret_cast<const float*>(mine);
+    br.stage_s = smem_u32(mine);
+    br.bar_s = smem_u32(&bbar[w][0]);
+    br.base = 0;
+    br.nblk = 0;
+    br.issued = br.waited = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            for (int k = 0; k < S::kSlots; ++k) mbar_init(smem_u32(&bbar[s][k]), 1);
+            for (int k = 0; k < kCostSlots; ++k) {
+                mbar_init(smem_u32(&cfull[s][k]), kWarp);   // the cost warp's lanes
+                mbar_init(smem_u32(&cempty[s][k]), kWarp);  // the DP warp's lanes
+            }
+        }
+        for (int s = 0; s <= NS; ++s)
+            for (int k = 0; k < kRingBlk; ++k) {
+                // ring 0 is filled by the reader's lanes, the others by lane 30
+                // of the DP warp above; every ring is emptied by a whole warp
+                mbar_init(smem_u32(&bfull[s][k]), s == 0 ? kWarp : 1);
+                mbar_init(smem_u32(&bempty[s][k]), kWarp);
+            }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // Lifetime sub-chunk counts of the cost rings and the border rings.
+    unsigned csub[NS], rsub[NS + 1];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) csub[s] = 0;
+#pragma unroll
+    for (int s = 0; s <= NS; ++s) rsub[s] = 0;
+    const unsigned nsub = (unsigned)((p.Lb + kSub - 1) / kSub);
+
+    for (;;) {
+        __syncthreads();  // every warp finished the previous group
+        if (threadIdx.x == 0) {
+            s_group = read_status(p.ctl) != 0 ? p.ngroups : atomicAdd(&p.ctl->ticket, 1);
+        }
+        // +inf border: the top rows of group 0
+        float* rf = &ring[0][0][0][0];
+        for (int k = threadIdx.x; k < kRing * 2; k += blockDim.x) rf[k] = INFINITY;
+        __syncthreads();
+        const int g = s_group;
+        if (g >= p.ngroups) return;
+        const GroupRoles gr = group_roles<NS>(p, g);
+        const int strip = g * NS + w;
+        if (role == 0) {
+            if (w < gr.nstrips_here)
+                run_cost<DP, R>(p, strip, lane, cring_s, cfull_s, cempty_s, csub[w], br);
+        } else if (role == 1) {
+            if (w < gr.nstrips_here)
+                run_dp<R, NS>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                              smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s, cfull_s,
+                              cempty_s, csub[w]);
+        } else if (role == 2) {
+            if (gr.reader)
+                run_reader(p, g, lane, ring[0], smem_u32(&bfull[0][0]), smem_u32(&bempty[0][0]),
+                           rsub[0]);
+        } else {
+            if (gr.writer)
+                run_writer(p, g, lane, ring[NS], smem_u32(&bfull[NS][0]),
+                           smem_u32(&bempty[NS][0]), rsub[NS]);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (s < gr.nstrips_here) csub[s] += nsub;
+#pragma unroll
+        for (int s = 0; s <= NS; ++s)
+            if (ring_used<NS>(gr, s)) rsub[s] += nsub;
+    }
+}
+
+template <int DP, int R>
+cudaError_t launch_t(const DpArgs& a, int num_sms, cudaStream_t s) {
+    constexpr int NS = kSplitStrips;
+    constexpr int kThreads = (2 * NS + 2) * 32;
+    const int smem = NS * SplitSmem<DP, R>::kStripBytes;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dp_split<DP, R, NS>,
+                                                          kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int grid = blocks_per_sm * num_sms;
+    if (grid > a.ngroups) grid = a.ngroups;
+    k_dp_split<DP, R, NS><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool split_supported(int dp, int R) {
+    if (R == 2 || R == 3) return dp <= 32;
+    if (R == 4) return dp <= 16;
+    return false;
+}
+
+cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s) {
+#define PARDTW_SPLIT_CASES(RR)                           \
+    switch (dp) {                                        \
+        case 4: return launch_t<4, RR>(a, num_sms, s);   \
+        case 8: return launch_t<8, RR>(a, num_sms, s);   \
+        case 12: return launch_t<12, RR>(a, num_sms, s); \
+        case 16: return launch_t<16, RR>(a, num_sms, s); \
+        default: break;                                  \
+    }
+    if (R == 2) {
+        PARDTW_SPLIT_CASES(2)
+        if (dp == 32) return launch_t<32, 2>(a, num_sms, s);
+    } else if (R == 3) {
+        PARDTW_SPLIT_CASES(3)
+        if (dp == 32) return launch_t<32, 3>(a, num_sms, s);
+    } else if (R == 4) {
+        PARDTW_SPLIT_CASES(4)
+    }
+#undef PARDTW_SPLIT_CASES
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pardtw

@@ -13,7 +13,8 @@ constexpr int kWarp = 32;
 constexpr int kRowsPerStrip = 30;   // rows of A per warp: lanes 0..29 (lanes 30, 31 carry
                                     // the two bottom rows of the strip above)
 constexpr int kColsPerWord = 16;    // 2-bit codes per uint32 backpointer word
-constexpr int kWarpsPerGroup = 4;   // strips per CTA ("strip group")
+constexpr int kWarpsPerGroup = 4;   // strips per CTA ("strip group") of the one-warp kernels
+constexpr int kSplitStrips = 2;     // strips per CTA of the cost/DP warp-pair kernel
 
 // Device status words (workspace).  [0] first error (DTW_* code), [1] detail,
 // [2] ticket counter of the persistent DP kernel, [3] spare.
@@ -53,6 +54,16 @@ __host__ __device__ inline size_t bp_word_index(int i, int j, int nchunk, int rp
            (size_t)(i - strip * rps);
 }
 
+// Backpointer field of cell (i, j): 2 bits at bit 2 * (j % 16) of its word.
+// Bit 0 is set when the (1,1) candidate attains the cell's minimum, bit 1
+// when the (1,2) candidate does.  The step taken is the first attaining
+// candidate in the order (1,1), (1,2), (2,1) (a later candidate must be
+// strictly smaller), so: bit 0 set -> (1,1); field 2 -> (1,2); field 0 ->
+// (2,1).  Returns the step code 0 = (1,1), 1 = (1,2), 2 = (2,1).
+__host__ __device__ inline int step_of_field(uint32_t field) {
+    return (field & 1u) ? 0 : (field == 2u ? 1 : 2);
+}
+
 // Strip geometry of the DP kernels: R rows per lane.  R = 1: lanes 0..29
 // are rows, lanes 30, 31 carry the strip above (30 rows, 32 words).  R >= 2:
 // lanes 0..30 hold R rows each, lane 31 carries the strip above (31 R rows,
@@ -79,6 +90,20 @@ cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);    
 cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 // Rows per lane the fused DP supports for a padded dimension (0 = none).
 bool multirow_supported(int dp, int R);
+// Warp-specialised DP (dp_split.cu): a cost warp and a DP warp per strip,
+// kSplitStrips strips per CTA; R = 2, 3 or 4.
+cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
+bool split_supported(int dp, int R);
+
+// Which DP kernel runs a problem: kind 0 = one row per lane (dp_kernel.cu),
+// 1 = fused multi-row (dp_multirow.cu), 2 = cost/DP warp pairs (dp_split.cu);
+// R rows per lane, spg strips per CTA (strip group).
+struct DpPlan {
+    int kind, R, spg;
+};
+DpPlan choose_plan(int La, int dp, const dtw_options& o, int num_sms);
+cudaError_t launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
+                        cudaStream_t s);
 cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int rps, int wpb,
                              const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
                              int32_t* scratch, int* path_len, float* total, cudaStream_t s);

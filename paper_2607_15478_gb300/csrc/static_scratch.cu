@@ -96,18 +96,13 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
         return DTW_ERR_CUDA;
     }
 
-    // rows per lane as in dtw_align
-    int R = 1;
-    if (o.rows_per_lane == 2 || o.rows_per_lane == 4) {
-        R = multirow_supported(dp, o.rows_per_lane) ? o.rows_per_lane : 1;
-    } else if (o.rows_per_lane != 1 && multirow_supported(dp, 2)) {
-        const long long warps2 = (La + strip_rows(2) - 1) / strip_rows(2);
-        R = (warps2 > 5LL * num_sms && multirow_supported(dp, 4)) ? 4 : 2;
-    }
+    // the DP kernel dtw_align would choose
+    const DpPlan plan = choose_plan(La, dp, o, num_sms);
+    const int R = plan.R;
     const int rps = strip_rows(R), wpb = strip_words(R);
     const int nstrips = (La + rps - 1) / rps;
     const int nchunk = (Lb + kColsPerWord - 1) / kColsPerWord;
-    const int ngroups = (nstrips + kWarpsPerGroup - 1) / kWarpsPerGroup;
+    const int ngroups = (nstrips + plan.spg - 1) / plan.spg;
     const int La_pad = nstrips * rps;
     const int capn = std::min(La, Lb);
 
@@ -170,8 +165,7 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     a.epoch = 1u;
     a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : 2000000000LL;
     a.skip_publish = o.debug_skip_publish;
-    const cudaError_t e =
-        R == 1 ? launch_dp(a, dp, num_sms, s) : launch_dp_multirow(a, dp, R, num_sms, s);
+    const cudaError_t e = launch_plan(plan, a, dp, num_sms, s);
     if (e != cudaSuccess ||
         launch_backtrace(bp, La, Lb, nchunk, rps, wpb, ctl, e_final, o.cost_shift, path, scratch,
                          path_len, total_cost, s) != cudaSuccess) {

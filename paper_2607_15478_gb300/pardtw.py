@@ -46,7 +46,9 @@ class PardtwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("cost_precision", ctypes.c_int), ("cost_shift", ctypes.c_float),
                 ("wait_limit", ctypes.c_int), ("debug_skip_publish", ctypes.c_int),
-                ("rows_per_lane", ctypes.c_int)]
+                ("rows_per_lane", ctypes.c_int), ("dp_schedule", ctypes.c_int)]
+
+SCHEDULE_AUTO, SCHEDULE_FUSED, SCHEDULE_SPLIT = 0, 1, 2
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -94,13 +96,15 @@ def status_string(status: int) -> str:
 
 
 def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
-                 debug_skip_publish: int = -1, rows_per_lane: int = 0) -> Options:
+                 debug_skip_publish: int = -1, rows_per_lane: int = 0,
+                 dp_schedule: int = SCHEDULE_AUTO) -> Options:
     o = Options()
     load_library().dtw_default_options(ctypes.byref(o))
     o.cost_shift = float(cost_shift)
     o.wait_limit = int(wait_limit_us)
     o.debug_skip_publish = int(debug_skip_publish)
     o.rows_per_lane = int(rows_per_lane)
+    o.dp_schedule = int(dp_schedule)
     return o
 
 

@@ -224,31 +224,55 @@ def test_align_many_matches_single(aligner):
         assert_parity(p.A, p.B, paths[idx], float(costs[idx]))
 
 
-@pytest.mark.parametrize("La,Lb", [(61, 70), (62, 100), (63, 64), (124, 150), (125, 200),
+# (rows per lane, schedule): one row per lane; the fused multi-row kernel;
+# the cost/DP warp pairs
+DECOMPOSITIONS = [(1, 0), (2, 1), (4, 1), (2, 2), (3, 2), (4, 2)]
+
+
+@pytest.mark.parametrize("La,Lb", [(61, 70), (62, 100), (63, 64), (92, 120), (93, 93),
+                                   (94, 150), (124, 150), (125, 200), (186, 250), (187, 190),
                                    (500, 620), (1000, 1200), (3001, 2500)])
 def test_rows_per_lane_decompositions_agree(aligner, La, Lb):
-    # 1, 2 or 4 rows per lane only change the work decomposition: every cell
-    # is computed with the same FP32 operations, so paths and totals must be
-    # bit-identical across decompositions, and match the oracle
+    # the row decomposition and the division of labour between warps only
+    # change who computes what: every cell is computed with the same FP32
+    # operations, so paths and totals must be bit-identical across
+    # decompositions, and match the oracle
     wp = synth.warped_pair(synth.rng_for(55, La + Lb), La, Lb, 12, knots=4, tmin=0.5, tmax=2.0)
     A, B = dev(wp.A), dev(wp.B)
     ref = None
-    for R in (1, 2, 4):
-        path, total = aligner.align(A, B, rows_per_lane=R)
+    for R, sched in DECOMPOSITIONS:
+        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched)
         if ref is None:
             ref = (path.cpu().numpy(), total)
             assert_parity(wp.A, wp.B, path, total)
         else:
-            np.testing.assert_array_equal(path.cpu().numpy(), ref[0])
-            assert total == ref[1]
+            np.testing.assert_array_equal(path.cpu().numpy(), ref[0], err_msg=f"R={R} s={sched}")
+            assert total == ref[1], (R, sched)
 
 
-@pytest.mark.parametrize("R", [1, 2, 4])
-def test_exact_ties_every_decomposition(aligner, R):
+@pytest.mark.parametrize("D", [4, 8, 16, 32])
+def test_decompositions_agree_feature_dims(aligner, D):
+    wp = synth.warped_pair(synth.rng_for(56, D), 400, 450, D, knots=4, tmin=0.5, tmax=2.0)
+    A, B = dev(wp.A), dev(wp.B)
+    ref = None
+    for R, sched in DECOMPOSITIONS:
+        if R == 4 and D > 16:
+            continue
+        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched)
+        if ref is None:
+            ref = (path.cpu().numpy(), total)
+            assert_parity(wp.A, wp.B, path, total)
+        else:
+            np.testing.assert_array_equal(path.cpu().numpy(), ref[0], err_msg=f"R={R} s={sched}")
+            assert total == ref[1], (R, sched)
+
+
+@pytest.mark.parametrize("R,sched", DECOMPOSITIONS)
+def test_exact_ties_every_decomposition(aligner, R, sched):
     rng = np.random.default_rng(77)
     A = np.eye(3, dtype=np.float32)[rng.integers(0, 3, 700)]
     B = np.eye(3, dtype=np.float32)[rng.integers(0, 3, 900)]
-    path, total = aligner.align(dev(A), dev(B), rows_per_lane=R)
+    path, total = aligner.align(dev(A), dev(B), rows_per_lane=R, dp_schedule=sched)
     po, to = oracle.dtw(A, B)
     assert total == to
     np.testing.assert_array_equal(path.cpu().numpy(), po)
