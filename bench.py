@@ -117,19 +117,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+DP_SOURCES = ("paper_2607_15478_gb300/csrc/dp_split.cu", "paper_2607_15478_gb300/csrc/dp_device.cuh",
+              "paper_2607_15478_gb300/csrc/pardtw_common.cuh")
+
+
+def dp_sources_sha256():
+    """One hash over the sources the timed DP kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in DP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def dp_traffic_from_profiles():
     """DRAM bytes per DP launch from the committed ncu summary, if it matches the source."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "dp_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2607_15478_gb300", "csrc", "dp_multirow.cu")
     if not os.path.exists(p):
         return None
     try:
         with open(p) as f:
             d = json.load(f)
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        if d.get("source_sha256") != sha:
+        if d.get("source_sha256") != dp_sources_sha256():
             return None
         return float(d["dram_bytes_per_launch_full"])
     except Exception:
@@ -304,7 +314,8 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": traffic,
-                         "kernel": "k_dp_multirow (column-sweep DP, cost on the fly)",
+                         "kernel": "k_dp_split (column-sweep DP: per strip a cost warp and a DP "
+                                   "warp, cost on the fly)",
                          "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{clock:.0f} MHz (sm_max_mhz, {src})"},

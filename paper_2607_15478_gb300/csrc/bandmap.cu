@@ -63,7 +63,9 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
     int en[kColsPerWord];
 #pragma unroll
     for (int q = 0; q < kColsPerWord; ++q) {
-        const int step = step_of_field((word >> (2 * q)) & 3u);
+        // field bits of column q (see step_of_field): bit 0 -> (1,1), else
+        // bit 1 -> (1,2), else (2,1)
+        const bool f11 = (word >> (2 * q)) & 1u, f12 = (word >> (2 * q + 1)) & 1u;
         int p11 = (q >= 1) ? e1[q - 1] : l1m1;                    // (i-1, j-1)
         int p12 = (q >= 2) ? e1[q - 2] : (q == 1 ? l1m1 : l1m2);  // (i-1, j-2)
         int p21 = (q >= 1) ? e2[q - 1] : l2m1;                    // (i-2, j-1)
@@ -79,7 +81,7 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
                 p21 = (r0 >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
             }
         }
-        int v = step == 0 ? p11 : (step == 1 ? p12 : p21);
+        int v = f11 ? p11 : (f12 ? p12 : p21);
         if (kTop && i == 0 && jb + q == 0) v = kOrigin;
         en[q] = v;
     }

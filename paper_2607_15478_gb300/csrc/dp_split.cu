@@ -247,10 +247,9 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
 #pragma unroll
     for (int k = 0; k < R; ++k) cur[k] = prv[k] = INFINITY;
     float ylp = INFINITY;
-    int status_seen = 0;  // loaded one chunk ahead of its test
+    // (no poll of the failure flag in the sweep: every wait checks it on its
+    // slow path, and a warp that never waits ends with its strip)
     for (int j0 = 0; j0 < Lb; j0 += kColsPerWord) {
-        if (__shfl_sync(kFull, status_seen, 0) != 0) return;
-        status_seen = read_status(p.ctl);
         uint32_t word[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) word[k] = 0;
