@@ -71,22 +71,35 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
+        # started before the timed region (nvidia-smi takes a moment to begin
+        # sampling); only samples read between mark_start and mark_end count
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.time() + 3.0
+            while not self.lines and time.time() < deadline:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_start(self):
+        self.window = [time.time(), None]
+
+    def mark_end(self):
+        if self.window:
+            self.window[1] = time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -99,7 +112,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = self.window if self.window and self.window[1] else (0.0, float("inf"))
+        # a sample arrives after its 20 ms interval: keep the ones taken inside
+        for ts, ln in self.lines:
+            if not (t0 < ts <= t1 + 0.02):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -240,16 +257,18 @@ def run_ours(args):
         raise RuntimeError(f"alignment failed on rank {rank}: {pardtw.status_string(-n_ok)}")
 
     step_ms, dp_ms = [], []
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(dev.index) as clk:
+    with ClockSampler(dev.index) as clk:  # sampling starts before the barrier
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
         for _ in range(args.steps):
             step()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
             dp_ms.append(al.stage_times()[1])
         torch.cuda.synchronize(dev)
+        clk.mark_end()
         if ws > 1:
             dist.barrier()
     t_local = sum(step_ms) / 1e3
