@@ -253,8 +253,21 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     a.skip_publish = o.debug_skip_publish;
     CU(launch_plan(L.plan, a, L.dp, h->num_sms, s));
     if (h->timing) CU(cudaEventRecord(h->ev[2], s));
-    CU(launch_backtrace_bands(bp, La, Lb, L.nchunk, L.rps, L.wpb, ctl, e_final, o.cost_shift,
-                              out_path, out_len, out_total, ws + L.off_bt, s));
+    BtArgs bt;
+    bt.bp = bp;
+    bt.La = La;
+    bt.Lb = Lb;
+    bt.nchunk = L.nchunk;
+    bt.rps = L.rps;
+    bt.wpb = L.wpb;
+    bt.ctl = ctl;
+    bt.e_final = e_final;
+    bt.mu = o.cost_shift;
+    bt.path = out_path;
+    bt.path_len = out_len;
+    bt.total = out_total;
+    bt.scratch = ws + L.off_bt;
+    CU(launch_backtrace_bands(bt, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
         h->timed = true;
@@ -266,6 +279,138 @@ int validate(const float* A, int La, const float* B, int Lb, int D) {
     if (!A || !B || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
     if (!reachable(La, Lb)) return DTW_ERR_UNREACHABLE;
     if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
+    return DTW_OK;
+}
+
+// The batched path of dtw_align_many (device inputs and outputs, D <= 32):
+// every pair of `idx` in one batched normalisation, one persistent DP launch
+// over a (pair, strip group) work queue and one batched backtrace.
+int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, const int* La,
+                const float* const* B, const int* Lb, int D, const dtw_options& o, int R,
+                int32_t* paths, const int64_t* path_off, int* path_len, float* cost) {
+    const int m = (int)idx.size();
+    if (m == 0) return DTW_OK;
+    // The work queue runs the pairs with the longest sweeps first, so that the
+    // last pairs to start are short and no long chain of strips is left alone
+    // at the end (the order does not change any result).
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return (long long)Lb[x] * 256 + La[x] > (long long)Lb[y] * 256 + La[y];
+    });
+    const int dp = padded_dim(D);
+    const DpPlan plan = {2, R, kSplitStrips};
+    std::vector<Layout> Ls(m);
+    std::vector<size_t> off(m), boff(m);
+    // descriptors, then one control block per pair, then every pair's buffers
+    size_t o0 = 0;
+    const size_t off_dp = o0;
+    o0 = align256(o0 + sizeof(DpArgs) * m);
+    const size_t off_norm = o0;
+    o0 = align256(o0 + sizeof(NormArgs) * m);
+    const size_t off_bt = o0;
+    o0 = align256(o0 + sizeof(BtArgs) * m);
+    const size_t off_item = o0;
+    o0 = align256(o0 + sizeof(int) * (m + 1) + 16);  // + the work-queue ticket
+    const size_t off_ctl = o0;
+    o0 = align256(o0 + (size_t)256 * m);
+    size_t border_total = 0;
+    int maxLa = 0, maxLb = 0, max_frames = 0;
+    std::vector<int> item0(m + 1, 0);
+    for (int q = 0; q < m; ++q) {
+        const int k = idx[q];
+        Ls[q] = make_layout(La[k], Lb[k], D, plan);
+        const Layout& L = Ls[q];
+        off[q] = o0;
+        o0 = align256(o0 + (L.off_stage_a - L.off_ahat));  // Ahat, Bhat, bp, band maps
+        boff[q] = border_total;
+        border_total += L.border_bytes;
+        item0[q + 1] = item0[q] + L.ngroups;
+        maxLa = std::max(maxLa, La[k]);
+        maxLb = std::max(maxLb, Lb[k]);
+        max_frames = std::max(max_frames, L.La_pad + L.nchunk * kColsPerWord);
+    }
+    int rc = ensure_workspace(h, o0, border_total);
+    if (rc != DTW_OK) return rc;
+    char* ws = h->ws;
+    cudaStream_t s = h->stream;
+    unsigned epoch = ++h->epoch;
+    if (epoch == 0) epoch = ++h->epoch;
+    std::vector<DpArgs> dps(m);
+    std::vector<NormArgs> nas(m);
+    std::vector<BtArgs> bts(m);
+    for (int q = 0; q < m; ++q) {
+        const int k = idx[q];
+        const Layout& L = Ls[q];
+        char* base = ws + off[q] - L.off_ahat;  // so that base + L.off_* addresses this pair
+        DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + off_ctl + (size_t)256 * q);
+        float* e_final = reinterpret_cast<float*>(ws + off_ctl + (size_t)256 * q + 16);
+        float* Ahat = reinterpret_cast<float*>(base + L.off_ahat);
+        float* Bhat = reinterpret_cast<float*>(base + L.off_bhat);
+        uint32_t* bpw = reinterpret_cast<uint32_t*>(base + L.off_bp);
+        NormArgs& na = nas[q];
+        na.A = A[k];
+        na.La = La[k];
+        na.La_pad = L.La_pad;
+        na.B = B[k];
+        na.Lb = Lb[k];
+        na.Lb_pad = L.nchunk * kColsPerWord;
+        na.Ahat = Ahat;
+        na.Bt = Bhat;
+        na.ctl = ctl;
+        DpArgs& a = dps[q];
+        a.Ahat = Ahat;
+        a.Bhat = Bhat;
+        a.bp = bpw;
+        a.gborder = h->border + boff[q] / sizeof(unsigned long long);
+        a.ctl = ctl;
+        a.e_final = e_final;
+        a.La = La[k];
+        a.Lb = Lb[k];
+        a.nstrips = L.nstrips;
+        a.nchunk = L.nchunk;
+        a.ngroups = L.ngroups;
+        a.rps = L.rps;
+        a.wpb = L.wpb;
+        a.mu = o.cost_shift;
+        a.kcost = 1.0f - o.cost_shift;
+        a.epoch = epoch;
+        a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
+        a.skip_publish = o.debug_skip_publish;
+        BtArgs& bt = bts[q];
+        bt.bp = bpw;
+        bt.La = La[k];
+        bt.Lb = Lb[k];
+        bt.nchunk = L.nchunk;
+        bt.rps = L.rps;
+        bt.wpb = L.wpb;
+        bt.ctl = ctl;
+        bt.e_final = e_final;
+        bt.mu = o.cost_shift;
+        bt.path = paths + 2 * path_off[k];
+        bt.path_len = path_len + k;
+        bt.total = cost ? cost + k : nullptr;
+        bt.scratch = base + L.off_bt;
+    }
+    CU(cudaMemcpyAsync(ws + off_dp, dps.data(), sizeof(DpArgs) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ws + off_norm, nas.data(), sizeof(NormArgs) * m, cudaMemcpyHostToDevice,
+                       s));
+    CU(cudaMemcpyAsync(ws + off_bt, bts.data(), sizeof(BtArgs) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ws + off_item, item0.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice,
+                       s));
+    int* ticket = reinterpret_cast<int*>(ws + off_item + sizeof(int) * (m + 1));
+    if (h->timing) CU(cudaEventRecord(h->ev[0], s));
+    CU(launch_normalise_many(reinterpret_cast<const NormArgs*>(ws + off_norm), m, max_frames, D,
+                             dp, ticket, s));
+    if (h->timing) CU(cudaEventRecord(h->ev[1], s));
+    CU(launch_dp_split_many(reinterpret_cast<const DpArgs*>(ws + off_dp),
+                            reinterpret_cast<const int*>(ws + off_item), m, item0[m], ticket, dp,
+                            R, h->num_sms, s));
+    if (h->timing) CU(cudaEventRecord(h->ev[2], s));
+    CU(launch_backtrace_bands_many(reinterpret_cast<const BtArgs*>(ws + off_bt), m, maxLa, maxLb,
+                                   s));
+    if (h->timing) {
+        CU(cudaEventRecord(h->ev[3], s));
+        h->timed = true;
+    }
     return DTW_OK;
 }
 
@@ -462,13 +607,31 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
     std::vector<int> hst(n, DTW_OK);
     std::vector<int> hlen(n, 0);
     std::vector<float> hcost(n, NAN);
+    // One batched launch sequence when every buffer is on the device and the
+    // warp-pair DP applies; otherwise one alignment after another.
+    const int dp = padded_dim(D);
+    const int Rb = (o.rows_per_lane >= 2 && o.rows_per_lane <= 4) ? o.rows_per_lane : 3;
+    bool batched = paths_dev && len_dev && cost_dev && dp != 0 && split_supported(dp, Rb) &&
+                   o.rows_per_lane != 1 && o.dp_schedule != DTW_SCHEDULE_FUSED;
+    std::vector<int> valid;
     for (int k = 0; k < n; ++k) {
-        int rc = validate(A[k], La[k], B[k], Lb[k], D);
+        const int rc = validate(A[k], La[k], B[k], Lb[k], D);
         if (rc != DTW_OK) {
             hst[k] = rc;
             hlen[k] = -rc;
-            continue;
+        } else {
+            valid.push_back(k);
+            if (!is_device_ptr(A[k]) || !is_device_ptr(B[k])) batched = false;
         }
+    }
+    if (batched) {
+        const int rc = align_batch(h, valid, A, La, B, Lb, D, o, Rb, paths, path_off, path_len,
+                                   cost);
+        if (rc != DTW_OK) return rc;
+    }
+    for (int k = 0; k < n && !batched; ++k) {
+        int rc = hst[k];
+        if (rc != DTW_OK) continue;
         int32_t* pk = paths + 2 * path_off[k];
         if (paths_dev && len_dev && cost_dev) {
             rc = align_device(h, A[k], La[k], B[k], Lb[k], D, o, pk, path_len + k,

@@ -35,7 +35,32 @@ constexpr int kSegThreads = 512;
 constexpr int kSegCols = kSegThreads * kColsPerWord;  // 8192 columns computed per CTA
 constexpr int kNoPath = -2;
 constexpr int kOrigin = -1;
+constexpr int kBand = 256;  // rows per band
 
+// The backtrace scratch of one pair (bandmap_scratch_bytes(La, Lb) bytes).
+struct BtScratch {
+    int2* exits;     // nbands x Lb: entries of each band's last two rows
+    int2* cross;     // nbands: the path's last cell in each band
+    int2* seg;       // nbands x band: each band's piece of the path, descending
+    int* count;      // nbands: cells in each piece
+    int* end_entry;  // the end cell's entry
+    int nbands;
+};
+__host__ __device__ inline BtScratch bt_scratch(void* scratch, int La, int Lb) {
+    BtScratch r;
+    r.nbands = (La + kBand - 1) / kBand;
+    char* p = static_cast<char*>(scratch);
+    r.exits = reinterpret_cast<int2*>(p);
+    p += (size_t)r.nbands * Lb * sizeof(int2);
+    r.cross = reinterpret_cast<int2*>(p);
+    p += (size_t)r.nbands * sizeof(int2);
+    r.seg = reinterpret_cast<int2*>(p);
+    p += (size_t)r.nbands * kBand * sizeof(int2);
+    r.count = reinterpret_cast<int*>(p);
+    p += (size_t)r.nbands * sizeof(int);
+    r.end_entry = reinterpret_cast<int*>(p);
+    return r;
+}
 
 }  // namespace
 
@@ -112,18 +137,27 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
 
 constexpr int kRowsAhead = 8;  // backpointer rows loaded ahead of use
 
-__global__ void __launch_bounds__(kSegThreads) k_bandmap(const uint32_t* __restrict__ bp, int La,
-                                                         int Lb, int nchunk, int rps, int wpb,
-                                                         int band, int2* __restrict__ exits,
-                                                         int* __restrict__ end_entry) {
+// kMany: one pair per blockIdx.z, from the array `many` (the grid covers the
+// largest pair; blocks beyond a pair's bands or columns leave at once).
+template <bool kMany>
+__global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
+                                                         const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.z] : one;
+    const uint32_t* __restrict__ bp = a.bp;
+    const int La = a.La, Lb = a.Lb, nchunk = a.nchunk, rps = a.rps, wpb = a.wpb;
+    const int band = kBand;
+    const BtScratch sc = bt_scratch(a.scratch, La, Lb);
+    int2* __restrict__ exits = sc.exits;
+    int* __restrict__ end_entry = sc.end_entry;
     // left-neighbour exchange, double-buffered by row parity: columns 14, 15
     // of row i-1 and column 15 of row i-2 of every thread
     __shared__ int s_x[2][kSegThreads][3];
     const int b = blockIdx.y;
-    const int r0 = b * band;
-    const int r1 = min(r0 + band, La);
     const int width = kSegCols - 2 * band;
     const int c0 = blockIdx.x * width;
+    if (b >= sc.nbands || c0 >= Lb) return;  // CTA-uniform
+    const int r0 = b * band;
+    const int r1 = min(r0 + band, La);
     const int halo = (c0 == 0) ? 0 : 2 * band;  // multiple of 16
     const int s0 = c0 - halo;
     const int t = threadIdx.x;
@@ -164,13 +198,19 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const uint32_t* __restr
 
 // One thread: the path's last cell in every band, from the end cell up.
 // cross[b] = (i, j) of that cell for b < last band; status on failure.
-__global__ void k_bt_chain(const int2* __restrict__ exits, const int* __restrict__ end_entry,
-                           int La, int Lb, int band, int nbands, int2* __restrict__ cross,
-                           DevCtl* ctl) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+template <bool kMany>
+__global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
+    if (threadIdx.x != 0) return;
+    const BtArgs& a = kMany ? many[blockIdx.x] : one;
+    const int La = a.La, Lb = a.Lb, band = kBand;
+    DevCtl* ctl = a.ctl;
+    const BtScratch sc = bt_scratch(a.scratch, La, Lb);
+    const int2* __restrict__ exits = sc.exits;
+    const int nbands = sc.nbands;
+    int2* __restrict__ cross = sc.cross;
     if (ctl->status != 0) return;
     cross[nbands - 1] = make_int2(La - 1, Lb - 1);
-    int e = *end_entry;
+    int e = *sc.end_entry;
     for (int b = nbands - 1; b >= 1; --b) {
         if (e < 0) {  // an entry must name a cell of the band above
             atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
@@ -196,9 +236,17 @@ __global__ void k_bt_chain(const int2* __restrict__ exits, const int* __restrict
 // words) that contains the current cell, lane l holding words l, l+32, ...;
 // a step reads its word with one shuffle, and a new block is one coalesced
 // load when the path leaves the current one.
-__global__ void k_bt_walk(const uint32_t* __restrict__ bp, int nchunk, int rps, int wpb,
-                          int band, int nbands, const int2* __restrict__ cross,
-                          int2* __restrict__ seg, int* __restrict__ count, DevCtl* ctl) {
+template <bool kMany>
+__global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.y] : one;
+    const uint32_t* __restrict__ bp = a.bp;
+    const int nchunk = a.nchunk, rps = a.rps, wpb = a.wpb, band = kBand;
+    DevCtl* ctl = a.ctl;
+    const BtScratch sc = bt_scratch(a.scratch, a.La, a.Lb);
+    const int nbands = sc.nbands;
+    const int2* __restrict__ cross = sc.cross;
+    int2* __restrict__ seg = sc.seg;
+    int* __restrict__ count = sc.count;
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nbands) return;
@@ -255,11 +303,21 @@ __global__ void k_bt_walk(const uint32_t* __restrict__ bp, int nchunk, int rps, 
 }
 
 // One CTA: prefix sum of the counts, then the cells in ascending order.
-__global__ void k_bt_emit(const int2* __restrict__ seg, const int* __restrict__ count, int band,
-                          int nbands, int cap, const DevCtl* __restrict__ ctl,
-                          const float* __restrict__ e_final, float mu, int La, int Lb,
-                          int32_t* __restrict__ path, int* __restrict__ path_len,
-                          float* __restrict__ total) {
+template <bool kMany>
+__global__ void k_bt_emit(const BtArgs one, const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.x] : one;
+    const int La = a.La, Lb = a.Lb, band = kBand;
+    const int cap = La < Lb ? La : Lb;
+    const DevCtl* __restrict__ ctl = a.ctl;
+    const float* __restrict__ e_final = a.e_final;
+    const float mu = a.mu;
+    int32_t* __restrict__ path = a.path;
+    int* __restrict__ path_len = a.path_len;
+    float* __restrict__ total = a.total;
+    const BtScratch sc = bt_scratch(a.scratch, La, Lb);
+    const int nbands = sc.nbands;
+    const int2* __restrict__ seg = sc.seg;
+    const int* __restrict__ count = sc.count;
     extern __shared__ int s_off[];  // nbands + 1
     __shared__ int s_err;
     if (threadIdx.x == 0) {
@@ -295,44 +353,38 @@ __global__ void k_bt_emit(const int2* __restrict__ seg, const int* __restrict__ 
     }
 }
 
-int bandmap_band_rows() { return 256; }
+int bandmap_band_rows() { return kBand; }
 
 size_t bandmap_scratch_bytes(int La, int Lb) {
-    const int band = bandmap_band_rows();
-    const int nbands = (La + band - 1) / band;
+    const int nbands = (La + kBand - 1) / kBand;
     return (size_t)nbands * Lb * sizeof(int2)        // exits
            + (size_t)nbands * sizeof(int2)            // cross
-           + (size_t)nbands * band * sizeof(int2)     // seg
+           + (size_t)nbands * kBand * sizeof(int2)    // seg
            + (size_t)nbands * sizeof(int) + 64;       // count, end entry
 }
 
-cudaError_t launch_backtrace_bands(const uint32_t* bp, int La, int Lb, int nchunk, int rps,
-                                   int wpb, DevCtl* ctl, const float* e_final, float mu,
-                                   int32_t* path, int* path_len, float* total, void* scratch,
-                                   cudaStream_t s) {
-    const int band = bandmap_band_rows();
-    const int nbands = (La + band - 1) / band;
-    char* p = static_cast<char*>(scratch);
-    int2* exits = reinterpret_cast<int2*>(p);
-    p += (size_t)nbands * Lb * sizeof(int2);
-    int2* cross = reinterpret_cast<int2*>(p);
-    p += (size_t)nbands * sizeof(int2);
-    int2* seg = reinterpret_cast<int2*>(p);
-    p += (size_t)nbands * band * sizeof(int2);
-    int* count = reinterpret_cast<int*>(p);
-    p += (size_t)nbands * sizeof(int);
-    int* end_entry = reinterpret_cast<int*>(p);
+cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s) {
+    const int nbands = (a.La + kBand - 1) / kBand;
+    const int width = kSegCols - 2 * kBand;
+    dim3 grid((unsigned)((a.Lb + width - 1) / width), (unsigned)nbands, 1);
+    k_bandmap<false><<<grid, kSegThreads, 0, s>>>(a, nullptr);
+    k_bt_chain<false><<<1, 32, 0, s>>>(a, nullptr);
+    k_bt_walk<false><<<(nbands + 3) / 4, 128, 0, s>>>(a, nullptr);
+    k_bt_emit<false><<<1, 256, (nbands + 1) * sizeof(int), s>>>(a, nullptr);
+    return cudaGetLastError();
+}
 
-    const int width = kSegCols - 2 * band;
-    dim3 grid((unsigned)((Lb + width - 1) / width), (unsigned)nbands);
-    k_bandmap<<<grid, kSegThreads, 0, s>>>(bp, La, Lb, nchunk, rps, wpb, band, exits, end_entry);
-    k_bt_chain<<<1, 32, 0, s>>>(exits, end_entry, La, Lb, band, nbands, cross, ctl);
-    k_bt_walk<<<(nbands + 3) / 4, 128, 0, s>>>(bp, nchunk, rps, wpb, band, nbands, cross, seg,
-                                               count, ctl);
-    const int cap = La < Lb ? La : Lb;
-    k_bt_emit<<<1, 256, (nbands + 1) * sizeof(int), s>>>(seg, count, band, nbands, cap, ctl,
-                                                         e_final, mu, La, Lb, path, path_len,
-                                                         total);
+cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, int maxLb,
+                                        cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nbands = (maxLa + kBand - 1) / kBand;
+    const int width = kSegCols - 2 * kBand;
+    dim3 grid((unsigned)((maxLb + width - 1) / width), (unsigned)nbands, (unsigned)n);
+    k_bandmap<true><<<grid, kSegThreads, 0, s>>>(BtArgs{}, many);
+    k_bt_chain<true><<<n, 32, 0, s>>>(BtArgs{}, many);
+    k_bt_walk<true><<<dim3((unsigned)((nbands + 3) / 4), (unsigned)n), 128, 0, s>>>(BtArgs{},
+                                                                                     many);
+    k_bt_emit<true><<<n, 256, (nbands + 1) * sizeof(int), s>>>(BtArgs{}, many);
     return cudaGetLastError();
 }
 

@@ -439,8 +439,12 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
 // own and the helpers share those of the cost warps.  Persistent: a CTA
 // takes strip groups from the ticket counter until none are left, so a
 // group only ever waits on groups that started earlier.
-template <int DP, int R, int NS>
-__global__ void __launch_bounds__((2 * NS + 2) * 32, 1) k_dp_split(const DpArgs p) {
+// kMany: the groups come from a work queue over many pairs (`many`, `item0`,
+// `ticket`; see launch_dp_split_many) instead of the pair `one`.
+template <int DP, int R, int NS, bool kMany>
+__global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
+    k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
+               int nmany, int* ticket) {
     using S = BStage<DP>;
     using M = SplitSmem<DP, R>;
     __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1) k_dp_split(const DpArgs 
     __shared__ __align__(8) unsigned long long cempty[NS][kCostSlots];
     __shared__ __align__(8) unsigned long long bfull[NS + 1][kRingBlk];
     __shared__ __align__(8) unsigned long long bempty[NS + 1][kRingBlk];
-    __shared__ int s_group;
+    __shared__ int s_group, s_pair;
     extern __shared__ __align__(128) unsigned char dyn[];  // NS * M::kStripBytes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
@@ -489,19 +493,45 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1) k_dp_split(const DpArgs 
     for (int s = 0; s < NS; ++s) csub[s] = 0;
 #pragma unroll
     for (int s = 0; s <= NS; ++s) rsub[s] = 0;
-    const unsigned nsub = (unsigned)((p.Lb + kSub - 1) / kSub);
 
     for (;;) {
         __syncthreads();  // every warp finished the previous group
         if (threadIdx.x == 0) {
-            s_group = read_status(p.ctl) != 0 ? p.ngroups : atomicAdd(&p.ctl->ticket, 1);
+            if (kMany) {
+                // item t -> (pair, group): the last pair whose first item is <= t
+                const int t = atomicAdd(ticket, 1);
+                int pi = -1, gi = 0;
+                if (t < item0[nmany]) {
+                    int lo = 0, hi = nmany - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (item0[mid] <= t)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    pi = lo;
+                    gi = t - item0[lo];
+                    if (read_status(many[pi].ctl) != 0) gi = -1;  // the pair has failed
+                }
+                s_pair = pi;
+                s_group = gi;
+            } else {
+                s_pair = 0;
+                s_group =
+                    read_status(one.ctl) != 0 ? one.ngroups : atomicAdd(&one.ctl->ticket, 1);
+            }
         }
         // +inf border: the top rows of group 0
         float* rf = &ring[0][0][0][0];
         for (int k = threadIdx.x; k < kRing * 2; k += blockDim.x) rf[k] = INFINITY;
         __syncthreads();
+        if (kMany && s_pair < 0) return;
+        if (kMany && s_group < 0) continue;  // nothing of a failed pair runs
+        const DpArgs p = kMany ? many[s_pair] : one;
         const int g = s_group;
         if (g >= p.ngroups) return;
+        const unsigned nsub = (unsigned)((p.Lb + kSub - 1) / kSub);
         const GroupRoles gr = group_roles<NS>(p, g);
         const int strip = g * NS + w;
         if (role == 0) {
@@ -530,25 +560,51 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1) k_dp_split(const DpArgs 
     }
 }
 
-template <int DP, int R>
-cudaError_t launch_t(const DpArgs& a, int num_sms, cudaStream_t s) {
+template <int DP, int R, bool kMany>
+cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
+                     int* ticket, int num_sms, cudaStream_t s) {
     constexpr int NS = kSplitStrips;
     constexpr int kThreads = (2 * NS + 2) * 32;
     const int smem = NS * SplitSmem<DP, R>::kStripBytes;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS>,
+        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS, kMany>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dp_split<DP, R, NS>,
-                                                          kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm,
+                                                          k_dp_split<DP, R, NS, kMany>, kThreads,
+                                                          smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int grid = blocks_per_sm * num_sms;
-    if (grid > a.ngroups) grid = a.ngroups;
-    k_dp_split<DP, R, NS><<<grid, kThreads, smem, s>>>(a);
+    if (grid > items) grid = items;
+    k_dp_split<DP, R, NS, kMany><<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
     return cudaGetLastError();
+}
+
+template <bool kMany>
+cudaError_t launch_any(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
+                       int* ticket, int dp, int R, int num_sms, cudaStream_t s) {
+#define PARDTW_SPLIT_CASES(RR)                                                              \
+    switch (dp) {                                                                           \
+        case 4: return launch_t<4, RR, kMany>(a, many, item0, n, items, ticket, num_sms, s);   \
+        case 8: return launch_t<8, RR, kMany>(a, many, item0, n, items, ticket, num_sms, s);   \
+        case 12: return launch_t<12, RR, kMany>(a, many, item0, n, items, ticket, num_sms, s); \
+        case 16: return launch_t<16, RR, kMany>(a, many, item0, n, items, ticket, num_sms, s); \
+        default: break;                                                                     \
+    }
+    if (R == 2) {
+        PARDTW_SPLIT_CASES(2)
+        if (dp == 32) return launch_t<32, 2, kMany>(a, many, item0, n, items, ticket, num_sms, s);
+    } else if (R == 3) {
+        PARDTW_SPLIT_CASES(3)
+        if (dp == 32) return launch_t<32, 3, kMany>(a, many, item0, n, items, ticket, num_sms, s);
+    } else if (R == 4) {
+        PARDTW_SPLIT_CASES(4)
+    }
+#undef PARDTW_SPLIT_CASES
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -560,25 +616,13 @@ bool split_supported(int dp, int R) {
 }
 
 cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s) {
-#define PARDTW_SPLIT_CASES(RR)                           \
-    switch (dp) {                                        \
-        case 4: return launch_t<4, RR>(a, num_sms, s);   \
-        case 8: return launch_t<8, RR>(a, num_sms, s);   \
-        case 12: return launch_t<12, RR>(a, num_sms, s); \
-        case 16: return launch_t<16, RR>(a, num_sms, s); \
-        default: break;                                  \
-    }
-    if (R == 2) {
-        PARDTW_SPLIT_CASES(2)
-        if (dp == 32) return launch_t<32, 2>(a, num_sms, s);
-    } else if (R == 3) {
-        PARDTW_SPLIT_CASES(3)
-        if (dp == 32) return launch_t<32, 3>(a, num_sms, s);
-    } else if (R == 4) {
-        PARDTW_SPLIT_CASES(4)
-    }
-#undef PARDTW_SPLIT_CASES
-    return cudaErrorInvalidValue;
+    return launch_any<false>(a, nullptr, nullptr, 1, a.ngroups, nullptr, dp, R, num_sms, s);
+}
+
+cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, int total_items,
+                                 int* ticket, int dp, int R, int num_sms, cudaStream_t s) {
+    if (n <= 0 || total_items <= 0) return cudaSuccess;
+    return launch_any<true>(DpArgs{}, many, item0, n, total_items, ticket, dp, R, num_sms, s);
 }
 
 }  // namespace pardtw

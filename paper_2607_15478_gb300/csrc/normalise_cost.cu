@@ -21,10 +21,11 @@ int padded_dim(int D) {
 // chunk-transposed (bt_index, Lb_pad frames).  Frames of A beyond La, frames
 // of B beyond Lb and feature slots beyond D are zero.  Thread 0 also clears
 // the control words of the call.
-__global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
-                            const float* __restrict__ B, int Lb, int Lb_pad, int D, int dp,
-                            float* __restrict__ Ahat, float* __restrict__ Bt, DevCtl* ctl) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void normalise_frame(int t, const float* __restrict__ A, int La,
+                                                int La_pad, const float* __restrict__ B, int Lb,
+                                                int Lb_pad, int D, int dp,
+                                                float* __restrict__ Ahat, float* __restrict__ Bt,
+                                                DevCtl* ctl) {
     if (t == 0) {
         ctl->status = 0;
         ctl->detail = 0;
@@ -62,6 +63,22 @@ __global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
     }
 }
 
+__global__ void k_normalise(const float* __restrict__ A, int La, int La_pad,
+                            const float* __restrict__ B, int Lb, int Lb_pad, int D, int dp,
+                            float* __restrict__ Ahat, float* __restrict__ Bt, DevCtl* ctl) {
+    normalise_frame(blockIdx.x * blockDim.x + threadIdx.x, A, La, La_pad, B, Lb, Lb_pad, D, dp,
+                    Ahat, Bt, ctl);
+}
+
+// One pair per blockIdx.y (the grid covers the largest pair); also clears the
+// batch's work-queue ticket.
+__global__ void k_normalise_many(const NormArgs* __restrict__ many, int D, int dp, int* ticket) {
+    const NormArgs& a = many[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && blockIdx.y == 0) *ticket = 0;
+    normalise_frame(t, a.A, a.La, a.La_pad, a.B, a.Lb, a.Lb_pad, D, dp, a.Ahat, a.Bt, a.ctl);
+}
+
 cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb,
                              int Lb_pad, int D, int dp, float* Ahat, float* Bt, DevCtl* ctl,
                              cudaStream_t s) {
@@ -69,6 +86,15 @@ cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B,
     const int threads = 256;
     k_normalise<<<(n + threads - 1) / threads, threads, 0, s>>>(A, La, La_pad, B, Lb, Lb_pad, D,
                                                                 dp, Ahat, Bt, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalise_many(const NormArgs* many, int n, int max_frames, int D, int dp,
+                                  int* ticket, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    dim3 grid((unsigned)((max_frames + threads - 1) / threads), (unsigned)n);
+    k_normalise_many<<<grid, threads, 0, s>>>(many, D, dp, ticket);
     return cudaGetLastError();
 }
 

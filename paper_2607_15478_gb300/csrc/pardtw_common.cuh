@@ -80,12 +80,27 @@ __host__ __device__ inline size_t bt_index(int f, int d, int dp) {
     return ((size_t)(f >> 4) * (size_t)dp + (size_t)d) * 16u + (size_t)(f & 15);
 }
 
+// Normalisation of one pair of a batch (k_normalise_many).
+struct NormArgs {
+    const float* A;
+    int La, La_pad;
+    const float* B;
+    int Lb, Lb_pad;
+    float* Ahat;
+    float* Bt;
+    DevCtl* ctl;
+};
+
 // Launchers (each returns a cudaError_t from the launch).
 cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb,
                              int Lb_pad, int D, int dp, float* Ahat, float* Bt, DevCtl* ctl,
                              cudaStream_t s);
 cudaError_t launch_cost(const float* Ahat, int La, const float* Bt, int Lb, int dp, float* C,
                         cudaStream_t s);
+// n pairs at once (`many`: device array); max_frames = largest La_pad + Lb_pad;
+// also zeroes *ticket, the work queue of launch_dp_split_many.
+cudaError_t launch_normalise_many(const NormArgs* many, int n, int max_frames, int D, int dp,
+                                  int* ticket, cudaStream_t s);
 cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);           // R = 1
 cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 // Rows per lane the fused DP supports for a padded dimension (0 = none).
@@ -94,6 +109,13 @@ bool multirow_supported(int dp, int R);
 // kSplitStrips strips per CTA; R = 2, 3 or 4.
 cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 bool split_supported(int dp, int R);
+// Many pairs in one persistent launch: `many` (device) holds n DpArgs, item0
+// (device, n + 1 ints) the prefix sums of their strip-group counts; CTAs take
+// (pair, group) items from *ticket in that order, so a group only waits on
+// groups of its own pair that were taken earlier.  Each pair's failures stay
+// in its own control block.
+cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, int total_items,
+                                 int* ticket, int dp, int R, int num_sms, cudaStream_t s);
 
 // Which DP kernel runs a problem: kind 0 = one row per lane (dp_kernel.cu),
 // 1 = fused multi-row (dp_multirow.cu), 2 = cost/DP warp pairs (dp_split.cu);
@@ -108,13 +130,26 @@ cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int
                              const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
                              int32_t* scratch, int* path_len, float* total, cudaStream_t s);
 
-// Parallel backtrace through per-band entry maps (bandmap.cu); scratch is
-// caller-provided device memory of bandmap_scratch_bytes(La, Lb) bytes.
+// Parallel backtrace through per-band entry maps (bandmap.cu) of one pair:
+// its backpointers and layout, its control block and end cell, the outputs,
+// and caller-provided scratch of bandmap_scratch_bytes(La, Lb) bytes.
+struct BtArgs {
+    const uint32_t* bp;
+    int La, Lb, nchunk, rps, wpb;
+    DevCtl* ctl;
+    const float* e_final;
+    float mu;
+    int32_t* path;
+    int* path_len;
+    float* total;
+    void* scratch;
+};
 size_t bandmap_scratch_bytes(int La, int Lb);
-cudaError_t launch_backtrace_bands(const uint32_t* bp, int La, int Lb, int nchunk, int rps,
-                                   int wpb, DevCtl* ctl, const float* e_final, float mu,
-                                   int32_t* path, int* path_len, float* total, void* scratch,
-                                   cudaStream_t s);
+cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s);
+// n pairs at once; `many` is a device array of n BtArgs, maxLa / maxLb the
+// largest sizes among them.
+cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, int maxLb,
+                                        cudaStream_t s);
 
 // Padded feature width used by the kernels for a given D (0 = unsupported).
 int padded_dim(int D);

@@ -1,0 +1,110 @@
+"""Batched alignment (dtw_align_many with device buffers): one normalisation
+launch, one persistent DP launch over a (pair, strip group) work queue and one
+batched backtrace for all pairs.  The kernels and their arithmetic are those of
+the single-pair path, so every pair must equal its own dtw_align result bit
+for bit, and match the FP64 oracle under the acceptance rule of
+test_gpu_parity.  A device-side failure stays with its pair."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_15478_gb300 import synth
+from tests._pins import check_path_valid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aligner():
+    from paper_2607_15478_gb300 import build, pardtw
+    build.build()
+    a = pardtw.Aligner(0)
+    yield a
+    a.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def uneven_pairs(seed, n, lo, hi, D=12):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        La = int(rng.integers(lo, hi + 1))
+        Lb = int(round(La * rng.uniform(0.8, 1.25)))
+        out.append(synth.warped_pair(synth.rng_for(seed, k), La, Lb, D, knots=8, tmin=0.7,
+                                     tmax=1.4))
+    return out
+
+
+def assert_oracle(A, B, path, total):
+    La, Lb = A.shape[0], B.shape[0]
+    p = path.cpu().numpy()
+    check_path_valid(p, La, Lb)
+    po, to = oracle.dtw(A, B)
+    assert abs(total - to) <= max(1e-5 * abs(to), 2e-6 * (La + Lb)), (total, to)
+    if not (p.shape == po.shape and np.array_equal(p, po)):
+        tg = oracle.path_cost(A, B, p)
+        assert abs(tg - to) <= 1e-6 * abs(to) + 1e-7 * (La + Lb), (tg, to)
+
+
+@pytest.mark.parametrize("R", [3, 2, 4])
+def test_batch_equals_single_and_oracle(aligner, R):
+    pairs = uneven_pairs(80 + R, 24, 30, 1500)
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    paths, costs, st = aligner.align_many(As, Bs, rows_per_lane=R)
+    assert (st == 0).all(), st
+    for k, p in enumerate(pairs):
+        single, total = aligner.align(As[k], Bs[k], rows_per_lane=R)
+        np.testing.assert_array_equal(paths[k].cpu().numpy(), single.cpu().numpy())
+        assert float(costs[k]) == total
+        assert_oracle(p.A, p.B, paths[k], float(costs[k]))
+
+
+def test_batch_of_one_and_tiny_pairs(aligner):
+    shapes = [(1, 1), (2, 3), (3, 2), (5, 9), (92, 94), (93, 93), (186, 187), (187, 300)]
+    pairs = [synth.warped_pair(synth.rng_for(90, k), La, Lb, 12, knots=2, tmin=0.5, tmax=2.0)
+             for k, (La, Lb) in enumerate(shapes)]
+    for sub in ([pairs[0]], pairs):
+        paths, costs, st = aligner.align_many([dev(p.A) for p in sub], [dev(p.B) for p in sub])
+        assert (st == 0).all(), st
+        for k, p in enumerate(sub):
+            assert_oracle(p.A, p.B, paths[k], float(costs[k]))
+
+
+def test_batch_failure_stays_with_its_pair(aligner):
+    # group 0 of every pair never publishes its border: pairs with more than
+    # one strip group (La > 186 rows at 3 rows per lane) time out after ~20 ms,
+    # single-group pairs are unaffected, and the handle keeps working
+    from paper_2607_15478_gb300 import pardtw
+    pairs = uneven_pairs(91, 12, 60, 700)
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    paths, costs, st = aligner.align_many(As, Bs, wait_limit_us=20000, debug_skip_publish=0)
+    for k, p in enumerate(pairs):
+        if p.A.shape[0] > 186:
+            assert st[k] == pardtw.DTW_ERR_TIMEOUT, (k, st[k])
+        else:
+            assert st[k] == 0
+            assert_oracle(p.A, p.B, paths[k], float(costs[k]))
+    paths, costs, st = aligner.align_many(As, Bs)
+    assert (st == 0).all()
+    for k, p in enumerate(pairs):
+        assert_oracle(p.A, p.B, paths[k], float(costs[k]))
+
+
+def test_batch_config2_shapes_equal_single(aligner):
+    # the batching workload's length mix (La ~ U[500, 8000]) on 12 pairs:
+    # bit-identical to one alignment after another
+    pairs = synth.config_batch(2, n_pairs=12)
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    paths, costs, st = aligner.align_many(As, Bs)
+    assert (st == 0).all()
+    for k in range(len(pairs)):
+        single, total = aligner.align(As[k], Bs[k])
+        np.testing.assert_array_equal(paths[k].cpu().numpy(), single.cpu().numpy())
+        assert float(costs[k]) == total
