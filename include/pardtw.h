@@ -57,9 +57,14 @@ extern "C" {
 
 /* ---- options -------------------------------------------------------------- */
 #define DTW_COST_FP32 0        /* cost from FP32 features with FP32 accumulation */
+#define DTW_COST_BF16 1        /* cost from BF16-rounded normalised features with FP32
+                                  accumulation on the tensor cores (D <= 128); the DP
+                                  stays FP32.  Approximate: costs differ from the FP32
+                                  ones by up to ~1e-2, so paths may differ where
+                                  alternatives are that close. */
 
 typedef struct dtw_options {
-    int cost_precision;    /* DTW_COST_FP32 */
+    int cost_precision;    /* DTW_COST_FP32 (default) or DTW_COST_BF16 */
     /* The DP runs on C - cost_shift and adds cost_shift * (La + Lb - 2) to the
      * total at the end.  Every path weighs exactly (La-1) + (Lb-1) (Sec. V),
      * so the optimal path is unchanged in exact arithmetic; a shift near the

@@ -78,7 +78,7 @@ bool reachable(int La, int Lb) {
 struct Layout {
     DpPlan plan;
     int dp, R, rps, wpb, nstrips, nchunk, ngroups, La_pad, cap;
-    size_t off_ctl, off_ahat, off_bhat, off_bp, off_bt, off_stage_a, off_stage_b,
+    size_t off_ctl, off_ahat, off_bhat, off_bbf, off_bp, off_bt, off_stage_a, off_stage_b,
         off_stage_path, total;
     size_t border_bytes;
 };
@@ -92,6 +92,7 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
     (void)La;
     (void)num_sms;
     const DpPlan one = {0, 1, kWarpsPerGroup};
+    if (o.cost_precision == DTW_COST_BF16) return {2, 3, kSplitStrips, 1};
     const int req = o.rows_per_lane;
     if (req == 1) return one;
     if (o.dp_schedule == DTW_SCHEDULE_FUSED) {
@@ -109,7 +110,9 @@ cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int
     switch (plan.kind) {
         case 0: return launch_dp(a, dp, num_sms, s);
         case 1: return launch_dp_multirow(a, dp, plan.R, num_sms, s);
-        case 2: return launch_dp_split(a, dp, plan.R, num_sms, s);
+        case 2:
+            return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s)
+                             : launch_dp_split(a, dp, plan.R, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -119,7 +122,8 @@ namespace {
 Layout make_layout(int La, int Lb, int D, const DpPlan& plan) {
     Layout L;
     L.plan = plan;
-    L.dp = padded_dim(D);
+    // the BF16 cost runs its tensor-core products over 64 or 128 features
+    L.dp = plan.bf16 ? (D <= 64 ? 64 : 128) : padded_dim(D);
     const int R = plan.R;
     L.R = R;
     L.rps = strip_rows(R);
@@ -136,6 +140,8 @@ Layout make_layout(int La, int Lb, int D, const DpPlan& plan) {
     o = align256(o + (size_t)L.La_pad * L.dp * sizeof(float));
     L.off_bhat = o;
     o = align256(o + (size_t)L.nchunk * kColsPerWord * L.dp * sizeof(float));
+    L.off_bbf = o;
+    if (plan.bf16) o = align256(o + (size_t)L.nchunk * kColsPerWord * kBfStride * 2);
     L.off_bp = o;
     o = align256(o + (size_t)L.nstrips * L.nchunk * L.wpb * sizeof(uint32_t));
     L.off_bt = o;
@@ -229,11 +235,14 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     if (h->timing) CU(cudaEventRecord(h->ev[0], s));
     CU(launch_normalise(dA, La, L.La_pad, dB, Lb, L.nchunk * kColsPerWord, D, L.dp, Ahat, Bhat,
                         ctl, s));
+    void* Bbf = L.plan.bf16 ? ws + L.off_bbf : nullptr;
+    if (Bbf) CU(launch_pack_b_bf16(dB, Lb, L.nchunk * kColsPerWord, D, Bbf, s));
     if (h->timing) CU(cudaEventRecord(h->ev[1], s));
 
     DpArgs a;
     a.Ahat = Ahat;
     a.Bhat = Bhat;
+    a.Bbf = Bbf;
     a.bp = bp;
     a.gborder = h->border;
     a.ctl = ctl;
@@ -359,6 +368,7 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         DpArgs& a = dps[q];
         a.Ahat = Ahat;
         a.Bhat = Bhat;
+        a.Bbf = nullptr;
         a.bp = bpw;
         a.gborder = h->border + boff[q] / sizeof(unsigned long long);
         a.ctl = ctl;
@@ -495,7 +505,8 @@ int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* by
     size_t most = 0;
     const DpPlan plans[] = {{0, 1, kWarpsPerGroup}, {1, 2, kWarpsPerGroup},
                             {1, 4, kWarpsPerGroup}, {2, 2, kSplitStrips},
-                            {2, 3, kSplitStrips},   {2, 4, kSplitStrips}};
+                            {2, 3, kSplitStrips},   {2, 4, kSplitStrips},
+                            {2, 3, kSplitStrips, 1}};
     for (const DpPlan& plan : plans) {
         const Layout L = make_layout(La, Lb, D, plan);
         most = std::max(most, L.total + L.border_bytes);
@@ -552,7 +563,9 @@ int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     if (rc != DTW_OK) return rc;
     if (cap < std::min(La, Lb)) return DTW_ERR_INVALID;
     const dtw_options o = opt ? *opt : defaults();
-    if (o.cost_precision != DTW_COST_FP32) return DTW_ERR_UNSUPPORTED;
+    if (o.cost_precision != DTW_COST_FP32 &&
+        (o.cost_precision != DTW_COST_BF16 || D > 128))
+        return DTW_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
 
@@ -597,7 +610,9 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
         return DTW_ERR_INVALID;
     if (n == 0) return DTW_OK;
     const dtw_options o = opt ? *opt : defaults();
-    if (o.cost_precision != DTW_COST_FP32) return DTW_ERR_UNSUPPORTED;
+    if (o.cost_precision != DTW_COST_FP32 &&
+        (o.cost_precision != DTW_COST_BF16 || D > 128))
+        return DTW_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
     const bool paths_dev = is_device_ptr(paths);
@@ -612,7 +627,8 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
     const int dp = padded_dim(D);
     const int Rb = (o.rows_per_lane >= 2 && o.rows_per_lane <= 4) ? o.rows_per_lane : 3;
     bool batched = paths_dev && len_dev && cost_dev && dp != 0 && split_supported(dp, Rb) &&
-                   o.rows_per_lane != 1 && o.dp_schedule != DTW_SCHEDULE_FUSED;
+                   o.rows_per_lane != 1 && o.dp_schedule != DTW_SCHEDULE_FUSED &&
+                   o.cost_precision == DTW_COST_FP32;
     std::vector<int> valid;
     for (int k = 0; k < n; ++k) {
         const int rc = validate(A[k], La[k], B[k], Lb[k], D);

@@ -45,10 +45,28 @@ struct CostRing {
     static constexpr int kBytes = kCostSlots * kSlotBytes;
 };
 
-template <int DP, int R>
+// BF16 cost: one cost slot holds the 8 costs of each of the 32 R rows of the
+// strip row by row, kRowFloats floats per row (48-byte rows: the DP warp's
+// 16-byte loads of rows 3l+k then fall in distinct bank groups).
+constexpr int kRowFloats = 12;
+template <int R>
+struct CostRingRM {
+    static constexpr int kSlotBytes = 32 * R * kRowFloats * 4;
+    static constexpr int kBytes = kCostSlots * kSlotBytes;
+};
+// BF16 cost: the strip's rows of A as bf16 (32 R rows of kBfStride), and a
+// ring of kBfSlots blocks of 16 frames of B (one chunk each) filled by TMA.
+constexpr int kBfSlots = 4;
+constexpr int kBfBlkBytes = kColsPerWord * kBfStride * 2;
+
+template <int DP, int R, bool kBF>
 struct SplitSmem {
-    // per strip slot: the cost warp's B stage, then the cost ring
-    static constexpr int kStripBytes = BStage<DP>::kWarpBytes + CostRing<R>::kBytes;
+    // per strip slot: the cost warp's operands (B stage, or A tile and B
+    // stage), then the cost ring
+    static constexpr int kOperandBytes =
+        kBF ? 32 * R * kBfStride * 2 + kBfSlots * kBfBlkBytes : BStage<DP>::kWarpBytes;
+    static constexpr int kStripBytes =
+        kOperandBytes + (kBF ? CostRingRM<R>::kBytes : CostRing<R>::kBytes);
 };
 
 // Barrier `slot` of an array of 8-byte mbarriers, and the phase parity a
@@ -159,10 +177,186 @@ __device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, u
     br.drain();
 }
 
-// The costs of lifetime sub-chunk t (its slot must be full) into c.
-template <int R>
+__device__ __forceinline__ void ldsm_x4(unsigned addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+// d += a (16x16 bf16, row) * b (16x8 bf16, col), FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// BF16 cost warp of `strip` (DP = K = 64 or 128, R = 3 rows per lane): per
+// 16 columns one 96 x 16 x DP product on the tensor cores (6 x 2 tiles of
+// m16n8k16 per 16 features), costs C' = (1 - mu) - dot written row-major into
+// two cost slots; the ghost lane's rows get 1e30.  A's rows are converted to
+// bf16 into shared memory once per strip; B's bf16 frames arrive by TMA, one
+// chunk per block.
+template <int DP, int R>
+__device__ __forceinline__ void run_cost_bf16(const DpArgs& p, int strip, int lane, unsigned a_s,
+                                              unsigned b_s, unsigned bbar_s, unsigned& bbase,
+                                              unsigned cring, unsigned cfull, unsigned cempty,
+                                              unsigned csub) {
+    constexpr int kRows = 31 * R;       // real rows of the strip
+    constexpr int kM = 32 * R;          // rows of the product (6 tiles of 16)
+    constexpr int kMT = kM / 16;
+    constexpr int kKS = DP / 16;        // k-steps of 16 features
+    constexpr int kRowBytes = kBfStride * 2;
+    const int Lb = p.Lb;
+    const int nchunk = p.nchunk;
+    const int nsub = (Lb + kSub - 1) / kSub;
+    // A: rows r = 0 .. kM-1 of the strip as bf16 (rows >= kRows are zero)
+    for (int r = lane; r < kM; r += kWarp) {
+        const float* src = p.Ahat + (size_t)(strip * kRows + r) * DP;
+#pragma unroll 4
+        for (int d = 0; d < DP; d += 8) {
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (r < kRows) {
+                v0 = __ldg(reinterpret_cast<const float4*>(src + d));
+                v1 = __ldg(reinterpret_cast<const float4*>(src + d + 4));
+            }
+            const uint32_t w0 = pack_bf16x2(v0.x, v0.y), w1 = pack_bf16x2(v0.z, v0.w);
+            const uint32_t w2 = pack_bf16x2(v1.x, v1.y), w3 = pack_bf16x2(v1.z, v1.w);
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             a_s + (unsigned)(r * kRowBytes + d * 2)),
+                         "r"(w0), "r"(w1), "r"(w2), "r"(w3)
+                         : "memory");
+        }
+    }
+    __syncwarp();
+    const char* gb = static_cast<const char*>(p.Bbf);
+    int issued = 0, waited = 0;
+    auto issue = [&](int c) {  // lane 0: chunk c of B into slot (bbase + c) % kBfSlots
+        if (lane == 0) {
+            const unsigned t = bbase + (unsigned)c;
+            tma_load(b_s + (t % kBfSlots) * kBfBlkBytes, gb + (size_t)c * kBfBlkBytes,
+                     (unsigned)kBfBlkBytes, bbar_s + 8 * (t % kBfSlots));
+        }
+    };
+    while (issued < nchunk && issued < kBfSlots - 1) issue(issued++);
+    const float kc = p.kcost;
+    const int g = lane >> 2, t4 = lane & 3;
+    bool ok = true;
+    for (int c = 0; c < nchunk && ok; ++c) {
+        // chunk c of B is in its slot
+        const unsigned tb = bbase + (unsigned)c;
+        if (!mbar_wait(bbar_s + 8 * (tb % kBfSlots), (tb / kBfSlots) & 1u, p.ctl, p.timeout_ns,
+                       4)) {
+            ok = false;
+            break;
+        }
+        waited = c + 1;
+        if (issued < nchunk) issue(issued++);
+        const int nj = (2 * c + 1 < nsub) ? 2 : 1;  // sub-chunks of this chunk
+        const unsigned t0 = csub + (unsigned)(2 * c);
+        for (int j = 0; j < nj; ++j)
+            if (!mbar_wait(bar_at(cempty, (t0 + j) % kCostSlots),
+                           use_parity(t0 + j, kCostSlots) ^ 1u, p.ctl, p.timeout_ns, 6)) {
+                ok = false;
+                break;
+            }
+        if (!ok) break;
+        // B fragments of the chunk's 16 frames: n-tile j = frames 8j .. 8j+7
+        const unsigned bslot = b_s + (tb % kBfSlots) * kBfBlkBytes;
+        uint32_t bf[2][kKS][2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int kq = 0; kq < kKS / 2; ++kq)
+                ldsm_x4(bslot + (unsigned)((8 * j + (lane & 7)) * kRowBytes +
+                                           (32 * kq + 8 * (lane >> 3)) * 2),
+                        bf[j][2 * kq][0], bf[j][2 * kq][1], bf[j][2 * kq + 1][0],
+                        bf[j][2 * kq + 1][1]);
+        float acc[kMT][2][4];
+#pragma unroll
+        for (int mt = 0; mt < kMT; ++mt)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][j][e] = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < kMT; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < kKS; ++ks) {
+                uint32_t a[4];
+                ldsm_x4(a_s + (unsigned)((16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1)) *
+                                             kRowBytes +
+                                         (16 * ks + 8 * (lane >> 4)) * 2),
+                        a[0], a[1], a[2], a[3]);
+                mma_bf16(acc[mt][0], a, bf[0][ks]);
+                mma_bf16(acc[mt][1], a, bf[1][ks]);
+            }
+        // costs into the two slots: rows 16 mt + g (+8), columns 2 t4, 2 t4 + 1
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (j >= nj) break;
+            const unsigned slot = cring + ((t0 + j) % kCostSlots) * CostRingRM<R>::kSlotBytes;
+#pragma unroll
+            for (int mt = 0; mt < kMT; ++mt) {
+                const int r0 = 16 * mt + g, r1 = r0 + 8;
+                const float v00 = r0 < kRows ? kc - acc[mt][j][0] : kGhostCost;
+                const float v01 = r0 < kRows ? kc - acc[mt][j][1] : kGhostCost;
+                const float v10 = r1 < kRows ? kc - acc[mt][j][2] : kGhostCost;
+                const float v11 = r1 < kRows ? kc - acc[mt][j][3] : kGhostCost;
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(
+                                 slot + (unsigned)(r0 * kRowFloats * 4 + t4 * 8)),
+                             "f"(v00), "f"(v01)
+                             : "memory");
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(
+                                 slot + (unsigned)(r1 * kRowFloats * 4 + t4 * 8)),
+                             "f"(v10), "f"(v11)
+                             : "memory");
+            }
+            mbar_arrive(bar_at(cfull, (t0 + j) % kCostSlots));
+        }
+    }
+    // leave no copy in flight (bounded)
+    for (int c = waited; c < issued; ++c) {
+        const unsigned tb = bbase + (unsigned)c;
+        const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+        while (!__all_sync(kFull, mbar_try_wait(bbar_s + 8 * (tb % kBfSlots),
+                                                (tb / kBfSlots) & 1u))) {
+            if (__shfl_sync(kFull, global_ns(), 0) - t0 > 1000000000LL) break;
+        }
+    }
+    bbase += (unsigned)issued;
+}
+
+// The costs of lifetime sub-chunk t (its slot must be full) into c;
+// kRM: the row-major slot of the BF16 cost.
+template <int R, bool kRM>
 __device__ __forceinline__ void load_costs(unsigned cring, unsigned t, int lane,
                                            float (*c)[kSub]) {
+    if constexpr (kRM) {
+        const unsigned src = cring + (t % kCostSlots) * CostRingRM<R>::kSlotBytes +
+                             (unsigned)(lane * R) * (kRowFloats * 4);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float4 v0 = lds128(src + (unsigned)k * (kRowFloats * 4));
+            const float4 v1 = lds128(src + (unsigned)k * (kRowFloats * 4) + 16);
+            c[k][0] = v0.x;
+            c[k][1] = v0.y;
+            c[k][2] = v0.z;
+            c[k][3] = v0.w;
+            c[k][4] = v1.x;
+            c[k][5] = v1.y;
+            c[k][6] = v1.z;
+            c[k][7] = v1.w;
+        }
+        return;
+    }
     using CR = CostRing<R>;
     const unsigned src = cring + (t % kCostSlots) * CR::kSlotBytes + (unsigned)lane * 16u;
 #pragma unroll
@@ -210,7 +404,7 @@ __device__ __forceinline__ bool ring_used(const GroupRoles& r, int w) {
 // bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
 // sub-chunk counts of the input and output rings at the start of this
 // group; csub: that of the cost ring.
-template <int R, int NS>
+template <int R, int NS, bool kRM>
 __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
@@ -240,7 +434,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
     if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
                    p.timeout_ns, 7))
         return;
-    load_costs<R>(cring, csub, lane, c);
+    load_costs<R, kRM>(cring, csub, lane, c);
     mbar_arrive(bar_at(cempty, csub % kCostSlots));
 
     float cur[R], prv[R];
@@ -303,7 +497,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                                             use_parity(t + 1, kCostSlots), p.ctl, p.timeout_ns,
                                             7))
                             return;
-                        load_costs<R>(cring, t + 1, lane, cn);
+                        load_costs<R, kRM>(cring, t + 1, lane, cn);
                         mbar_arrive(bar_at(cempty, (t + 1) % kCostSlots));
                     }
                     float cu[R];
@@ -441,12 +635,12 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
 // group only ever waits on groups that started earlier.
 // kMany: the groups come from a work queue over many pairs (`many`, `item0`,
 // `ticket`; see launch_dp_split_many) instead of the pair `one`.
-template <int DP, int R, int NS, bool kMany>
+template <int DP, int R, int NS, bool kMany, bool kBF>
 __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
                int nmany, int* ticket) {
     using S = BStage<DP>;
-    using M = SplitSmem<DP, R>;
+    using M = SplitSmem<DP, R, kBF>;
     __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
     __shared__ __align__(8) unsigned long long bbar[NS][S::kSlots];
     __shared__ __align__(8) unsigned long long cfull[NS][kCostSlots];
@@ -459,7 +653,10 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
     const int w = role == 0 ? wid : (role == 1 ? wid - NS : 0);  // strip slot
     unsigned char* mine = dyn + (size_t)w * M::kStripBytes;
-    const unsigned cring_s = smem_u32(mine + S::kWarpBytes);
+    const unsigned cring_s = smem_u32(mine + M::kOperandBytes);
+    const unsigned a_s = smem_u32(mine);                                  // kBF: A tile
+    const unsigned b_s = smem_u32(mine + 32 * R * kBfStride * 2);         // kBF: B ring
+    unsigned bbase = 0;  // kBF: lifetime count of this cost warp's B blocks
     const unsigned cfull_s = smem_u32(&cfull[w][0]);
     const unsigned cempty_s = smem_u32(&cempty[w][0]);
 
@@ -536,10 +733,16 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
         const int strip = g * NS + w;
         if (role == 0) {
             if (w < gr.nstrips_here)
-                run_cost<DP, R>(p, strip, lane, cring_s, cfull_s, cempty_s, csub[w], br);
+            {
+                if constexpr (kBF)
+                    run_cost_bf16<DP, R>(p, strip, lane, a_s, b_s, smem_u32(&bbar[w][0]), bbase,
+                                         cring_s, cfull_s, cempty_s, csub[w]);
+                else
+                    run_cost<DP, R>(p, strip, lane, cring_s, cfull_s, cempty_s, csub[w], br);
+            }
         } else if (role == 1) {
             if (w < gr.nstrips_here)
-                run_dp<R, NS>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                run_dp<R, NS, kBF>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
                               smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s, cfull_s,
                               cempty_s, csub[w]);
         } else if (role == 2) {
@@ -560,26 +763,26 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     }
 }
 
-template <int DP, int R, bool kMany>
+template <int DP, int R, bool kMany, bool kBF = false>
 cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
                      int* ticket, int num_sms, cudaStream_t s) {
     constexpr int NS = kSplitStrips;
     constexpr int kThreads = (2 * NS + 2) * 32;
-    const int smem = NS * SplitSmem<DP, R>::kStripBytes;
+    const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS, kMany>,
+        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS, kMany, kBF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm,
-                                                          k_dp_split<DP, R, NS, kMany>, kThreads,
+                                                          k_dp_split<DP, R, NS, kMany, kBF>, kThreads,
                                                           smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int grid = blocks_per_sm * num_sms;
     if (grid > items) grid = items;
-    k_dp_split<DP, R, NS, kMany><<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
+    k_dp_split<DP, R, NS, kMany, kBF><<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
     return cudaGetLastError();
 }
 
@@ -623,6 +826,17 @@ cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, in
                                  int* ticket, int dp, int R, int num_sms, cudaStream_t s) {
     if (n <= 0 || total_items <= 0) return cudaSuccess;
     return launch_any<true>(DpArgs{}, many, item0, n, total_items, ticket, dp, R, num_sms, s);
+}
+
+bool split_bf16_supported(int dp) { return dp == 64 || dp == 128; }
+
+cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s) {
+    if (dp == 64) return launch_t<64, 3, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr,
+                                                      num_sms, s);
+    if (dp == 128)
+        return launch_t<128, 3, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms,
+                                             s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace pardtw

@@ -6,6 +6,8 @@
 // fused multiply-add per feature, in feature order.  The DP kernel computes
 // the cost of each cell the same way on the fly (Sec. II-D: the cost
 // matrix is never stored); dtw_cost materialises it for inspection.
+#include <cuda_bf16.h>
+
 #include "pardtw_common.cuh"
 
 namespace pardtw {
@@ -86,6 +88,37 @@ cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B,
     const int threads = 256;
     k_normalise<<<(n + threads - 1) / threads, threads, 0, s>>>(A, La, La_pad, B, Lb, Lb_pad, D,
                                                                 dp, Ahat, Bt, ctl);
+    return cudaGetLastError();
+}
+
+// One warp per frame of B: normalise in FP32 (the same sum of squares and
+// reciprocal square root as k_normalise), round each feature to bf16.
+__global__ void k_pack_b_bf16(const float* __restrict__ B, int Lb, int Lb_pad, int D,
+                              __nv_bfloat16* __restrict__ Bbf) {
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (f >= Lb_pad) return;
+    float r = 0.f;
+    if (f < Lb && lane == 0) {
+        float ss = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float v = B[(size_t)f * D + d];
+            ss = fmaf(v, v, ss);
+        }
+        r = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int d = lane; d < kBfStride; d += 32) {
+        const float v = (f < Lb && d < D) ? B[(size_t)f * D + d] * r : 0.f;
+        Bbf[(size_t)f * kBfStride + d] = __float2bfloat16_rn(v);
+    }
+}
+
+cudaError_t launch_pack_b_bf16(const float* B, int Lb, int Lb_pad, int D, void* Bbf,
+                               cudaStream_t s) {
+    const int warps = 8;
+    k_pack_b_bf16<<<(Lb_pad + warps - 1) / warps, warps * 32, 0, s>>>(
+        B, Lb, Lb_pad, D, static_cast<__nv_bfloat16*>(Bbf));
     return cudaGetLastError();
 }
 

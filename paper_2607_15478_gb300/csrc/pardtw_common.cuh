@@ -15,6 +15,10 @@ constexpr int kRowsPerStrip = 30;   // rows of A per warp: lanes 0..29 (lanes 30
 constexpr int kColsPerWord = 16;    // 2-bit codes per uint32 backpointer word
 constexpr int kWarpsPerGroup = 4;   // strips per CTA ("strip group") of the one-warp kernels
 constexpr int kSplitStrips = 2;     // strips per CTA of the cost/DP warp-pair kernel
+// BF16 cost (tensor cores): a frame of B (or row of A) takes kBfStride bf16
+// in memory, 128 features and 8 of padding, so that the 8 rows an ldmatrix
+// reads start 272 bytes apart, in 8 different bank groups.
+constexpr int kBfStride = 136;
 
 // Device status words (workspace).  [0] first error (DTW_* code), [1] detail,
 // [2] ticket counter of the persistent DP kernel, [3] spare.
@@ -29,6 +33,8 @@ struct DevCtl {
 struct DpArgs {
     const float* Ahat;              // nstrips*30 x dp, row-normalised, rows >= La are zero
     const float* Bhat;              // row-normalised B, chunk-transposed (see bt_index)
+    const void* Bbf;                // BF16 cost only: normalised B as bf16, frame-major,
+                                    // kBfStride elements per frame (else null)
     uint32_t* bp;                   // nstrips * nchunk * 32 words (strip, chunk, row in strip)
     unsigned long long* gborder;    // ngroups * Lb * 2 tagged values (group bottom rows)
     DevCtl* ctl;
@@ -109,6 +115,14 @@ bool multirow_supported(int dp, int R);
 // kSplitStrips strips per CTA; R = 2, 3 or 4.
 cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 bool split_supported(int dp, int R);
+// The same DP with the cost from BF16 features and FP32 accumulation on the
+// tensor cores (mma.sync m16n8k16): D padded to 64 or 128, R = 3.
+cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s);
+bool split_bf16_supported(int dp);
+// B normalised and stored as bf16 for the BF16 cost: Lb_pad frames of
+// kBfStride elements (features beyond D and frames beyond Lb are zero).
+cudaError_t launch_pack_b_bf16(const float* B, int Lb, int Lb_pad, int D, void* Bbf,
+                               cudaStream_t s);
 // Many pairs in one persistent launch: `many` (device) holds n DpArgs, item0
 // (device, n + 1 ints) the prefix sums of their strip-group counts; CTAs take
 // (pair, group) items from *ticket in that order, so a group only waits on
@@ -122,6 +136,7 @@ cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, in
 // R rows per lane, spg strips per CTA (strip group).
 struct DpPlan {
     int kind, R, spg;
+    int bf16;  // kind 2 only: the cost on the tensor cores from BF16 features
 };
 DpPlan choose_plan(int La, int dp, const dtw_options& o, int num_sms);
 cudaError_t launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,

@@ -28,6 +28,7 @@ DTW_ERR_TIMEOUT = 5
 DTW_ERR_UNSUPPORTED = 6
 DTW_ERR_SCRATCH_LIMIT = 7
 DTW_COST_FP32 = 0
+DTW_COST_BF16 = 1
 
 # every entry point include/pardtw.h declares
 EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destroy",
@@ -97,9 +98,10 @@ def status_string(status: int) -> str:
 
 def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
                  debug_skip_publish: int = -1, rows_per_lane: int = 0,
-                 dp_schedule: int = SCHEDULE_AUTO) -> Options:
+                 dp_schedule: int = SCHEDULE_AUTO, cost_precision: int = DTW_COST_FP32) -> Options:
     o = Options()
     load_library().dtw_default_options(ctypes.byref(o))
+    o.cost_precision = int(cost_precision)
     o.cost_shift = float(cost_shift)
     o.wait_limit = int(wait_limit_us)
     o.debug_skip_publish = int(debug_skip_publish)
