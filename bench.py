@@ -350,6 +350,273 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _rank0_line(line):
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """The batching workload: 256 seeded pairs (La ~ U[500, 8000], Lb = La x
+    U[0.8, 1.25], D = 12) aligned by one dtw_align_many call (one batched
+    normalisation, one persistent DP launch over a (pair, strip group) work
+    queue, one batched backtrace).  N ranks split the pairs by cell count
+    (LPT) and align their shares independently (strong scaling)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    if rank == 0 or ws == 1:
+        pbuild.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2607_15478_gb300 import pardtw, shard, synth
+    pairs_all = synth.config_batch(2)
+    cells_all = [p.A.shape[0] * p.B.shape[0] for p in pairs_all]
+    mine = shard.partition_pairs(cells_all, ws)[rank]
+    pairs = [pairs_all[k] for k in mine]
+    cells = sum(cells_all[k] for k in mine)
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    As = [torch.from_numpy(p.A).to(dev) for p in pairs]
+    Bs = [torch.from_numpy(p.B).to(dev) for p in pairs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    st = None
+
+    def step():
+        nonlocal st
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            _, _, st = al.align_many(As, Bs)
+            ev1.record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if st is not None and (st != 0).any():
+        raise RuntimeError(f"batch alignment failed on rank {rank}")
+    step_ms, dp_ms = [], []
+    with ClockSampler(dev.index) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(args.steps):
+            step()
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            dp_ms.append(al.stage_times()[1])
+        torch.cuda.synchronize(dev)
+        clk.mark_end()
+        if ws > 1:
+            dist.barrier()
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    if ws > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = sum(cells_all) * args.steps / t_max / 1e9
+    # end to end: pinned host features in, costs, lengths and paths out
+    Ah = [torch.from_numpy(p.A).pin_memory() for p in pairs]
+    Bh = [torch.from_numpy(p.B).pin_memory() for p in pairs]
+    al.enable_timing(False)
+    e2e_t, h2d, d2h = [], 0, 0
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            Ad = [a.to(dev, non_blocking=True) for a in Ah]
+            Bd = [b.to(dev, non_blocking=True) for b in Bh]
+            paths, costs, st2 = al.align_many(Ad, Bd)
+            out = [q.cpu() for q in paths if q is not None]
+        e2e_t.append(time.perf_counter() - t0)
+        h2d = sum(a.numel() * 4 for a in Ah) + sum(b.numel() * 4 for b in Bh)
+        d2h = sum(q.numel() * 4 for q in out) + 8 * len(pairs)
+    t_e2e = sum(e2e_t[args.warmup:])
+    if ws > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    if rank == 0:
+        peaks, src = measured_peaks()
+        clock = peaks.get("sm_max_mhz", 2070.0)
+        peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6
+        dp_avg = statistics.mean(dp_ms) / 1e3
+        achieved = cells * 18 / dp_avg
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            done = 0
+            for p in pairs_all:
+                if time.perf_counter() - t0 > 15.0:
+                    break
+                oracle.dtw(p.A, p.B)
+                done += p.A.shape[0] * p.B.shape[0]
+            dt = time.perf_counter() - t0
+            cpu = {"value": done / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the first pairs of the batch, one after another, until 15 s "
+                             f"({done / 1e9:.2f} Gcells in {dt:.1f} s), single-threaded FP64"}
+        _rank0_line({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch-256-pairs La~U[500,8000] Lb=La*U[0.8,1.25] D=12 "
+                                   "chroma-like, warped (8 knots)",
+                       "pairs": len(pairs_all), "cells": sum(cells_all), "D": 12,
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"pairs split by cell count over {ws} rank(s)"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
+                         "traffic": None,
+                         "kernel": "k_dp_split, batch mode (work queue over pairs)",
+                         "ops_per_cell": 18, "dp_ms": 1e3 * dp_avg,
+                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                       f"{clock:.0f} MHz (sm_max_mhz, {src})"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary(),
+        })
+    al.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_precision(args):
+    """The precision workload: the 40000x128 vs 48000x128 pair with the cost
+    from bf16 features on the tensor cores (FP32 accumulate, FP32 DP); the
+    FP32 cost path is timed once beside it, and the errors against it and
+    against the FP64 oracle (on a 2000x2400 pair of the same recipe) are
+    reported."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2607_15478_gb300 import pardtw, synth
+    wp = synth.config_pair(3, pair=rank)
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    cells = La * Lb
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    A = torch.from_numpy(wp.A).to(dev)
+    B = torch.from_numpy(wp.B).to(dev)
+    cap = min(La, Lb)
+    path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    plen = torch.zeros(1, dtype=torch.int32, device=dev)
+    tot = torch.zeros(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def step(prec):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            al.align_into(A, B, path, plen, tot, cost_precision=prec)
+            ev1.record(stream)
+
+    for _ in range(args.warmup):
+        step(1)
+    step_ms, dp_ms = [], []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(args.steps):
+            step(1)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            dp_ms.append(al.stage_times()[1])
+        clk.mark_end()
+    t = sum(step_ms) / 1e3
+    value = cells * args.steps / t / 1e9
+    tot_bf, path_bf = float(tot.item()), path[:int(plen.item())].cpu().numpy()
+    step(0)  # the FP32 cost path once, for comparison
+    ev1.synchronize()
+    fp32_ms = ev0.elapsed_time(ev1)
+    tot_f32, path_f32 = float(tot.item()), path[:int(plen.item())].cpu().numpy()
+    # e2e: host features in, path out
+    Ah = torch.from_numpy(wp.A).pin_memory()
+    Bh = torch.from_numpy(wp.B).pin_memory()
+    ph = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
+    lh = torch.zeros(1, dtype=torch.int32).pin_memory()
+    th = torch.zeros(1, dtype=torch.float32).pin_memory()
+    al.enable_timing(False)
+    opts = pardtw.make_options(cost_precision=1)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pardtw.dtw_align(al.h, Ah, Bh, ph, lh, th, opts)
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = sum(e2e_t[args.warmup:])
+    # error against the FP64 oracle on a smaller pair of the same recipe
+    import oracle
+    oracle.build()
+    sp = synth.config_pair(3, La=2000, Lb=2400)
+    pb, tb = al.align(torch.from_numpy(sp.A).to(dev), torch.from_numpy(sp.B).to(dev),
+                      cost_precision=1)
+    po, to = oracle.dtw(sp.A, sp.B)
+    pbn = pb.cpu().numpy()
+    tg = oracle.path_cost(sp.A, sp.B, pbn)
+
+    def jbar(pp, n):
+        acc, cnt = np.zeros(n), np.zeros(n)
+        np.add.at(acc, pp[:, 0], pp[:, 1])
+        np.add.at(cnt, pp[:, 0], 1)
+        rows = np.flatnonzero(cnt)
+        return np.interp(np.arange(n), rows, acc[rows] / cnt[rows])
+    dev_frames = float(np.mean(np.abs(jbar(pbn, 2000) - jbar(po, 2000))))
+    dev_full = float(np.mean(np.abs(jbar(path_bf, La) - jbar(path_f32, La))))
+    peaks, src = measured_peaks()
+    dp_avg = statistics.mean(dp_ms) / 1e3
+    tflops = cells * 2 * 128 / dp_avg / 1e12
+    peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    _rank0_line({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 cost (f32 accumulate), f32 DP",
+        "data": "synthetic",
+        "config": {"workload": "pair-40000x128-vs-48000x128 gaussian frames, L2-normalised, "
+                               "warped (64 knots) + N(0,0.1)", "La": La, "Lb": Lb, "D": D,
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU"},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": tflops / peak_tf, "traffic": None,
+                     "kernel": "k_dp_split BF16 (cost warps: mma.sync m16n8k16; DP warps FP32)",
+                     "dp_ms": 1e3 * dp_avg,
+                     "note": "cost contraction flops (2 x 128 per cell) over the DP launch; the "
+                             "launch is bound by the DP recurrence, not the tensor pipe"},
+        "precision": {"fp32_cost_step_ms": fp32_ms, "speedup_vs_fp32_cost": fp32_ms / (1e3 * t / args.steps),
+                      "total_rel_diff_vs_fp32": abs(tot_bf - tot_f32) / abs(tot_f32),
+                      "mean_path_deviation_vs_fp32_frames": dev_full,
+                      "oracle_pair": "2000x2400, same recipe",
+                      "total_rel_error_vs_fp64": abs(tb - to) / abs(to),
+                      "path_cost_rel_excess_vs_fp64": (tg - to) / abs(to),
+                      "mean_path_deviation_vs_fp64_frames": dev_frames},
+        "cpu_baseline": None,
+        "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": int(lh[0]) * 8 + 8},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk.summary(),
+    })
+    al.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,11 +627,18 @@ def main():
     ap.add_argument("--La", type=int, default=None,
                     help="override the pair's lengths (same recipe; for profiling smaller cases)")
     ap.add_argument("--Lb", type=int, default=None)
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3],
+                    help="1: the 20000x25000 pair (default, the headline line); 2: the "
+                         "256-pair batch; 3: the D = 128 pair with the BF16 cost")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 2:
+        run_batch(args)
+    elif args.config == 3:
+        run_precision(args)
     else:
         run_ours(args)
 

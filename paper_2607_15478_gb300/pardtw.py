@@ -244,6 +244,19 @@ class Aligner:
     def __exit__(self, *a):
         self.close()
 
+    def _enter(self):
+        """The handle's stream waits for the work queued so far on torch's current
+        stream (the inputs), so that a handle with its own stream sees them."""
+        if self._stream is not None:
+            import torch
+            self._stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        """torch's current stream waits for the handle's work (the outputs)."""
+        if self._stream is not None:
+            import torch
+            torch.cuda.current_stream(self.device).wait_stream(self._stream)
+
     def enable_timing(self, on: bool = True):
         _check(load_library().dtw_enable_timing(self.h, int(on)), "dtw_enable_timing")
 
@@ -257,12 +270,16 @@ class Aligner:
         A, B = _features(A), _features(B)
         C = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32,
                         device=A.device if A.is_cuda else self.device)
+        self._enter()
         dtw_cost(self.h, A, B, C)
+        self._leave()
         return C
 
     def align_into(self, A, B, path, path_len, total, **opts):
         """Asynchronous form: all outputs are caller-owned device tensors."""
+        self._enter()
         dtw_align(self.h, A, B, path, path_len, total, make_options(**opts) if opts else None)
+        self._leave()
 
     def align(self, A, B, **opts):
         """Return (path as an (n, 2) int32 tensor on the device, total cost as float)."""
@@ -273,7 +290,9 @@ class Aligner:
         path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
         plen = torch.zeros(1, dtype=torch.int32, device=dev)
         tot = torch.zeros(1, dtype=torch.float32, device=dev)
+        self._enter()
         dtw_align(self.h, A, B, path, plen, tot, make_options(**opts) if opts else None)
+        self._leave()
         n = int(plen.item())
         if n < 0:
             raise PardtwError(-n, "dtw_align (device)")
@@ -289,8 +308,10 @@ class Aligner:
         plen = torch.zeros(n, dtype=torch.int32, device=self.device)
         cost = torch.zeros(n, dtype=torch.float32, device=self.device)
         status = torch.zeros(n, dtype=torch.int32, device=self.device)
+        self._enter()
         dtw_align_many(self.h, As, Bs, paths, off, plen, cost, status,
                        make_options(**opts) if opts else None)
+        self._leave()
         plen_h = plen.cpu().numpy()
         st = status.cpu().numpy()
         out = []

@@ -276,3 +276,16 @@ def test_exact_ties_every_decomposition(aligner, R, sched):
     po, to = oracle.dtw(A, B)
     assert total == to
     np.testing.assert_array_equal(path.cpu().numpy(), po)
+
+
+def test_aligner_on_its_own_stream(aligner):
+    # a handle bound to a side stream: the convenience calls order that stream
+    # after the inputs and torch's stream after the outputs
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.config_pair(0)
+    side = torch.cuda.Stream()
+    with pardtw.Aligner(0, side) as al2:
+        for _ in range(3):
+            A, B = dev(wp.A), dev(wp.B)
+            path, total = al2.align(A, B)
+            assert_parity(wp.A, wp.B, path, total)
