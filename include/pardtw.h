@@ -164,6 +164,28 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
                    int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
                    int* status);
 
+/* ---- banded alignment ------------------------------------------------------ */
+/* Exact DTW inside a band found at a coarser scale.  The paper notes that
+ * bands and multiscale DTW cut the quadratic cost (Sec. II); this entry
+ * point builds the band from the exact alignment of A and B averaged over
+ * `downsample` frames: every row i of the fine problem keeps the columns
+ * within `halfwidth` of the coarse path scaled by `downsample` (rounded out
+ * to whole strips of rows and 8-column blocks), and the exact DP (Sec. V
+ * recurrence, steps, weights and tie order) runs inside that band.  If the
+ * best path inside the band comes within one block of a side of the band
+ * (other than the matrix's own sides), the band may have cut off a better
+ * path, and the full exact DTW runs instead; *fell_back then reads 1.
+ *
+ *   A, B, path, path_len, total_cost : device pointers (total_cost may be
+ *       NULL), as in dtw_align; D <= 32 and FP32 cost
+ *   downsample >= 1, halfwidth >= 0 (in fine frames)
+ *   fell_back : host int (may be NULL)
+ * The call synchronises the handle's stream (to read the band-side test).
+ * Returns DTW_ERR_UNSUPPORTED for D > 32 or a BF16 cost. */
+int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                     const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
+                     int cap, int* path_len, float* total_cost, int* fell_back);
+
 /* ---- alignment without device allocation ---------------------------------- */
 /* The paper has no counterpart of this entry point; it is a service of this
  * library.  Some callers cannot allocate device memory while they align: a

@@ -31,6 +31,8 @@ struct dtw_handle {
     bool timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int* h_small = nullptr;      // pinned host: [0] path_len, [1] total bits
+    char* band = nullptr;        // dtw_align_banded: pooled inputs, coarse path, ranges
+    size_t band_cap = 0;
 };
 
 namespace {
@@ -208,8 +210,13 @@ dtw_options defaults() {
 // One pair, all the way to device-resident outputs.  `out_path`,
 // `out_len`, `out_total` are device pointers (out_total may be null).
 int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
-                 const dtw_options& o, int32_t* out_path, int* out_len, float* out_total) {
-    const Layout L = make_layout(La, Lb, D, choose_plan(La, padded_dim(D), o, h->num_sms));
+                 const dtw_options& o, int32_t* out_path, int* out_len, float* out_total,
+                 const int2* ranges = nullptr) {
+    // a band (per-strip column ranges) needs the warp-pair kernel at 3 rows
+    // per lane, FP32 cost
+    const DpPlan plan = ranges ? DpPlan{2, 3, kSplitStrips}
+                               : choose_plan(La, padded_dim(D), o, h->num_sms);
+    const Layout L = make_layout(La, Lb, D, plan);
     int rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     cudaStream_t s = h->stream;
@@ -243,6 +250,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     a.Ahat = Ahat;
     a.Bhat = Bhat;
     a.Bbf = Bbf;
+    a.ranges = ranges;
     a.bp = bp;
     a.gborder = h->border;
     a.ctl = ctl;
@@ -276,6 +284,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     bt.path_len = out_len;
     bt.total = out_total;
     bt.scratch = ws + L.off_bt;
+    bt.ranges = ranges;
     CU(launch_backtrace_bands(bt, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
@@ -369,6 +378,7 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         a.Ahat = Ahat;
         a.Bhat = Bhat;
         a.Bbf = nullptr;
+        a.ranges = nullptr;
         a.bp = bpw;
         a.gborder = h->border + boff[q] / sizeof(unsigned long long);
         a.ctl = ctl;
@@ -399,6 +409,7 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         bt.path_len = path_len + k;
         bt.total = cost ? cost + k : nullptr;
         bt.scratch = base + L.off_bt;
+        bt.ranges = nullptr;
     }
     CU(cudaMemcpyAsync(ws + off_dp, dps.data(), sizeof(DpArgs) * m, cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(ws + off_norm, nas.data(), sizeof(NormArgs) * m, cudaMemcpyHostToDevice,
@@ -484,6 +495,7 @@ int dtw_destroy(dtw_handle* h) {
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     if (h->border) cudaFree(h->border);
+    if (h->band) cudaFree(h->band);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->h_small) cudaFreeHost(h->h_small);
@@ -690,6 +702,77 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
         CU(cudaMemcpy(status, hst.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     else
         memcpy(status, hst.data(), sizeof(int) * n);
+    return DTW_OK;
+}
+
+int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                     const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
+                     int cap, int* path_len, float* total_cost, int* fell_back) {
+    if (!h || !path || !path_len || downsample < 1 || halfwidth < 0) return DTW_ERR_INVALID;
+    int rc = validate(A, La, B, Lb, D);
+    if (rc != DTW_OK) return rc;
+    if (cap < std::min(La, Lb)) return DTW_ERR_INVALID;
+    const dtw_options o = opt ? *opt : defaults();
+    if (o.cost_precision != DTW_COST_FP32 || !split_supported(padded_dim(D), 3))
+        return DTW_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(path) ||
+        !is_device_ptr(path_len) || (total_cost && !is_device_ptr(total_cost)))
+        return DTW_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    if (fell_back) *fell_back = 0;
+    const int Lac = (La + downsample - 1) / downsample, Lbc = (Lb + downsample - 1) / downsample;
+    if (downsample == 1 || !reachable(Lac, Lbc)) {
+        if (fell_back) *fell_back = 1;
+        return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
+    }
+    const int rps = strip_rows(3);
+    const int nstrips = (La + rps - 1) / rps;
+    const int capc = std::min(Lac, Lbc);
+    // band buffer: pooled A and B, coarse path and length, ranges, touch flag
+    const size_t off_pa = 0;
+    const size_t off_pb = align256(off_pa + (size_t)Lac * D * sizeof(float));
+    const size_t off_cp = align256(off_pb + (size_t)Lbc * D * sizeof(float));
+    const size_t off_cl = align256(off_cp + (size_t)2 * capc * sizeof(int32_t));
+    const size_t off_rg = align256(off_cl + 16);
+    const size_t off_tc = align256(off_rg + (size_t)nstrips * sizeof(int2));
+    const size_t need = off_tc + 256;
+    if (need > h->band_cap) {
+        CU(cudaStreamSynchronize(s));
+        if (h->band) cudaFree(h->band);
+        h->band = nullptr;
+        h->band_cap = 0;
+        if (cudaMalloc(&h->band, need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->band = nullptr;
+            return DTW_ERR_OOM;
+        }
+        h->band_cap = need;
+    }
+    float* pa = reinterpret_cast<float*>(h->band + off_pa);
+    float* pb = reinterpret_cast<float*>(h->band + off_pb);
+    int32_t* cpath = reinterpret_cast<int32_t*>(h->band + off_cp);
+    int* clen = reinterpret_cast<int*>(h->band + off_cl);
+    int2* ranges = reinterpret_cast<int2*>(h->band + off_rg);
+    int* touch = reinterpret_cast<int*>(h->band + off_tc);
+    // 1. the coarse pair and its exact alignment
+    CU(launch_pool(A, La, D, downsample, pa, s));
+    CU(launch_pool(B, Lb, D, downsample, pb, s));
+    rc = align_device(h, pa, Lac, pb, Lbc, D, o, cpath, clen, nullptr);
+    if (rc != DTW_OK) return rc;
+    // 2. the band and the exact DP inside it
+    CU(launch_band_ranges(cpath, clen, downsample, halfwidth, La, Lb, nstrips, rps, ranges, s));
+    rc = align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost, ranges);
+    if (rc != DTW_OK) return rc;
+    // 3. a path at the band's side: the full exact DP instead
+    CU(launch_band_touch(path, path_len, std::min(La, Lb), Lb, rps, ranges, touch, s));
+    CU(cudaMemcpyAsync(h->h_small + 2, touch, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h->h_small[2]) {
+        if (fell_back) *fell_back = 1;
+        return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
+    }
     return DTW_OK;
 }
 

@@ -1,0 +1,121 @@
+// Band for the multiscale exact alignment (dtw_align_banded).  The paper
+// mentions bands and multiscale DTW as ways to cut the quadratic cost
+// (Sec. II); this library builds the band from an exact alignment of the two
+// sequences averaged over `ds` frames, and the exact DP then runs inside it.
+//
+//   k_pool         average of each window of ds frames (the last window may
+//                  be shorter)
+//   k_band_ranges  per strip of the fine DP, the 8-column blocks within
+//                  `w` columns of the upsampled coarse path over the strip's
+//                  rows, widened to be monotone in the strip (the banded DP
+//                  needs the start and the end of the ranges non-decreasing)
+//   k_band_touch   whether the banded path comes within one block of a side
+//                  of the band that is not the side of the matrix (the band
+//                  may then have cut off a better path: the caller falls back
+//                  to the full exact DP)
+#include "pardtw_common.cuh"
+
+namespace pardtw {
+
+namespace {
+
+__global__ void k_pool(const float* __restrict__ X, int L, int D, int ds, float* __restrict__ Y) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Lc = (L + ds - 1) / ds;
+    if (t >= Lc * D) return;
+    const int c = t / D, d = t - c * D;
+    const int f0 = c * ds, f1 = min(f0 + ds, L);
+    float acc = 0.f;
+    for (int f = f0; f < f1; ++f) acc += X[(size_t)f * D + d];
+    Y[(size_t)c * D + d] = acc / (float)(f1 - f0);
+}
+
+// One thread per strip (k_band_monotone then widens the ranges to monotone).
+__global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __restrict__ clen,
+                              int ds, int w, int La, int Lb, int nstrips, int rps,
+                              int2* __restrict__ ranges) {
+    const int n = *clen;
+    const int nsub = (Lb + 7) / 8;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n <= 0) {  // the coarse alignment failed: every strip sweeps all columns
+        if (s < nstrips) ranges[s] = make_int2(0, nsub);
+        return;
+    }
+    if (s < nstrips) {
+        const int r0 = s * rps, r1 = min(r0 + rps, La) - 1;
+        // coarse rows around the strip's rows (a (2,1) step may skip one)
+        const int icl = r0 / ds - 1, ich = r1 / ds + 1;
+        int lo = 0, hi = n;  // first path entry with row >= icl
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cpath[2 * mid] < icl)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int jmin = 0x7fffffff, jmax = -1;
+        for (int k = lo; k < n && cpath[2 * k] <= ich; ++k) {
+            jmin = min(jmin, cpath[2 * k + 1]);
+            jmax = max(jmax, cpath[2 * k + 1]);
+        }
+        if (jmax < 0) {  // cannot happen for a path covering every coarse row
+            jmin = 0;
+            jmax = (Lb - 1) / ds;
+        }
+        const int jlo = max(jmin * ds - w, 0);
+        const int jhi = min((jmax + 1) * ds - 1 + w, Lb - 1);
+        int x = (jlo / 8) & ~1;           // even: whole 16-column words
+        int y = min((jhi + 8) / 8, nsub);
+        if (s == 0) x = 0;
+        if (s == nstrips - 1) y = nsub;
+        ranges[s] = make_int2(x, y);
+    }
+}
+
+// Widen the ranges to monotone: starts by a suffix minimum, ends by a
+// prefix maximum (one thread; a few thousand strips at most).
+__global__ void k_band_monotone(int nstrips, int2* __restrict__ ranges) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int q = nstrips - 2; q >= 0; --q) ranges[q].x = min(ranges[q].x, ranges[q + 1].x);
+    for (int q = 1; q < nstrips; ++q) ranges[q].y = max(ranges[q].y, ranges[q - 1].y);
+}
+
+__global__ void k_band_touch(const int32_t* __restrict__ path, const int* __restrict__ plen,
+                             int Lb, int rps, const int2* __restrict__ ranges,
+                             int* __restrict__ touch) {
+    const int n = *plen;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && n <= 0) atomicOr(touch, 1);  // no path inside the band
+    if (k >= n) return;
+    const int i = path[2 * k], j = path[2 * k + 1];
+    const int2 r = ranges[i / rps];
+    const int x8 = r.x * 8, y8 = min(r.y * 8, Lb);
+    if ((x8 > 0 && j < x8 + 8) || (y8 < Lb && j >= y8 - 8)) atomicOr(touch, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStream_t s) {
+    const int n = ((L + ds - 1) / ds) * D;
+    k_pool<<<(n + 255) / 256, 256, 0, s>>>(X, L, D, ds, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w, int La,
+                               int Lb, int nstrips, int rps, int2* ranges, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (nstrips + threads - 1) / threads;
+    k_band_ranges<<<blocks, threads, 0, s>>>(cpath, clen, ds, w, La, Lb, nstrips, rps, ranges);
+    k_band_monotone<<<1, 32, 0, s>>>(nstrips, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
+                              const int2* ranges, int* touch, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(touch, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_band_touch<<<(cap + 255) / 256, 256, 0, s>>>(path, plen, Lb, rps, ranges, touch);
+    return cudaGetLastError();
+}
+
+}  // namespace pardtw

@@ -71,11 +71,19 @@ __host__ __device__ inline BtScratch bt_scratch(void* scratch, int La, int Lb) {
 // the two left-neighbour columns a thread needs come through shared memory.
 // One row of the band map for a thread's 16 columns.  kTop: the row is one
 // of the band's first two rows, whose predecessors may lie in the band above.
-template <bool kTop>
+template <bool kTop, bool kBanded>
 __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int Lb, int jb, int c0,
                                             int width, int b, uint32_t word, int t,
                                             int (*s_x)[kSegThreads][3], int* e1, int* e2,
-                                            int2* __restrict__ exits, int* __restrict__ end_entry) {
+                                            int2* __restrict__ exits, int* __restrict__ end_entry,
+                                            const int2* __restrict__ ranges, int rps) {
+    // banded DP: cells outside the row's strip range were never computed
+    int cx = 0, cy = 0;
+    if (kBanded) {
+        const int2 r = __ldg(ranges + i / rps);
+        cx = r.x * 8;
+        cy = r.y * 8;
+    }
     const int par = i & 1;
     s_x[par][t][0] = e1[kColsPerWord - 2];
     s_x[par][t][1] = e1[kColsPerWord - 1];
@@ -108,6 +116,7 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
         }
         int v = f11 ? p11 : (f12 ? p12 : p21);
         if (kTop && i == 0 && jb + q == 0) v = kOrigin;
+        if (kBanded && (jb + q < cx || jb + q >= cy)) v = kNoPath;
         en[q] = v;
     }
     // the band's last two rows are kept for the band below
@@ -139,7 +148,7 @@ constexpr int kRowsAhead = 8;  // backpointer rows loaded ahead of use
 
 // kMany: one pair per blockIdx.z, from the array `many` (the grid covers the
 // largest pair; blocks beyond a pair's bands or columns leave at once).
-template <bool kMany>
+template <bool kMany, bool kBanded>
 __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
                                                          const BtArgs* __restrict__ many) {
     const BtArgs& a = kMany ? many[blockIdx.z] : one;
@@ -158,6 +167,12 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
     if (b >= sc.nbands || c0 >= Lb) return;  // CTA-uniform
     const int r0 = b * band;
     const int r1 = min(r0 + band, La);
+    if (kBanded) {
+        // the band's columns over these rows (ranges are monotone in the strip)
+        const int xs = a.ranges[r0 / rps].x * 8, ys = a.ranges[(r1 - 1) / rps].y * 8;
+        const int halo0 = (c0 == 0) ? 0 : 2 * band;
+        if (c0 + width <= xs || c0 - halo0 >= ys) return;  // CTA-uniform
+    }
     const int halo = (c0 == 0) ? 0 : 2 * band;  // multiple of 16
     const int s0 = c0 - halo;
     const int t = threadIdx.x;
@@ -176,11 +191,11 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
     uint32_t wq[kRowsAhead];
 #pragma unroll
     for (int u = 0; u < kRowsAhead; ++u) wq[u] = load(r0 + 2 + u);
-    bandmap_row<true>(r0, r0, r1, La, Lb, jb, c0, width, b, top0, t, s_x, e1, e2, exits,
-                      end_entry);
+    bandmap_row<true, kBanded>(r0, r0, r1, La, Lb, jb, c0, width, b, top0, t, s_x, e1, e2,
+                               exits, end_entry, a.ranges, rps);
     if (r0 + 1 < r1)
-        bandmap_row<true>(r0 + 1, r0, r1, La, Lb, jb, c0, width, b, top1, t, s_x, e1, e2, exits,
-                          end_entry);
+        bandmap_row<true, kBanded>(r0 + 1, r0, r1, La, Lb, jb, c0, width, b, top1, t, s_x, e1,
+                                   e2, exits, end_entry, a.ranges, rps);
     // the rest, kRowsAhead at a time, loading the next group meanwhile
     for (int i = r0 + 2; i < r1; i += kRowsAhead) {
         uint32_t wn[kRowsAhead];
@@ -189,8 +204,8 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
 #pragma unroll
         for (int u = 0; u < kRowsAhead; ++u)
             if (i + u < r1)
-                bandmap_row<false>(i + u, r0, r1, La, Lb, jb, c0, width, b, wq[u], t, s_x, e1, e2,
-                                   exits, end_entry);
+                bandmap_row<false, kBanded>(i + u, r0, r1, La, Lb, jb, c0, width, b, wq[u], t,
+                                            s_x, e1, e2, exits, end_entry, a.ranges, rps);
 #pragma unroll
         for (int u = 0; u < kRowsAhead; ++u) wq[u] = wn[u];
     }
@@ -367,7 +382,10 @@ cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s) {
     const int nbands = (a.La + kBand - 1) / kBand;
     const int width = kSegCols - 2 * kBand;
     dim3 grid((unsigned)((a.Lb + width - 1) / width), (unsigned)nbands, 1);
-    k_bandmap<false><<<grid, kSegThreads, 0, s>>>(a, nullptr);
+    if (a.ranges)
+        k_bandmap<false, true><<<grid, kSegThreads, 0, s>>>(a, nullptr);
+    else
+        k_bandmap<false, false><<<grid, kSegThreads, 0, s>>>(a, nullptr);
     k_bt_chain<false><<<1, 32, 0, s>>>(a, nullptr);
     k_bt_walk<false><<<(nbands + 3) / 4, 128, 0, s>>>(a, nullptr);
     k_bt_emit<false><<<1, 256, (nbands + 1) * sizeof(int), s>>>(a, nullptr);
@@ -380,7 +398,7 @@ cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, in
     const int nbands = (maxLa + kBand - 1) / kBand;
     const int width = kSegCols - 2 * kBand;
     dim3 grid((unsigned)((maxLb + width - 1) / width), (unsigned)nbands, (unsigned)n);
-    k_bandmap<true><<<grid, kSegThreads, 0, s>>>(BtArgs{}, many);
+    k_bandmap<true, false><<<grid, kSegThreads, 0, s>>>(BtArgs{}, many);
     k_bt_chain<true><<<n, 32, 0, s>>>(BtArgs{}, many);
     k_bt_walk<true><<<dim3((unsigned)((nbands + 3) / 4), (unsigned)n), 128, 0, s>>>(BtArgs{},
                                                                                      many);

@@ -253,16 +253,24 @@ struct BRing {
     const float* stage;   // this warp's kSlots * kBlk frames
     unsigned stage_s;     // its shared address
     unsigned bar_s;       // shared address of this warp's kSlots mbarriers
-    unsigned base;        // lifetime block number of block 0 of the current strip
-    int nblk;             // blocks in the current strip (ceil(Lb / kBlk))
-    int issued;           // blocks of this strip issued so far
+    unsigned base;        // lifetime block number of block `first` of the current strip
+    int first;            // first block of B the current strip reads
+    int nblk;             // blocks of B up to the end of the strip's columns
+    int issued;           // blocks of this strip issued so far (first <= issued)
     int waited;           // blocks of this strip known complete
 
     // Copy block q (frames q*kBlk .., whole 16-frame chunks) of the
     // chunk-transposed B (Lb_pad frames) into its slot.
+    // A new strip reading blocks q0 .. nb-1: the lifetime numbering continues
+    // after the blocks the previous strip issued.
+    __device__ __forceinline__ void begin(int q0, int nb) {
+        base += (unsigned)(issued - first);
+        first = issued = waited = q0;
+        nblk = nb;
+    }
     __device__ __forceinline__ void issue(int q, const float* Bt, int Lb_pad, int lane) {
         if (lane == 0) {
-            const unsigned t = base + (unsigned)q;
+            const unsigned t = base + (unsigned)(q - first);
             const int f0 = q * S::kBlk;
             const int nf = min(S::kBlk, Lb_pad - f0);
             tma_load(stage_s + (t % S::kSlots) * (S::kBlk * DP * 4), Bt + (size_t)f0 * DP,
@@ -278,7 +286,7 @@ struct BRing {
     }
     // Wait until block q is in shared memory (bounded); warp-uniform.
     __device__ __forceinline__ int wait(int q, DevCtl* ctl, long long timeout_ns) {
-        const unsigned t = base + (unsigned)q;
+        const unsigned t = base + (unsigned)(q - first);
         const unsigned bar = bar_s + (t % S::kSlots) * 8;
         const unsigned par = (t / S::kSlots) & 1u;
         if (__all_sync(kFull, mbar_try_wait(bar, par))) {
@@ -305,7 +313,7 @@ struct BRing {
     // no bulk copy is still writing this CTA's shared memory.
     __device__ __forceinline__ void drain() {
         for (int q = waited; q < issued; ++q) {
-            const unsigned t = base + (unsigned)q;
+            const unsigned t = base + (unsigned)(q - first);
             const unsigned bar = bar_s + (t % S::kSlots) * 8;
             const unsigned par = (t / S::kSlots) & 1u;
             const long long t0 = __shfl_sync(kFull, global_ns(), 0);
@@ -319,14 +327,14 @@ struct BRing {
     // Shared address of the 16 x DP feature-major values of chunk k.
     __device__ __forceinline__ unsigned chunk_s(int k) const {
         const int f = k * kColsPerWord;
-        const unsigned t = base + (unsigned)(f / S::kBlk);
+        const unsigned t = base + (unsigned)(f / S::kBlk - first);
         return stage_s +
                (unsigned)(((t % S::kSlots) * S::kBlk + (unsigned)(f % S::kBlk)) * DP * 4);
     }
     // The 16 x DP feature-major values of chunk k (its block must be complete).
     __device__ __forceinline__ const float* chunk(int k) const {
         const int f = k * kColsPerWord;
-        const unsigned t = base + (unsigned)(f / S::kBlk);
+        const unsigned t = base + (unsigned)(f / S::kBlk - first);
         return stage + ((size_t)(t % S::kSlots) * S::kBlk + (size_t)(f % S::kBlk)) * DP;
     }
 };

@@ -134,10 +134,7 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
     const bool from_global = (w == 0) && (g > 0);
 
     // B pipeline and, for warp 0 below another group, the border window
-    br.base += (unsigned)br.nblk;  // continue the lifetime block numbering
-    br.nblk = (p.nchunk * kColsPerWord + S::kBlk - 1) / S::kBlk;
-    br.issued = 0;
-    br.waited = 0;
+    br.begin(0, (p.nchunk * kColsPerWord + S::kBlk - 1) / S::kBlk);
     const int Lb_pad = p.nchunk * kColsPerWord;
     br.top_up(0, p.Bhat, Lb_pad, lane);
     unsigned long long g0 = 0, g1 = 0;
@@ -298,6 +295,7 @@ __global__ void __launch_bounds__(NW * 32, DP <= 32 ? 2 : 1) k_dp(const DpArgs p
     br.stage_s = smem_u32(bstage + (size_t)w * S::kWarpBytes);
     br.bar_s = smem_u32(&bars[w][0]);
     br.base = 0;
+    br.first = 0;
     br.nblk = 0;
     br.issued = br.waited = 0;
     if (lane == 0) {

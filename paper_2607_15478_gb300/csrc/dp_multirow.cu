@@ -96,10 +96,7 @@ __device__ __forceinline__ void run_strip(const DpArgs& p, int g, int w, int lan
 
     // B pipeline and, for warp 0 below another group, the border window
     const int Lb_pad = p.nchunk * kColsPerWord;
-    br.base += (unsigned)br.nblk;  // continue the lifetime block numbering
-    br.nblk = (Lb_pad + S::kBlk - 1) / S::kBlk;
-    br.issued = 0;
-    br.waited = 0;
+    br.begin(0, (Lb_pad + S::kBlk - 1) / S::kBlk);
     br.top_up(0, p.Bhat, Lb_pad, lane);
     unsigned long long g0 = 0, g1 = 0;
     if (from_global && lane < Lb) ldg2(gin + (size_t)lane * 2, g0, g1);
@@ -284,6 +281,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_dp_multirow(const DpArgs p) {
     br.stage_s = smem_u32(bstage + (size_t)w * S::kWarpBytes);
     br.bar_s = smem_u32(&bars[w][0]);
     br.base = 0;
+    br.first = 0;
     br.nblk = 0;
     br.issued = br.waited = 0;
     if (lane == 0) {

@@ -74,6 +74,13 @@ struct SplitSmem {
 __device__ __forceinline__ unsigned bar_at(unsigned base, unsigned slot) { return base + 8 * slot; }
 __device__ __forceinline__ unsigned use_parity(unsigned t, unsigned n) { return (t / n) & 1u; }
 
+// Sub-chunks [x, y) (columns 8x .. 8y-1) that `strip` sweeps: all of them
+// without a band, else the band's range of the strip.
+__device__ __forceinline__ int2 strip_range(const DpArgs& p, int strip) {
+    if (!p.ranges) return make_int2(0, (p.Lb + kSub - 1) / kSub);
+    return p.ranges[strip];
+}
+
 // Cost warp of `strip`: all sub-chunks of the sweep, in order.
 template <int DP, int R>
 __device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, unsigned cring,
@@ -100,22 +107,19 @@ __device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, u
         }
     }
     const float kc = ghost ? kGhostCost : p.kcost;
-    const int Lb = p.Lb;
     const int Lb_pad = p.nchunk * kColsPerWord;
-    const int nsub = (Lb + kSub - 1) / kSub;
-    br.base += (unsigned)br.nblk;
-    br.nblk = (Lb_pad + S::kBlk - 1) / S::kBlk;
-    br.issued = 0;
-    br.waited = 0;
-    br.top_up(0, p.Bhat, Lb_pad, lane);
-    for (int n = 0; n < nsub; ++n) {
+    const int2 rg = strip_range(p, strip);  // sub-chunks rg.x .. rg.y-1
+    const int q0 = rg.x * kSub / S::kBlk;
+    br.begin(q0, min((rg.y * kSub + S::kBlk - 1) / S::kBlk, (Lb_pad + S::kBlk - 1) / S::kBlk));
+    br.top_up(q0, p.Bhat, Lb_pad, lane);
+    for (int n = rg.x; n < rg.y; ++n) {
         const int js = n * kSub;
-        if (js % S::kBlk == 0) {
+        if (js % S::kBlk == 0 || n == rg.x) {
             const int q = js / S::kBlk;
             if (!br.wait(q, p.ctl, p.timeout_ns)) break;
             br.top_up(q, p.Bhat, Lb_pad, lane);
         }
-        const unsigned t = csub + (unsigned)n;
+        const unsigned t = csub + (unsigned)(n - rg.x);
         const unsigned slot = t % kCostSlots;
         // the DP warp has read this slot's previous contents
         if (!mbar_wait(bar_at(cempty, slot), use_parity(t, kCostSlots) ^ 1u, p.ctl, p.timeout_ns,
@@ -214,9 +218,9 @@ __device__ __forceinline__ void run_cost_bf16(const DpArgs& p, int strip, int la
     constexpr int kMT = kM / 16;
     constexpr int kKS = DP / 16;        // k-steps of 16 features
     constexpr int kRowBytes = kBfStride * 2;
-    const int Lb = p.Lb;
-    const int nchunk = p.nchunk;
-    const int nsub = (Lb + kSub - 1) / kSub;
+    const int2 rg = strip_range(p, strip);  // sub-chunks rg.x (even) .. rg.y-1
+    const int c_lo = rg.x / 2, c_hi = (rg.y + 1) / 2;
+    const int nsub = rg.y;
     // A: rows r = 0 .. kM-1 of the strip as bf16 (rows >= kRows are zero)
     for (int r = lane; r < kM; r += kWarp) {
         const float* src = p.Ahat + (size_t)(strip * kRows + r) * DP;
@@ -237,30 +241,30 @@ __device__ __forceinline__ void run_cost_bf16(const DpArgs& p, int strip, int la
     }
     __syncwarp();
     const char* gb = static_cast<const char*>(p.Bbf);
-    int issued = 0, waited = 0;
-    auto issue = [&](int c) {  // lane 0: chunk c of B into slot (bbase + c) % kBfSlots
+    int issued = c_lo, waited = c_lo;
+    auto issue = [&](int c) {  // lane 0: chunk c of B into slot (bbase + c - c_lo) % kBfSlots
         if (lane == 0) {
-            const unsigned t = bbase + (unsigned)c;
+            const unsigned t = bbase + (unsigned)(c - c_lo);
             tma_load(b_s + (t % kBfSlots) * kBfBlkBytes, gb + (size_t)c * kBfBlkBytes,
                      (unsigned)kBfBlkBytes, bbar_s + 8 * (t % kBfSlots));
         }
     };
-    while (issued < nchunk && issued < kBfSlots - 1) issue(issued++);
+    while (issued < c_hi && issued < c_lo + kBfSlots - 1) issue(issued++);
     const float kc = p.kcost;
     const int g = lane >> 2, t4 = lane & 3;
     bool ok = true;
-    for (int c = 0; c < nchunk && ok; ++c) {
+    for (int c = c_lo; c < c_hi && ok; ++c) {
         // chunk c of B is in its slot
-        const unsigned tb = bbase + (unsigned)c;
+        const unsigned tb = bbase + (unsigned)(c - c_lo);
         if (!mbar_wait(bbar_s + 8 * (tb % kBfSlots), (tb / kBfSlots) & 1u, p.ctl, p.timeout_ns,
                        4)) {
             ok = false;
             break;
         }
         waited = c + 1;
-        if (issued < nchunk) issue(issued++);
+        if (issued < c_hi) issue(issued++);
         const int nj = (2 * c + 1 < nsub) ? 2 : 1;  // sub-chunks of this chunk
-        const unsigned t0 = csub + (unsigned)(2 * c);
+        const unsigned t0 = csub + (unsigned)(2 * c - rg.x);
         for (int j = 0; j < nj; ++j)
             if (!mbar_wait(bar_at(cempty, (t0 + j) % kCostSlots),
                            use_parity(t0 + j, kCostSlots) ^ 1u, p.ctl, p.timeout_ns, 6)) {
@@ -324,14 +328,14 @@ __device__ __forceinline__ void run_cost_bf16(const DpArgs& p, int strip, int la
     }
     // leave no copy in flight (bounded)
     for (int c = waited; c < issued; ++c) {
-        const unsigned tb = bbase + (unsigned)c;
+        const unsigned tb = bbase + (unsigned)(c - c_lo);
         const long long t0 = __shfl_sync(kFull, global_ns(), 0);
         while (!__all_sync(kFull, mbar_try_wait(bbar_s + 8 * (tb % kBfSlots),
                                                 (tb / kBfSlots) & 1u))) {
             if (__shfl_sync(kFull, global_ns(), 0) - t0 > 1000000000LL) break;
         }
     }
-    bbase += (unsigned)issued;
+    bbase += (unsigned)(issued - c_lo);
 }
 
 // The costs of lifetime sub-chunk t (its slot must be full) into c;
@@ -409,7 +413,8 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
                                        unsigned cring, unsigned cfull, unsigned cempty,
-                                       unsigned csub) {
+                                       unsigned csub,
+                                       unsigned inf_blk) {
     constexpr int kRows = 31 * R;
     const bool ghost = lane == kGhostLane;
     const int i0 = strip * kRows + lane * R;
@@ -428,8 +433,23 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
     for (int k = 0; k < R; ++k) w12[k] = (ghost && k >= R - 2) ? 0.0f : 3.0f;
     const int srcA = (lane + 31) & 31;
     const bool is_origin = (i0 == 0) && !ghost;
+    // this strip's sub-chunks, and those its border ring's producer publishes
+    // (the strip above; for the first strip of a group the reader, which
+    // publishes exactly this strip's range)
+    const int2 rg = strip_range(p, strip);
+    const int2 rp = w > 0 ? strip_range(p, strip - 1) : rg;
+    // blocks the strip above published before this strip's first column are
+    // consumed unread, so that the ring's producer and consumer stay in step
+    if (from_ring)
+        for (int n = rp.x; n < rg.x; ++n) {
+            const unsigned ti = rin + (unsigned)(n - rp.x);
+            if (!mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                           p.timeout_ns, 1))
+                return;
+            mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+        }
 
-    // costs of sub-chunk 0
+    // costs of the first sub-chunk
     float c[R][kSub];
     if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
                    p.timeout_ns, 7))
@@ -443,27 +463,30 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
     float ylp = INFINITY;
     // (no poll of the failure flag in the sweep: every wait checks it on its
     // slow path, and a warp that never waits ends with its strip)
-    for (int j0 = 0; j0 < Lb; j0 += kColsPerWord) {
+    const int jend = min(rg.y * kSub, Lb);
+    for (int j0 = rg.x * kSub; j0 < jend; j0 += kColsPerWord) {
         uint32_t word[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) word[k] = 0;
 #pragma unroll
         for (int h = 0; h < kColsPerWord / kSub; ++h) {
             const int js = j0 + h * kSub;
-            if (js >= Lb) break;
+            if (js >= jend) break;
             const int n = js / kSub;
             const int nsteps = min(kSub, Lb - js);
-            const unsigned ti = rin + (unsigned)n, to = rout + (unsigned)n;
-            const unsigned t = csub + (unsigned)n;
+            const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
+            const unsigned t = csub + (unsigned)(n - rg.x);
 
             // border rows top-2, top-1 of columns js .. js+7 (the group's top
-            // border is +inf in group 0)
-            if (from_ring && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk),
-                                        p.ctl, p.timeout_ns, 1))
+            // border is +inf in group 0, and so are the columns the strip
+            // above did not sweep: block 0 of ring 0 holds +inf)
+            const bool have_in = from_ring && n < rp.y;
+            if (have_in && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk),
+                                      p.ctl, p.timeout_ns, 1))
                 return;
             float gv0[kSub], gv1[kSub];
             {
-                const unsigned s0 = smem_u32(&myring[from_ring ? ti % kRingBlk : 0][0][0]);
+                const unsigned s0 = have_in ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk;
                 const float4 a0 = lds128(s0), a1 = lds128(s0 + 16);
                 const float4 b0 = lds128(s0 + 32), b1 = lds128(s0 + 48);
                 gv0[0] = a0.x; gv0[1] = a0.y; gv0[2] = a0.z; gv0[3] = a0.w;
@@ -471,7 +494,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                 gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
                 gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
             }
-            if (from_ring) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+            if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
             // the output block must have been read below
             if (to_ring && !mbar_wait(bar_at(bempty_out, to % kRingBlk),
                                       use_parity(to, kRingBlk) ^ 1u, p.ctl, p.timeout_ns, 2))
@@ -481,7 +504,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
 #pragma unroll
             for (int k = 0; k < R; ++k) fw[k] = 0.0f;
-            const bool has_next = js + kSub < Lb;
+            const bool has_next = js + kSub < jend;
             float cn[R][kSub];
             if (nsteps == kSub) {
                 unsigned ready = 1;
@@ -552,9 +575,13 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
 // value whose tag is not yet this call's is re-polled (bounded).
 constexpr int kAheadSub = 4;
 __device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, float (*ring0)[2][kSub],
-                                           unsigned bfull0, unsigned bempty0, unsigned rbase) {
+                                           unsigned bfull0, unsigned bempty0, unsigned rbase,
+                                           int nfirst, int nsub, int clo, int chi) {
+    // blocks nfirst .. nsub-1 (this group's first strip's range); only columns
+    // clo .. chi-1 were published above (the others read as +inf)
     const int Lb = p.Lb;
-    const int nsub = (Lb + kSub - 1) / kSub;
+    clo = max(clo, 0);
+    chi = min(chi, Lb);
     const unsigned long long* gin = p.gborder + (size_t)(g - 1) * Lb * 2;
     const unsigned epoch = p.epoch;
     const bool act_lane = lane < 2 * kSub;
@@ -562,16 +589,16 @@ __device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, flo
     unsigned long long pend[kAheadSub];
 #pragma unroll
     for (int q = 0; q < kAheadSub; ++q) {
-        const int col = q * kSub + cofs;
-        pend[q] = (act_lane && col < Lb) ? ldg1(gin + (size_t)col * 2 + row) : 0ull;
+        const int col = (nfirst + q) * kSub + cofs;
+        pend[q] = (act_lane && col >= clo && col < chi) ? ldg1(gin + (size_t)col * 2 + row) : 0ull;
     }
-    for (int n0 = 0; n0 < nsub; n0 += kAheadSub) {
+    for (int n0 = nfirst; n0 < nsub; n0 += kAheadSub) {
 #pragma unroll
         for (int q = 0; q < kAheadSub; ++q) {
             const int n = n0 + q;
             if (n >= nsub) break;
             const int col = n * kSub + cofs;
-            const bool act = act_lane && col < Lb;
+            const bool act = act_lane && col >= clo && col < chi;
             int ok = !act || tag_of(pend[q]) == epoch;
             if (!__all_sync(kFull, ok)) {
                 // each poll is a round trip to L2; status and deadline every 16 polls
@@ -592,14 +619,14 @@ __device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, flo
                     }
                 }
             }
-            const unsigned t = rbase + (unsigned)n;
+            const unsigned t = rbase + (unsigned)(n - nfirst);
             if (!mbar_wait(bar_at(bempty0, t % kRingBlk), use_parity(t, kRingBlk) ^ 1u, p.ctl,
                            p.timeout_ns, 8))
                 return;
-            if (act) ring0[t % kRingBlk][row][cofs] = val_of(pend[q]);
+            if (act_lane) ring0[t % kRingBlk][row][cofs] = act ? val_of(pend[q]) : INFINITY;
             mbar_arrive(bar_at(bfull0, t % kRingBlk));
             const int ncol = col + kAheadSub * kSub;
-            if (act_lane && ncol < Lb) pend[q] = ldg1(gin + (size_t)ncol * 2 + row);
+            if (act_lane && ncol >= clo && ncol < chi) pend[q] = ldg1(gin + (size_t)ncol * 2 + row);
         }
     }
 }
@@ -609,14 +636,14 @@ __device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, flo
 // coalesced 128-byte line per sub-chunk.
 __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
                                            float (*ringo)[2][kSub], unsigned bfullo,
-                                           unsigned bemptyo, unsigned rbase) {
+                                           unsigned bemptyo, unsigned rbase, int nfirst,
+                                           int nsub) {
     const int Lb = p.Lb;
-    const int nsub = (Lb + kSub - 1) / kSub;
     unsigned long long* gout = p.gborder + (size_t)g * Lb * 2;
     const unsigned epoch = p.epoch;
     const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
-    for (int n = 0; n < nsub; ++n) {
-        const unsigned t = rbase + (unsigned)n;
+    for (int n = nfirst; n < nsub; ++n) {
+        const unsigned t = rbase + (unsigned)(n - nfirst);
         if (!mbar_wait(bar_at(bfullo, t % kRingBlk), use_parity(t, kRingBlk), p.ctl, p.timeout_ns,
                        9))
             return;
@@ -647,6 +674,7 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     __shared__ __align__(8) unsigned long long cempty[NS][kCostSlots];
     __shared__ __align__(8) unsigned long long bfull[NS + 1][kRingBlk];
     __shared__ __align__(8) unsigned long long bempty[NS + 1][kRingBlk];
+    __shared__ __align__(16) float s_inf[2][kSub];  // +inf border block, never written after
     __shared__ int s_group, s_pair;
     extern __shared__ __align__(128) unsigned char dyn[];  // NS * M::kStripBytes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -665,8 +693,10 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     br.stage_s = smem_u32(mine);
     br.bar_s = smem_u32(&bbar[w][0]);
     br.base = 0;
+    br.first = 0;
     br.nblk = 0;
     br.issued = br.waited = 0;
+    if (threadIdx.x < 2 * kSub) (&s_inf[0][0])[threadIdx.x] = INFINITY;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             for (int k = 0; k < S::kSlots; ++k) mbar_init(smem_u32(&bbar[s][k]), 1);
@@ -728,9 +758,13 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
         const DpArgs p = kMany ? many[s_pair] : one;
         const int g = s_group;
         if (g >= p.ngroups) return;
-        const unsigned nsub = (unsigned)((p.Lb + kSub - 1) / kSub);
         const GroupRoles gr = group_roles<NS>(p, g);
         const int strip = g * NS + w;
+        // the sub-chunk ranges of the group's strips (all columns without a band)
+        int2 rgs[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            rgs[q] = q < gr.nstrips_here ? strip_range(p, g * NS + q) : make_int2(0, 0);
         if (role == 0) {
             if (w < gr.nstrips_here)
             {
@@ -743,23 +777,31 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
         } else if (role == 1) {
             if (w < gr.nstrips_here)
                 run_dp<R, NS, kBF>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
-                              smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s, cfull_s,
-                              cempty_s, csub[w]);
+                                   smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
+                                   cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]));
         } else if (role == 2) {
-            if (gr.reader)
+            if (gr.reader) {
+                // the first strip's blocks; the strip above (last of the group
+                // above) published its own range's columns
+                const int2 above = strip_range(p, g * NS - 1);
                 run_reader(p, g, lane, ring[0], smem_u32(&bfull[0][0]), smem_u32(&bempty[0][0]),
-                           rsub[0]);
+                           rsub[0], rgs[0].x, rgs[0].y, above.x * kSub, above.y * kSub);
+            }
         } else {
             if (gr.writer)
                 run_writer(p, g, lane, ring[NS], smem_u32(&bfull[NS][0]),
-                           smem_u32(&bempty[NS][0]), rsub[NS]);
+                           smem_u32(&bempty[NS][0]), rsub[NS], rgs[NS - 1].x, rgs[NS - 1].y);
         }
+        // ring uses of this group, in blocks of 8 columns: a cost ring the
+        // strip's range; ring 0 the first strip's range; ring w (1 <= w < NS)
+        // and ring NS the range of the strip that fills them
 #pragma unroll
-        for (int s = 0; s < NS; ++s)
-            if (s < gr.nstrips_here) csub[s] += nsub;
+        for (int q = 0; q < NS; ++q)
+            if (q < gr.nstrips_here) csub[q] += (unsigned)(rgs[q].y - rgs[q].x);
+        if (ring_used<NS>(gr, 0)) rsub[0] += (unsigned)(rgs[0].y - rgs[0].x);
 #pragma unroll
-        for (int s = 0; s <= NS; ++s)
-            if (ring_used<NS>(gr, s)) rsub[s] += nsub;
+        for (int q = 1; q <= NS; ++q)
+            if (ring_used<NS>(gr, q)) rsub[q] += (unsigned)(rgs[q - 1].y - rgs[q - 1].x);
     }
 }
 

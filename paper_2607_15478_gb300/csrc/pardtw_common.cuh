@@ -48,6 +48,9 @@ struct DpArgs {
     unsigned epoch;                 // call tag for global border entries
     long long timeout_ns;
     int skip_publish;               // group that never publishes (fault injection), -1 off
+    const int2* ranges;             // banded DP (warp-pair kernel): per strip the sub-chunks
+                                    // [x, y) of 8 columns it sweeps (x even; x and y
+                                    // non-decreasing in the strip); null = every column
 };
 
 // Backpointer word address of cell (i, j): strip-major, then 16-column chunk,
@@ -158,6 +161,8 @@ struct BtArgs {
     int* path_len;
     float* total;
     void* scratch;
+    const int2* ranges;  // banded DP: the strips' sub-chunk ranges (cells outside have no
+                         // path), else null
 };
 size_t bandmap_scratch_bytes(int La, int Lb);
 cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s);
@@ -168,5 +173,16 @@ cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, in
 
 // Padded feature width used by the kernels for a given D (0 = unsupported).
 int padded_dim(int D);
+
+// Multiscale band (band.cu): Y (ceil(L/ds) x D) = averages of ds frames of X;
+// per strip of rps fine rows the 8-column blocks within w columns of the
+// coarse path (cpath, *clen cells) scaled by ds, widened to monotone; *touch
+// = 1 if the banded path (path, *plen cells) comes within one block of a
+// side of the band that is not the side of the matrix.
+cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStream_t s);
+cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w, int La,
+                               int Lb, int nstrips, int rps, int2* ranges, cudaStream_t s);
+cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
+                              const int2* ranges, int* touch, cudaStream_t s);
 
 }  // namespace pardtw

@@ -34,7 +34,7 @@ DTW_COST_BF16 = 1
 EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destroy",
            "dtw_set_stream", "dtw_workspace_size", "dtw_cost", "dtw_align", "dtw_align_many",
            "dtw_enable_timing", "dtw_stage_times", "dtw_align_static",
-           "dtw_static_scratch_bytes")
+           "dtw_static_scratch_bytes", "dtw_align_banded")
 
 
 class PardtwError(RuntimeError):
@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_size_t)]
     lib.dtw_cost.argtypes = [vp, vp, ci, vp, ci, ci, vp]
     lib.dtw_align.argtypes = [vp, vp, ci, vp, ci, ci, ctypes.POINTER(Options), vp, ci, vp, vp]
+    lib.dtw_align_banded.argtypes = [vp, vp, ci, vp, ci, ci, ctypes.POINTER(Options), ci, ci, vp,
+                                     ci, vp, vp, ctypes.POINTER(ci)]
     lib.dtw_align_many.argtypes = [vp, ci, vp, vp, vp, vp, ci, ctypes.POINTER(Options), vp, vp,
                                    vp, vp, vp]
     lib.dtw_enable_timing.argtypes = [vp, ci]
@@ -193,6 +195,20 @@ def dtw_align_many(h: int, As: Sequence, Bs: Sequence, paths, path_off, path_len
         cost.data_ptr() if cost is not None else None, status.data_ptr()), "dtw_align_many")
 
 
+def dtw_align_banded(h: int, A, B, path, path_len, total=None, downsample: int = 8,
+                     halfwidth: int = 256, options: Options | None = None) -> bool:
+    """Exact DTW inside the band of the coarse alignment (include/pardtw.h);
+    returns True when the band was given up for the full exact DTW."""
+    A, B = _features(A), _features(B)
+    fb = ctypes.c_int(0)
+    _check(load_library().dtw_align_banded(
+        h, A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1],
+        ctypes.byref(options) if options else None, int(downsample), int(halfwidth),
+        path.data_ptr(), path.shape[0], path_len.data_ptr(),
+        total.data_ptr() if total is not None else None, ctypes.byref(fb)), "dtw_align_banded")
+    return bool(fb.value)
+
+
 def dtw_align_static(A, B, path, path_len, total=None, options: Options | None = None,
                      stream=None) -> None:
     """Exact DTW into caller device buffers without any device allocation.
@@ -297,6 +313,23 @@ class Aligner:
         if n < 0:
             raise PardtwError(-n, "dtw_align (device)")
         return path[:n], float(tot.item())
+
+    def align_banded(self, A, B, downsample: int = 8, halfwidth: int = 256, **opts):
+        """Banded exact DTW; returns (path, total, fell_back)."""
+        import torch
+        A, B = _features(A), _features(B)
+        cap = min(A.shape[0], B.shape[0])
+        path = torch.empty((cap, 2), dtype=torch.int32, device=A.device)
+        plen = torch.zeros(1, dtype=torch.int32, device=A.device)
+        tot = torch.zeros(1, dtype=torch.float32, device=A.device)
+        self._enter()
+        fb = dtw_align_banded(self.h, A, B, path, plen, tot, downsample, halfwidth,
+                              make_options(**opts) if opts else None)
+        self._leave()
+        n = int(plen.item())
+        if n < 0:
+            raise PardtwError(-n, "dtw_align_banded (device)")
+        return path[:n], float(tot.item()), fb
 
     def align_many(self, As: List, Bs: List, **opts):
         """Align independent pairs; returns (list of paths or None, costs, statuses)."""
