@@ -35,6 +35,9 @@ UNIT = "GCUPS"
 WORKLOAD = "pair-20000x12-vs-25000x12 chroma-like, warped (64 knots, tempo 0.7-1.4), cosine cost"
 L2_FLUSH_BYTES = 512 << 20
 KERNELS_PER_STEP = 6  # normalise, DP, band map, band chain, band walks, emit
+# learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (6), band
+# ranges (2), banded alignment (6), band-side test (1)
+KERNELS_PER_LEARNED_STEP = 10 + 6 + 2 + 6 + 1
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -617,6 +620,147 @@ def run_precision(args):
     al.close()
 
 
+def run_band(args):
+    """The learned-band workload: the 100000x12 vs 100000-130000x12 pair
+    (tempo 0.6-1.6, 256 knots) aligned exactly inside the band of the learned
+    encoder (dtw_align_learned, bf16 encoder, trained weights of the
+    package), against the full exact DP of the same pair on the same GPU.
+    value = full-matrix cells (La x Lb) per second of the banded alignment;
+    the speedup over the exact DP and the path deviation from the exact path
+    are reported beside it."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import band_train
+    from paper_2607_15478_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2607_15478_gb300 import pardtw, synth
+    wp = synth.config_pair(4, pair=rank)
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    cells = La * Lb
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    P = band_train.load(device=dev)
+    A = torch.from_numpy(wp.A).to(dev)
+    B = torch.from_numpy(wp.B).to(dev)
+    cap = min(La, Lb)
+    path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    plen = torch.zeros(1, dtype=torch.int32, device=dev)
+    tot = torch.zeros(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    fell = []
+
+    def step(exact=False):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            if exact:
+                al.align_into(A, B, path, plen, tot)
+            else:
+                fell.append(pardtw.dtw_align_learned(al.h, A, B, P, path, plen, tot, 8, True))
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    # the exact DP of the same pair: its path, total and time
+    for _ in range(2):
+        step(exact=True)
+    exact_ms = statistics.median([step(exact=True) for _ in range(max(3, args.steps // 4))])
+    p_exact = path[:int(plen.item())].cpu().numpy()
+    t_exact = float(tot.item())
+    for _ in range(args.warmup):
+        step()
+    fell.clear()
+    step_ms, dp_ms = [], []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(args.steps):
+            step_ms.append(step())
+            dp_ms.append(al.stage_times()[1])
+        clk.mark_end()
+    t = sum(step_ms) / 1e3
+    value = cells * args.steps / t / 1e9
+    band_cells = al.band_cells()
+    p_band = path[:int(plen.item())].cpu().numpy()
+    t_band = float(tot.item())
+
+    def jbar(pp, n):
+        acc, cnt = np.zeros(n), np.zeros(n)
+        np.add.at(acc, pp[:, 0], pp[:, 1])
+        np.add.at(cnt, pp[:, 0], 1)
+        rows = np.flatnonzero(cnt)
+        return np.interp(np.arange(n), rows, acc[rows] / cnt[rows])
+    deviation = float(np.mean(np.abs(jbar(p_band, La) - jbar(p_exact, La))))
+    # e2e: host features in, path out, through the public API
+    Ah = torch.from_numpy(wp.A).pin_memory()
+    Bh = torch.from_numpy(wp.B).pin_memory()
+    al.enable_timing(False)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            Ad = Ah.to(dev, non_blocking=True)
+            Bd = Bh.to(dev, non_blocking=True)
+        pth, tt, fb = al.align_learned(Ad, Bd, P)
+        ph = pth.cpu()
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = sum(e2e_t[args.warmup:])
+    peaks, src = measured_peaks()
+    clock = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6
+    ops_per_cell = D + 6
+    dp_avg = statistics.mean(dp_ms) / 1e3
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        a, b, dt = oracle_sample(wp, cells_target=3.0e8)
+        cpu = {"value": a * b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"leading {a}x{b} block of the pair, single-threaded FP64 row-by-row "
+                         f"exact DTW ({dt:.1f} s)"}
+    _rank0_line({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (encoder bf16)",
+        "data": "synthetic",
+        "config": {"workload": f"pair-{La}x12-vs-{Lb}x12 chroma-like, warped (256 knots, tempo "
+                               f"0.6-1.6), exact DTW in the learned band",
+                   "La": La, "Lb": Lb, "D": D, "downsample": 8,
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU",
+                   "value_definition": "La x Lb cells over the banded alignment's time"},
+        "band": {"exact_ms": exact_ms, "band_ms": 1e3 * t / args.steps,
+                 "speedup_vs_exact": exact_ms / (1e3 * t / args.steps),
+                 "fell_back_steps": int(sum(fell)), "same_path_as_exact":
+                     bool(p_band.shape == p_exact.shape and np.array_equal(p_band, p_exact)),
+                 "mean_path_deviation_frames": deviation,
+                 "total_rel_diff": abs(t_band - t_exact) / abs(t_exact),
+                 "band_cells": band_cells, "band_fraction": band_cells / cells,
+                 "weights": "paper_2607_15478_gb300/weights/band_encoder_d12.npy"},
+        "roofline": {"bound": "alu", "achieved": band_cells * ops_per_cell / dp_avg / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "T FP32 lane-ops/s",
+                     "frac": band_cells * ops_per_cell / dp_avg / peak_ops, "traffic": None,
+                     "kernel": "k_dp_split over the band's strip ranges",
+                     "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
+                     "note": "the banded DP is one chain of strips (each waits for the "
+                             "bottom rows of the one above): bound by the per-column step "
+                             "latency of a strip, not by a pipe"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": int(ph.shape[0]) * 8 + 8},
+        "gpu_launches": KERNELS_PER_LEARNED_STEP * args.steps,
+        "clocks": clk.summary(),
+    })
+    al.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -627,9 +771,10 @@ def main():
     ap.add_argument("--La", type=int, default=None,
                     help="override the pair's lengths (same recipe; for profiling smaller cases)")
     ap.add_argument("--Lb", type=int, default=None)
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3],
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4],
                     help="1: the 20000x25000 pair (default, the headline line); 2: the "
-                         "256-pair batch; 3: the D = 128 pair with the BF16 cost")
+                         "256-pair batch; 3: the D = 128 pair with the BF16 cost; 4: the "
+                         "100000x(100000-130000) pair in the learned band")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -639,6 +784,8 @@ def main():
         run_batch(args)
     elif args.config == 3:
         run_precision(args)
+    elif args.config == 4:
+        run_band(args)
     else:
         run_ours(args)
 

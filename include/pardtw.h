@@ -186,6 +186,77 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
                      const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
                      int cap, int* path_len, float* total_cost, int* fell_back);
 
+/* ---- learned band ---------------------------------------------------------- */
+/* A band predicted by a small network instead of a fixed half-width.  The
+ * paper names bands and multiscale DTW only as related ways to cut the
+ * quadratic cost (Sec. II); the encoder, its training and its use are this
+ * library's.  The encoder maps each sequence, averaged over `downsample`
+ * frames and L2-normalised per frame, through three convolutions of width 5
+ * (64 channels, zero padding 2, ReLU) to a 16-dimensional unit embedding per
+ * coarse frame, and for A to a half-width per coarse frame
+ *   hw = DTW_BAND_WMIN * (DTW_BAND_WMAX / DTW_BAND_WMIN)^sigmoid(s)   (fine frames).
+ * dtw_align_learned aligns the embeddings exactly (cosine cost), takes per
+ * strip of the fine DP the band of the widest predicted half-width around
+ * the upsampled coarse path, runs the exact DP inside it, and falls back to
+ * the full exact DP when the banded path comes within one 8-column block of
+ * a side of the band (as dtw_align_banded).
+ *
+ * Parameters: one float32 array of dtw_encoder_param_count(D) values (device
+ * memory), in this order (weights of a convolution [out][in][5], row-major):
+ *   W1 [64][D][5], b1 [64], W2 [64][64][5], b2 [64], W3 [64][64][5], b3 [64],
+ *   W4 [16][64], b4 [16] (embedding), W5 [64], b5 [1] (half-width logit). */
+#define DTW_BAND_WMIN 256
+#define DTW_BAND_WMAX 2048
+#define DTW_ENC_CHANNELS 64
+#define DTW_ENC_EMBED 16
+#define DTW_ENC_KERNEL 5
+
+/* Number of parameters for input dimension D (1 <= D <= 64), else 0.  Host
+ * function; needs no device. */
+size_t dtw_encoder_param_count(int D);
+
+/* Encoder forward of one sequence X (L x D, device) at `downsample`:
+ * emb (ceil(L/downsample) x 16, device) and, if not NULL, halfwidth
+ * (ceil(L/downsample), device, fine frames).  bf16 != 0 rounds the inputs
+ * and weights of the convolutions and of the embedding head to bfloat16
+ * (FP32 accumulation). */
+int dtw_encode(dtw_handle* h, const float* params, int D, const float* X, int L, int downsample,
+               int bf16, float* emb, float* halfwidth);
+
+/* Training: adds to grad (device, dtw_encoder_param_count(D) floats) the
+ * gradient of the loss of one pair and adds the loss to *loss (device).
+ * path / path_len (device) is the exact alignment of (A, B) (as dtw_align
+ * writes it).  Per coarse row i of A the exact path matches coarse column
+ * c_i (its mean column in the row's frames / downsample).
+ *   mode 0: embedding loss, mean over i of -log softmax_j(eA_i . eB_j / 0.1)
+ *           at j = c_i, j over the coarse columns within 16 of c_i; gradient
+ *           of the trunk and the embedding head.
+ *   mode 1: half-width loss, mean over i of the pinball loss at quantile 0.9
+ *           of sigmoid(s_i) against the log-scale half-width (in [0, 1]) the
+ *           band of the coarse alignment of the current embeddings needs at
+ *           row i to hold the exact path, plus 64 frames; gradient of W5, b5.
+ * FP32 throughout; downsample >= 2.  Asynchronous. */
+int dtw_encoder_grad(dtw_handle* h, const float* params, int D, int downsample, const float* A,
+                     int La, const float* B, int Lb, const int32_t* path, const int* path_len,
+                     int mode, float* grad, float* loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; `step`
+ * counts from 1) over n parameters, all device arrays; grad is zeroed. */
+int dtw_encoder_adam(dtw_handle* h, int n, float* params, float* grad, float* m, float* v,
+                     int step, float lr);
+
+/* Exact DTW inside the learned band, with the same arguments, device-only
+ * rule, synchronisation and fallback as dtw_align_banded; params (device)
+ * as above for this D (D <= 32, FP32 cost). */
+int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                      const dtw_options* opt, const float* params, int downsample, int bf16,
+                      int32_t* path, int cap, int* path_len, float* total_cost, int* fell_back);
+
+/* Cells of the band the last dtw_align_banded / dtw_align_learned call on
+ * this handle swept (rows x columns of every strip's range); 0 if it fell
+ * back or no band was run.  Synchronises the handle's stream. */
+int dtw_band_cells(dtw_handle* h, long long* cells);
+
 /* ---- alignment without device allocation ---------------------------------- */
 /* The paper has no counterpart of this entry point; it is a service of this
  * library.  Some callers cannot allocate device memory while they align: a

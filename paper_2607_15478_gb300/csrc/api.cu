@@ -31,8 +31,14 @@ struct dtw_handle {
     bool timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int* h_small = nullptr;      // pinned host: [0] path_len, [1] total bits
-    char* band = nullptr;        // dtw_align_banded: pooled inputs, coarse path, ranges
+    char* band = nullptr;        // banded calls: pooled inputs, coarse path, ranges, flag
     size_t band_cap = 0;
+    int band_nstrips = 0;        // strips, rows per strip and columns of the last band
+    int band_rps = 0;
+    int band_Lb = 0;
+    const int2* band_ranges = nullptr;
+    char* enc = nullptr;         // band encoder activations and gradients
+    size_t enc_cap = 0;
 };
 
 namespace {
@@ -496,6 +502,7 @@ int dtw_destroy(dtw_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->border) cudaFree(h->border);
     if (h->band) cudaFree(h->band);
+    if (h->enc) cudaFree(h->enc);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->h_small) cudaFreeHost(h->h_small);
@@ -705,74 +712,364 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
     return DTW_OK;
 }
 
-int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
-                     const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
-                     int cap, int* path_len, float* total_cost, int* fell_back) {
-    if (!h || !path || !path_len || downsample < 1 || halfwidth < 0) return DTW_ERR_INVALID;
-    int rc = validate(A, La, B, Lb, D);
-    if (rc != DTW_OK) return rc;
-    if (cap < std::min(La, Lb)) return DTW_ERR_INVALID;
-    const dtw_options o = opt ? *opt : defaults();
-    if (o.cost_precision != DTW_COST_FP32 || !split_supported(padded_dim(D), 3))
-        return DTW_ERR_UNSUPPORTED;
-    DeviceGuard g(h->device);
-    if (!g.ok) return DTW_ERR_CUDA;
-    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(path) ||
-        !is_device_ptr(path_len) || (total_cost && !is_device_ptr(total_cost)))
-        return DTW_ERR_INVALID;
-    cudaStream_t s = h->stream;
-    if (fell_back) *fell_back = 0;
-    const int Lac = (La + downsample - 1) / downsample, Lbc = (Lb + downsample - 1) / downsample;
-    if (downsample == 1 || !reachable(Lac, Lbc)) {
-        if (fell_back) *fell_back = 1;
-        return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
+}  // extern "C"
+
+namespace {
+
+// Grow a handle-owned device buffer (synchronising the stream first, since
+// queued work may still use the old one).
+int grow(dtw_handle* h, char** buf, size_t* cap, size_t need) {
+    if (need <= *cap) return DTW_OK;
+    CU(cudaStreamSynchronize(h->stream));
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *buf = nullptr;
+        return DTW_ERR_OOM;
     }
+    *cap = need;
+    return DTW_OK;
+}
+
+// Offsets in the band buffer: pooled A and B (pooled = true), the coarse
+// path and its length, the strip ranges and the band-side flag.
+struct BandBuf {
+    size_t pa, pb, cp, cl, rg, tc, total;
+};
+BandBuf band_buf(int Lac, int Lbc, int D, int nstrips, bool pooled) {
+    BandBuf b;
+    size_t o = 0;
+    b.pa = o;
+    if (pooled) o = align256(o + (size_t)Lac * D * sizeof(float));
+    b.pb = o;
+    if (pooled) o = align256(o + (size_t)Lbc * D * sizeof(float));
+    b.cp = o;
+    o = align256(o + (size_t)2 * std::min(Lac, Lbc) * sizeof(int32_t));
+    b.cl = o;
+    o = align256(o + 16);
+    b.rg = o;
+    o = align256(o + (size_t)nstrips * sizeof(int2));
+    b.tc = o;
+    b.total = o + 256;
+    return b;
+}
+
+// The band pipeline after the coarse features: exact alignment of the
+// coarse sequences cA (Lac x Dc) and cB (Lbc x Dc), per strip of the fine DP
+// the blocks within the half-width (w, or wrow per coarse row) of the
+// upsampled coarse path, the exact DP inside the band, and the full exact
+// DP when the banded path meets a side of the band.
+int band_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+               const dtw_options& o, int ds, const float* cA, int Lac, const float* cB, int Lbc,
+               int Dc, int w, const float* wrow, const BandBuf& bb, int32_t* path, int* path_len,
+               float* total_cost, int* fell_back) {
+    cudaStream_t s = h->stream;
     const int rps = strip_rows(3);
     const int nstrips = (La + rps - 1) / rps;
-    const int capc = std::min(Lac, Lbc);
-    // band buffer: pooled A and B, coarse path and length, ranges, touch flag
-    const size_t off_pa = 0;
-    const size_t off_pb = align256(off_pa + (size_t)Lac * D * sizeof(float));
-    const size_t off_cp = align256(off_pb + (size_t)Lbc * D * sizeof(float));
-    const size_t off_cl = align256(off_cp + (size_t)2 * capc * sizeof(int32_t));
-    const size_t off_rg = align256(off_cl + 16);
-    const size_t off_tc = align256(off_rg + (size_t)nstrips * sizeof(int2));
-    const size_t need = off_tc + 256;
-    if (need > h->band_cap) {
-        CU(cudaStreamSynchronize(s));
-        if (h->band) cudaFree(h->band);
-        h->band = nullptr;
-        h->band_cap = 0;
-        if (cudaMalloc(&h->band, need) != cudaSuccess) {
-            (void)cudaGetLastError();
-            h->band = nullptr;
-            return DTW_ERR_OOM;
-        }
-        h->band_cap = need;
-    }
-    float* pa = reinterpret_cast<float*>(h->band + off_pa);
-    float* pb = reinterpret_cast<float*>(h->band + off_pb);
-    int32_t* cpath = reinterpret_cast<int32_t*>(h->band + off_cp);
-    int* clen = reinterpret_cast<int*>(h->band + off_cl);
-    int2* ranges = reinterpret_cast<int2*>(h->band + off_rg);
-    int* touch = reinterpret_cast<int*>(h->band + off_tc);
-    // 1. the coarse pair and its exact alignment
-    CU(launch_pool(A, La, D, downsample, pa, s));
-    CU(launch_pool(B, Lb, D, downsample, pb, s));
-    rc = align_device(h, pa, Lac, pb, Lbc, D, o, cpath, clen, nullptr);
+    int32_t* cpath = reinterpret_cast<int32_t*>(h->band + bb.cp);
+    int* clen = reinterpret_cast<int*>(h->band + bb.cl);
+    int2* ranges = reinterpret_cast<int2*>(h->band + bb.rg);
+    int* touch = reinterpret_cast<int*>(h->band + bb.tc);
+    dtw_options oc = o;
+    oc.rows_per_lane = 0;
+    oc.dp_schedule = DTW_SCHEDULE_AUTO;
+    int rc = align_device(h, cA, Lac, cB, Lbc, Dc, oc, cpath, clen, nullptr);
     if (rc != DTW_OK) return rc;
-    // 2. the band and the exact DP inside it
-    CU(launch_band_ranges(cpath, clen, downsample, halfwidth, La, Lb, nstrips, rps, ranges, s));
+    CU(launch_band_ranges(cpath, clen, ds, w, wrow, Lac, La, Lb, nstrips, rps, ranges, s));
+    h->band_nstrips = nstrips;
+    h->band_rps = rps;
+    h->band_Lb = Lb;
+    h->band_ranges = ranges;
     rc = align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost, ranges);
     if (rc != DTW_OK) return rc;
-    // 3. a path at the band's side: the full exact DP instead
     CU(launch_band_touch(path, path_len, std::min(La, Lb), Lb, rps, ranges, touch, s));
     CU(cudaMemcpyAsync(h->h_small + 2, touch, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (h->h_small[2]) {
         if (fell_back) *fell_back = 1;
+        h->band_nstrips = 0;
         return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
     }
+    return DTW_OK;
+}
+
+// Checks shared by the banded entry points; returns DTW_OK and the options.
+int band_checks(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                const dtw_options* opt, int ds, int32_t* path, int cap, int* path_len,
+                float* total_cost, dtw_options* o) {
+    if (!h || !path || !path_len || ds < 1) return DTW_ERR_INVALID;
+    int rc = validate(A, La, B, Lb, D);
+    if (rc != DTW_OK) return rc;
+    if (cap < std::min(La, Lb)) return DTW_ERR_INVALID;
+    *o = opt ? *opt : defaults();
+    if (o->cost_precision != DTW_COST_FP32 || !split_supported(padded_dim(D), 3))
+        return DTW_ERR_UNSUPPORTED;
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(path) ||
+        !is_device_ptr(path_len) || (total_cost && !is_device_ptr(total_cost)))
+        return DTW_ERR_INVALID;
+    return DTW_OK;
+}
+
+// Encoder buffers of one sequence of Lc coarse frames in the handle's
+// encoder buffer (floats unless noted).
+struct EncSeq {
+    size_t X, H1, H2, H3, E, invn, S, HW, G, dHa, dHb, total;
+};
+EncSeq enc_seq(size_t base, int Lc, int D) {
+    EncSeq q;
+    size_t o = base;
+    auto take = [&](size_t n) { size_t at = o; o = align256(o + n * sizeof(float)); return at; };
+    q.X = take((size_t)Lc * D);
+    q.H1 = take((size_t)Lc * kEncChannels);
+    q.H2 = take((size_t)Lc * kEncChannels);
+    q.H3 = take((size_t)Lc * kEncChannels);
+    q.E = take((size_t)Lc * kEncEmbed);
+    q.invn = take(Lc);
+    q.S = take(Lc);
+    q.HW = take(Lc);
+    q.G = take((size_t)Lc * kEncEmbed);
+    q.dHa = take((size_t)Lc * kEncChannels);
+    q.dHb = take((size_t)Lc * kEncChannels);
+    q.total = o;
+    return q;
+}
+// Both sequences, then the per-row training data of A: targets (int), the
+// sums behind them (u64, int), width targets, width-logit gradients.
+struct EncBuf {
+    EncSeq a, b;
+    size_t tgt, jsum, cnt, wt, dS, total;
+};
+EncBuf enc_buf(int Lac, int Lbc, int D) {
+    EncBuf e;
+    e.a = enc_seq(0, Lac, D);
+    e.b = enc_seq(e.a.total, Lbc, D);
+    size_t o = e.b.total;
+    e.tgt = o; o = align256(o + (size_t)Lac * sizeof(int));
+    e.jsum = o; o = align256(o + (size_t)Lac * sizeof(unsigned long long));
+    e.cnt = o; o = align256(o + (size_t)Lac * sizeof(int));
+    e.wt = o; o = align256(o + (size_t)Lac * sizeof(float));
+    e.dS = o; o = align256(o + (size_t)Lac * sizeof(float));
+    e.total = o;
+    return e;
+}
+
+float* ef(dtw_handle* h, size_t off) { return reinterpret_cast<float*>(h->enc + off); }
+
+// Encoder forward of one sequence X (L fine frames): pooled input, the three
+// conv layers and the heads, into the buffers of q.
+int enc_forward(dtw_handle* h, const float* P, const EncLayout& pl, int D, const float* X, int L,
+                int ds, int bf16, const EncSeq& q) {
+    cudaStream_t s = h->stream;
+    const int Lc = (L + ds - 1) / ds;
+    CU(launch_pool_norm(X, L, D, ds, ef(h, q.X), s));
+    CU(launch_conv(ef(h, q.X), nullptr, Lc, D, P + pl.W1, P + pl.b1, 1, 0, bf16, ef(h, q.H1), s));
+    CU(launch_conv(ef(h, q.H1), nullptr, Lc, kEncChannels, P + pl.W2, P + pl.b2, 1, 0, bf16,
+                   ef(h, q.H2), s));
+    CU(launch_conv(ef(h, q.H2), nullptr, Lc, kEncChannels, P + pl.W3, P + pl.b3, 1, 0, bf16,
+                   ef(h, q.H3), s));
+    CU(launch_embed(ef(h, q.H3), Lc, P, pl, bf16, (float)DTW_BAND_WMIN, (float)DTW_BAND_WMAX,
+                    ef(h, q.E), ef(h, q.invn), ef(h, q.S), ef(h, q.HW), s));
+    return DTW_OK;
+}
+
+// Backward of the trunk and the embedding head of one sequence, from the
+// gradient of the loss with respect to its embeddings (in q.G).
+int enc_backward(dtw_handle* h, const float* P, const EncLayout& pl, int D, int Lc,
+                 const EncSeq& q, float* grad) {
+    cudaStream_t s = h->stream;
+    constexpr int C = kEncChannels;
+    CU(launch_embed_bwd(ef(h, q.E), ef(h, q.invn), Lc, P + pl.W4, ef(h, q.G), ef(h, q.dHa), s));
+    CU(launch_outer(ef(h, q.G), kEncEmbed, ef(h, q.H3), C, Lc, grad + pl.W4, s));
+    CU(launch_outer(ef(h, q.G), kEncEmbed, nullptr, 1, Lc, grad + pl.b4, s));
+    // layer 3: dH3 in dHa (masked by H3 inside)
+    CU(launch_conv_wgrad(ef(h, q.H2), Lc, C, ef(h, q.dHa), ef(h, q.H3), grad + pl.W3,
+                         grad + pl.b3, s));
+    CU(launch_conv(ef(h, q.dHa), ef(h, q.H3), Lc, C, P + pl.W3, nullptr, 0, 1, 0, ef(h, q.dHb),
+                   s));
+    // layer 2: dH2 in dHb
+    CU(launch_conv_wgrad(ef(h, q.H1), Lc, C, ef(h, q.dHb), ef(h, q.H2), grad + pl.W2,
+                         grad + pl.b2, s));
+    CU(launch_conv(ef(h, q.dHb), ef(h, q.H2), Lc, C, P + pl.W2, nullptr, 0, 1, 0, ef(h, q.dHa),
+                   s));
+    // layer 1: dH1 in dHa
+    CU(launch_conv_wgrad(ef(h, q.X), Lc, D, ef(h, q.dHa), ef(h, q.H1), grad + pl.W1,
+                         grad + pl.b1, s));
+    return DTW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                     const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
+                     int cap, int* path_len, float* total_cost, int* fell_back) {
+    if (halfwidth < 0) return DTW_ERR_INVALID;
+    dtw_options o;
+    int rc = band_checks(h, A, La, B, Lb, D, opt, downsample, path, cap, path_len, total_cost, &o);
+    if (rc != DTW_OK) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    if (fell_back) *fell_back = 0;
+    h->band_nstrips = 0;
+    const int Lac = (La + downsample - 1) / downsample, Lbc = (Lb + downsample - 1) / downsample;
+    if (downsample == 1 || !reachable(Lac, Lbc)) {
+        if (fell_back) *fell_back = 1;
+        return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
+    }
+    const int nstrips = (La + strip_rows(3) - 1) / strip_rows(3);
+    const BandBuf bb = band_buf(Lac, Lbc, D, nstrips, true);
+    rc = grow(h, &h->band, &h->band_cap, bb.total);
+    if (rc != DTW_OK) return rc;
+    float* pa = reinterpret_cast<float*>(h->band + bb.pa);
+    float* pb = reinterpret_cast<float*>(h->band + bb.pb);
+    CU(launch_pool(A, La, D, downsample, pa, h->stream));
+    CU(launch_pool(B, Lb, D, downsample, pb, h->stream));
+    return band_align(h, A, La, B, Lb, D, o, downsample, pa, Lac, pb, Lbc, D, halfwidth, nullptr,
+                      bb, path, path_len, total_cost, fell_back);
+}
+
+size_t dtw_encoder_param_count(int D) {
+    if (D < 1 || D > kEncChannels) return 0;
+    return enc_layout(D).count;
+}
+
+int dtw_encode(dtw_handle* h, const float* params, int D, const float* X, int L, int downsample,
+               int bf16, float* emb, float* halfwidth) {
+    if (!h || !params || !X || !emb || L < 1 || D < 1 || D > kEncChannels || downsample < 1)
+        return DTW_ERR_INVALID;
+    if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(emb) ||
+        (halfwidth && !is_device_ptr(halfwidth)))
+        return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    const int Lc = (L + downsample - 1) / downsample;
+    const EncSeq q = enc_seq(0, Lc, D);
+    int rc = grow(h, &h->enc, &h->enc_cap, q.total);
+    if (rc != DTW_OK) return rc;
+    const EncLayout pl = enc_layout(D);
+    rc = enc_forward(h, params, pl, D, X, L, downsample, bf16 != 0, q);
+    if (rc != DTW_OK) return rc;
+    CU(cudaMemcpyAsync(emb, ef(h, q.E), sizeof(float) * (size_t)Lc * kEncEmbed,
+                       cudaMemcpyDeviceToDevice, h->stream));
+    if (halfwidth)
+        CU(cudaMemcpyAsync(halfwidth, ef(h, q.HW), sizeof(float) * (size_t)Lc,
+                           cudaMemcpyDeviceToDevice, h->stream));
+    return DTW_OK;
+}
+
+int dtw_encoder_grad(dtw_handle* h, const float* params, int D, int downsample, const float* A,
+                     int La, const float* B, int Lb, const int32_t* path, const int* path_len,
+                     int mode, float* grad, float* loss) {
+    if (!h || !params || !A || !B || !path || !path_len || !grad || !loss || La < 1 || Lb < 1 ||
+        D < 1 || D > kEncChannels || downsample < 2 || (mode != 0 && mode != 1))
+        return DTW_ERR_INVALID;
+    if (!is_device_ptr(params) || !is_device_ptr(A) || !is_device_ptr(B) ||
+        !is_device_ptr(path) || !is_device_ptr(path_len) || !is_device_ptr(grad) ||
+        !is_device_ptr(loss))
+        return DTW_ERR_INVALID;
+    const int Lac = (La + downsample - 1) / downsample, Lbc = (Lb + downsample - 1) / downsample;
+    if (!reachable(La, Lb) || !reachable(Lac, Lbc)) return DTW_ERR_UNREACHABLE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    cudaStream_t s = h->stream;
+    h->band_nstrips = 0;  // the band buffer may move
+    const EncBuf eb = enc_buf(Lac, Lbc, D);
+    int rc = grow(h, &h->enc, &h->enc_cap, eb.total);
+    if (rc != DTW_OK) return rc;
+    const EncLayout pl = enc_layout(D);
+    rc = enc_forward(h, params, pl, D, A, La, downsample, 0, eb.a);
+    if (rc == DTW_OK) rc = enc_forward(h, params, pl, D, B, Lb, downsample, 0, eb.b);
+    if (rc != DTW_OK) return rc;
+    if (mode == 0) {
+        int* tgt = reinterpret_cast<int*>(h->enc + eb.tgt);
+        CU(launch_targets(path, path_len, std::min(La, Lb), downsample, Lac, Lbc,
+                          reinterpret_cast<unsigned long long*>(h->enc + eb.jsum),
+                          reinterpret_cast<int*>(h->enc + eb.cnt), tgt, s));
+        CU(launch_loss_emb(ef(h, eb.a.E), Lac, ef(h, eb.b.E), Lbc, tgt, ef(h, eb.a.G),
+                           ef(h, eb.b.G), loss, s));
+        rc = enc_backward(h, params, pl, D, Lac, eb.a, grad);
+        if (rc == DTW_OK) rc = enc_backward(h, params, pl, D, Lbc, eb.b, grad);
+        return rc;
+    }
+    // mode 1: the coarse path on the current embeddings, the half-width each
+    // coarse row of A needs, and the width head's gradient (trunk frozen)
+    const BandBuf bb = band_buf(Lac, Lbc, kEncEmbed, 1, false);
+    rc = grow(h, &h->band, &h->band_cap, bb.total);
+    if (rc != DTW_OK) return rc;
+    int32_t* cpath = reinterpret_cast<int32_t*>(h->band + bb.cp);
+    int* clen = reinterpret_cast<int*>(h->band + bb.cl);
+    rc = align_device(h, ef(h, eb.a.E), Lac, ef(h, eb.b.E), Lbc, kEncEmbed, defaults(), cpath,
+                      clen, nullptr);
+    if (rc != DTW_OK) return rc;
+    CU(launch_width_target(cpath, clen, path, path_len, downsample, Lac, (float)DTW_BAND_WMIN,
+                           (float)DTW_BAND_WMAX, ef(h, eb.wt), s));
+    CU(launch_loss_width(ef(h, eb.a.S), ef(h, eb.wt), Lac, ef(h, eb.dS), loss, s));
+    CU(launch_outer(ef(h, eb.dS), 1, ef(h, eb.a.H3), kEncChannels, Lac, grad + pl.W5, s));
+    CU(launch_outer(ef(h, eb.dS), 1, nullptr, 1, Lac, grad + pl.b5, s));
+    return DTW_OK;
+}
+
+int dtw_encoder_adam(dtw_handle* h, int n, float* params, float* grad, float* m, float* v,
+                     int step, float lr) {
+    if (!h || n < 1 || !params || !grad || !m || !v || step < 1 || !(lr > 0.f))
+        return DTW_ERR_INVALID;
+    if (!is_device_ptr(params) || !is_device_ptr(grad) || !is_device_ptr(m) || !is_device_ptr(v))
+        return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    CU(launch_adam(n, params, grad, m, v, step, lr, 0.9f, 0.999f, 1e-8f, h->stream));
+    return DTW_OK;
+}
+
+int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
+                      const dtw_options* opt, const float* params, int downsample, int bf16,
+                      int32_t* path, int cap, int* path_len, float* total_cost, int* fell_back) {
+    dtw_options o;
+    int rc = band_checks(h, A, La, B, Lb, D, opt, downsample, path, cap, path_len, total_cost, &o);
+    if (rc != DTW_OK) return rc;
+    if (!params || !is_device_ptr(params) || D > kEncChannels) return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    if (fell_back) *fell_back = 0;
+    h->band_nstrips = 0;
+    const int Lac = (La + downsample - 1) / downsample, Lbc = (Lb + downsample - 1) / downsample;
+    if (downsample == 1 || !reachable(Lac, Lbc)) {
+        if (fell_back) *fell_back = 1;
+        return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
+    }
+    const EncBuf eb = enc_buf(Lac, Lbc, D);
+    rc = grow(h, &h->enc, &h->enc_cap, eb.total);
+    if (rc != DTW_OK) return rc;
+    const int nstrips = (La + strip_rows(3) - 1) / strip_rows(3);
+    const BandBuf bb = band_buf(Lac, Lbc, kEncEmbed, nstrips, false);
+    rc = grow(h, &h->band, &h->band_cap, bb.total);
+    if (rc != DTW_OK) return rc;
+    const EncLayout pl = enc_layout(D);
+    rc = enc_forward(h, params, pl, D, A, La, downsample, bf16 != 0, eb.a);
+    if (rc == DTW_OK) rc = enc_forward(h, params, pl, D, B, Lb, downsample, bf16 != 0, eb.b);
+    if (rc != DTW_OK) return rc;
+    return band_align(h, A, La, B, Lb, D, o, downsample, ef(h, eb.a.E), Lac, ef(h, eb.b.E), Lbc,
+                      kEncEmbed, 0, ef(h, eb.a.HW), bb, path, path_len, total_cost, fell_back);
+}
+
+int dtw_band_cells(dtw_handle* h, long long* cells) {
+    if (!h || !cells) return DTW_ERR_INVALID;
+    *cells = 0;
+    if (h->band_nstrips <= 0) return DTW_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    std::vector<int2> r(h->band_nstrips);
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpy(r.data(), h->band_ranges, sizeof(int2) * r.size(), cudaMemcpyDeviceToHost));
+    long long c = 0;
+    for (int q = 0; q < h->band_nstrips; ++q) {
+        const int x = r[q].x * 8, y = std::min(r[q].y * 8, h->band_Lb);
+        c += (long long)std::max(y - x, 0) * h->band_rps;
+    }
+    *cells = c;
     return DTW_OK;
 }
 

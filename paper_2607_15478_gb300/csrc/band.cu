@@ -6,7 +6,8 @@
 //   k_pool         average of each window of ds frames (the last window may
 //                  be shorter)
 //   k_band_ranges  per strip of the fine DP, the 8-column blocks within
-//                  `w` columns of the upsampled coarse path over the strip's
+//                  `w` columns (or the per-row predicted half-width of the
+//                  learned band) of the upsampled coarse path over the strip's
 //                  rows, widened to be monotone in the strip (the banded DP
 //                  needs the start and the end of the ranges non-decreasing)
 //   k_band_touch   whether the banded path comes within one block of a side
@@ -32,8 +33,8 @@ __global__ void k_pool(const float* __restrict__ X, int L, int D, int ds, float*
 
 // One thread per strip (k_band_monotone then widens the ranges to monotone).
 __global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __restrict__ clen,
-                              int ds, int w, int La, int Lb, int nstrips, int rps,
-                              int2* __restrict__ ranges) {
+                              int ds, int w, const float* __restrict__ wrow, int Lac, int La,
+                              int Lb, int nstrips, int rps, int2* __restrict__ ranges) {
     const int n = *clen;
     const int nsub = (Lb + 7) / 8;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,6 +62,11 @@ __global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __re
         if (jmax < 0) {  // cannot happen for a path covering every coarse row
             jmin = 0;
             jmax = (Lb - 1) / ds;
+        }
+        if (wrow) {  // the widest predicted half-width of the coarse rows around the strip
+            float wm = 0.f;
+            for (int i = max(icl, 0); i <= min(ich, Lac - 1); ++i) wm = fmaxf(wm, wrow[i]);
+            w = (int)ceilf(fminf(wm, (float)Lb));
         }
         const int jlo = max(jmin * ds - w, 0);
         const int jhi = min((jmax + 1) * ds - 1 + w, Lb - 1);
@@ -101,11 +107,13 @@ cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w, int La,
-                               int Lb, int nstrips, int rps, int2* ranges, cudaStream_t s) {
+cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w,
+                               const float* wrow, int Lac, int La, int Lb, int nstrips, int rps,
+                               int2* ranges, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (nstrips + threads - 1) / threads;
-    k_band_ranges<<<blocks, threads, 0, s>>>(cpath, clen, ds, w, La, Lb, nstrips, rps, ranges);
+    k_band_ranges<<<blocks, threads, 0, s>>>(cpath, clen, ds, w, wrow, Lac, La, Lb, nstrips, rps,
+                                             ranges);
     k_band_monotone<<<1, 32, 0, s>>>(nstrips, ranges);
     return cudaGetLastError();
 }

@@ -35,6 +35,7 @@ namespace {
 constexpr int kGhostLane = 31;
 constexpr int kOutLane = 30;    // holds the strip's two bottom rows
 constexpr int kCostSlots = 4;   // sub-chunks of costs in flight per strip
+static_assert(kRingBlk >= 4, "the DP warp waits for output ring blocks four at a time");
 
 // One slot holds the 8 costs of each of a lane's R rows: float4 q of lane l
 // (q = 2 k + half) at [q][l], so a warp's 16-byte accesses are contiguous.
@@ -495,10 +496,15 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                 gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
             }
             if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
-            // the output block must have been read below
-            if (to_ring && !mbar_wait(bar_at(bempty_out, to % kRingBlk),
-                                      use_parity(to, kRingBlk) ^ 1u, p.ctl, p.timeout_ns, 2))
-                return;
+            // the output blocks must have been read below: the consumer
+            // empties them in order, so once the previous use of block to+3
+            // is consumed so are those of to .. to+2 (one wait per 4 blocks)
+            if (to_ring && ((n - rg.x) & 3) == 0) {
+                const unsigned tl = to + 3u;
+                if (!mbar_wait(bar_at(bempty_out, tl % kRingBlk), use_parity(tl, kRingBlk) ^ 1u,
+                               p.ctl, p.timeout_ns, 2))
+                    return;
+            }
 
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
             float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1

@@ -179,10 +179,50 @@ int padded_dim(int D);
 // coarse path (cpath, *clen cells) scaled by ds, widened to monotone; *touch
 // = 1 if the banded path (path, *plen cells) comes within one block of a
 // side of the band that is not the side of the matrix.
+// wrow (may be null): per coarse row of A a half-width in fine frames that
+// replaces w (the largest over the coarse rows next to a strip is used).
 cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStream_t s);
-cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w, int La,
-                               int Lb, int nstrips, int rps, int2* ranges, cudaStream_t s);
+cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w,
+                               const float* wrow, int Lac, int La, int Lb, int nstrips, int rps,
+                               int2* ranges, cudaStream_t s);
 cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
                               const int2* ranges, int* touch, cudaStream_t s);
+
+// Band encoder (encoder.cu).  Parameter offsets (floats) of the flat
+// parameter array for input dimension D; see pardtw.h for the layout.
+constexpr int kEncChannels = 64;
+constexpr int kEncEmbed = 16;
+constexpr int kEncKernel = 5;
+struct EncLayout {
+    size_t W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, count;
+};
+EncLayout enc_layout(int D);
+cudaError_t launch_pool_norm(const float* X, int L, int D, int ds, float* Y, cudaStream_t s);
+// conv5 of L rows: forward (bwd = 0: W [64][Cin][5], bias, relu) or the
+// backward-data pass (bwd = 1: W the forward weight [64][64][5] read
+// transposed and flipped, X masked by mask > 0); bf16 rounds inputs and
+// weights (forward only).
+cudaError_t launch_conv(const float* X, const float* mask, int L, int Cin, const float* W,
+                        const float* b, int relu, int bwd, int bf16, float* Y, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const float* X, int L, int Cin, const float* dY, const float* Yout,
+                              float* dW, float* db, cudaStream_t s);
+cudaError_t launch_embed(const float* H, int L, const float* params, const EncLayout& p, int bf16,
+                         float wmin, float wmax, float* Emb, float* invn, float* S, float* HW,
+                         cudaStream_t s);
+cudaError_t launch_embed_bwd(const float* Emb, const float* invn, int L, const float* W4,
+                             float* G, float* dH, cudaStream_t s);
+cudaError_t launch_outer(const float* U, int na, const float* V, int nb, int L, float* out,
+                         cudaStream_t s);
+cudaError_t launch_targets(const int32_t* path, const int* plen, int cap, int ds, int Lac, int Lbc,
+                           unsigned long long* jsum, int* cnt, int* tgt, cudaStream_t s);
+cudaError_t launch_loss_emb(const float* eA, int Lac, const float* eB, int Lbc, const int* tgt,
+                            float* gA, float* gB, float* loss, cudaStream_t s);
+cudaError_t launch_width_target(const int32_t* cpath, const int* clen, const int32_t* path,
+                                const int* plen, int ds, int Lac, float wmin, float wmax,
+                                float* wt, cudaStream_t s);
+cudaError_t launch_loss_width(const float* S, const float* wt, int Lac, float* dS, float* loss,
+                              cudaStream_t s);
+cudaError_t launch_adam(int n, float* P, float* G, float* M, float* V, int step, float lr,
+                        float b1, float b2, float eps, cudaStream_t s);
 
 }  // namespace pardtw

@@ -34,7 +34,16 @@ DTW_COST_BF16 = 1
 EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destroy",
            "dtw_set_stream", "dtw_workspace_size", "dtw_cost", "dtw_align", "dtw_align_many",
            "dtw_enable_timing", "dtw_stage_times", "dtw_align_static",
-           "dtw_static_scratch_bytes", "dtw_align_banded")
+           "dtw_static_scratch_bytes", "dtw_align_banded", "dtw_encoder_param_count",
+           "dtw_encode", "dtw_encoder_grad", "dtw_encoder_adam", "dtw_align_learned",
+           "dtw_band_cells")
+
+# learned band (include/pardtw.h)
+DTW_BAND_WMIN = 256
+DTW_BAND_WMAX = 2048
+ENC_CHANNELS = 64
+ENC_EMBED = 16
+ENC_KERNEL = 5
 
 
 class PardtwError(RuntimeError):
@@ -87,8 +96,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      vp]
     lib.dtw_static_scratch_bytes.argtypes = []
     lib.dtw_static_scratch_bytes.restype = ctypes.c_size_t
+    lib.dtw_encoder_param_count.argtypes = [ci]
+    lib.dtw_encoder_param_count.restype = ctypes.c_size_t
+    lib.dtw_encode.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, vp]
+    lib.dtw_encoder_grad.argtypes = [vp, vp, ci, ci, vp, ci, vp, ci, vp, vp, ci, vp, vp]
+    lib.dtw_encoder_adam.argtypes = [vp, ci, vp, vp, vp, vp, ci, cf]
+    lib.dtw_align_learned.argtypes = [vp, vp, ci, vp, ci, ci, ctypes.POINTER(Options), vp, ci,
+                                      ci, vp, ci, vp, vp, ctypes.POINTER(ci)]
+    lib.dtw_band_cells.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTS:
-        if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes"):
+        if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes",
+                        "dtw_encoder_param_count"):
             getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -207,6 +225,55 @@ def dtw_align_banded(h: int, A, B, path, path_len, total=None, downsample: int =
         path.data_ptr(), path.shape[0], path_len.data_ptr(),
         total.data_ptr() if total is not None else None, ctypes.byref(fb)), "dtw_align_banded")
     return bool(fb.value)
+
+
+def dtw_encoder_param_count(D: int) -> int:
+    return int(load_library().dtw_encoder_param_count(int(D)))
+
+
+def dtw_encode(h: int, params, X, emb, halfwidth=None, downsample: int = 8,
+               bf16: bool = False) -> None:
+    """Band encoder forward of one sequence (include/pardtw.h)."""
+    X = _features(X)
+    _check(load_library().dtw_encode(
+        h, params.data_ptr(), X.shape[1], X.data_ptr(), X.shape[0], int(downsample), int(bf16),
+        emb.data_ptr(), halfwidth.data_ptr() if halfwidth is not None else None), "dtw_encode")
+
+
+def dtw_encoder_grad(h: int, params, A, B, path, path_len, mode: int, grad, loss,
+                     downsample: int = 8) -> None:
+    """Adds one pair's loss gradient (mode 0: embedding, 1: half-width) to grad."""
+    A, B = _features(A), _features(B)
+    _check(load_library().dtw_encoder_grad(
+        h, params.data_ptr(), A.shape[1], int(downsample), A.data_ptr(), A.shape[0],
+        B.data_ptr(), B.shape[0], path.data_ptr(), path_len.data_ptr(), int(mode),
+        grad.data_ptr(), loss.data_ptr()), "dtw_encoder_grad")
+
+
+def dtw_encoder_adam(h: int, params, grad, m, v, step: int, lr: float) -> None:
+    _check(load_library().dtw_encoder_adam(
+        h, params.numel(), params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(),
+        int(step), float(lr)), "dtw_encoder_adam")
+
+
+def dtw_align_learned(h: int, A, B, params, path, path_len, total=None, downsample: int = 8,
+                      bf16: bool = True, options: Options | None = None) -> bool:
+    """Exact DTW inside the learned band; returns True when it fell back to
+    the full exact DTW."""
+    A, B = _features(A), _features(B)
+    fb = ctypes.c_int(0)
+    _check(load_library().dtw_align_learned(
+        h, A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1],
+        ctypes.byref(options) if options else None, params.data_ptr(), int(downsample),
+        int(bf16), path.data_ptr(), path.shape[0], path_len.data_ptr(),
+        total.data_ptr() if total is not None else None, ctypes.byref(fb)), "dtw_align_learned")
+    return bool(fb.value)
+
+
+def dtw_band_cells(h: int) -> int:
+    c = ctypes.c_longlong(0)
+    _check(load_library().dtw_band_cells(h, ctypes.byref(c)), "dtw_band_cells")
+    return int(c.value)
 
 
 def dtw_align_static(A, B, path, path_len, total=None, options: Options | None = None,
@@ -330,6 +397,38 @@ class Aligner:
         if n < 0:
             raise PardtwError(-n, "dtw_align_banded (device)")
         return path[:n], float(tot.item()), fb
+
+    def align_learned(self, A, B, params, downsample: int = 8, bf16: bool = True, **opts):
+        """Exact DTW in the learned band; returns (path, total, fell_back)."""
+        import torch
+        A, B = _features(A), _features(B)
+        cap = min(A.shape[0], B.shape[0])
+        path = torch.empty((cap, 2), dtype=torch.int32, device=A.device)
+        plen = torch.zeros(1, dtype=torch.int32, device=A.device)
+        tot = torch.zeros(1, dtype=torch.float32, device=A.device)
+        self._enter()
+        fb = dtw_align_learned(self.h, A, B, params, path, plen, tot, downsample, bf16,
+                               make_options(**opts) if opts else None)
+        self._leave()
+        n = int(plen.item())
+        if n < 0:
+            raise PardtwError(-n, "dtw_align_learned (device)")
+        return path[:n], float(tot.item()), fb
+
+    def encode(self, X, params, downsample: int = 8, bf16: bool = False):
+        """Band encoder forward: (embeddings, half-widths) of one sequence."""
+        import torch
+        X = _features(X)
+        Lc = (X.shape[0] + downsample - 1) // downsample
+        emb = torch.empty((Lc, ENC_EMBED), dtype=torch.float32, device=X.device)
+        hw = torch.empty(Lc, dtype=torch.float32, device=X.device)
+        self._enter()
+        dtw_encode(self.h, params, X, emb, hw, downsample, bf16)
+        self._leave()
+        return emb, hw
+
+    def band_cells(self) -> int:
+        return dtw_band_cells(self.h)
 
     def align_many(self, As: List, Bs: List, **opts):
         """Align independent pairs; returns (list of paths or None, costs, statuses)."""

@@ -37,6 +37,7 @@ __all__ = [
     "WarpedPair",
     "config_pair",
     "config_batch",
+    "band_training_pair",
     "CONFIGS",
 ]
 
@@ -185,3 +186,19 @@ def config_batch(config: int = 2, n_pairs: int | None = None,
         out.append(warped_pair(rng, La, Lb, c["D"], kind=c["kind"], knots=c["knots"],
                                tmin=c["tmin"], tmax=c["tmax"], sigma=c["sigma"]))
     return out
+
+
+def band_training_pair(k: int, La: int | None = None) -> WarpedPair:
+    """Pair ``k`` of the band encoder's training set: the recipe of the long
+    learned-band workload (config 4: chroma-like, tempo in [0.6, 1.6],
+    noise 0.05) at La ~ U[5000, 20000], Lb = round(La * U[1.0, 1.3]), with the
+    knot density of that workload (256 knots per 100000 frames, at least 8).
+    Seeds 1000 * 4 + 1000 + k, disjoint from the workload's own pair."""
+    c = CONFIGS[4]
+    rng = rng_for(4, 1000 + k)
+    if La is None:
+        La = int(rng.integers(5000, 20001))
+    Lb = int(round(La * rng.uniform(1.0, 1.3)))
+    knots = max(8, int(round(256 * La / 100000)))
+    return warped_pair(rng, La, Lb, c["D"], kind=c["kind"], knots=knots, tmin=c["tmin"],
+                       tmax=c["tmax"], sigma=c["sigma"])

@@ -4,6 +4,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2607_15478_gb300 import build as pbuild
@@ -84,3 +85,27 @@ def test_create_without_gpu_fails_cleanly(lib):
     rc = lib.dtw_create(ctypes.byref(h), 0, None)
     assert rc in (pardtw.DTW_ERR_CUDA, pardtw.DTW_ERR_INVALID)
     assert h.value is None
+
+
+def test_encoder_parameter_count_matches_layout(lib):
+    # the flat parameter array of the learned band's encoder (include/pardtw.h)
+    from paper_2607_15478_gb300 import band_train
+    for D in (1, 12, 32, 64):
+        lay, n = band_train.layout(D)
+        assert pardtw.dtw_encoder_param_count(D) == n
+        assert n == 64 * D * 5 + 64 + 2 * (64 * 64 * 5 + 64) + 16 * 64 + 16 + 64 + 1
+    assert pardtw.dtw_encoder_param_count(0) == 0
+    assert pardtw.dtw_encoder_param_count(65) == 0
+
+
+def test_encoder_init_params():
+    from paper_2607_15478_gb300 import band_train
+    p = band_train.init_params(12, seed=0)
+    lay, n = band_train.layout(12)
+    assert p.shape == (n,) and p.dtype.name == "float32"
+    o, shp = lay["W2"]
+    w2 = p[o:o + 64 * 64 * 5]
+    lim = (6.0 / (64 * 5)) ** 0.5
+    assert np.abs(w2).max() <= lim and abs(w2.std() - lim / 3 ** 0.5) < 0.05 * lim
+    assert p[lay["b5"][0]] == -2.0
+    assert np.array_equal(p, band_train.init_params(12, seed=0))
