@@ -38,6 +38,9 @@ KERNELS_PER_STEP = 6  # normalise, DP, band map, band chain, band walks, emit
 # learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (6), band
 # ranges (2), banded alignment (6), band-side test (1)
 KERNELS_PER_LEARNED_STEP = 10 + 6 + 2 + 6 + 1
+# WSDTW: batched normalisation, subsequence DP, segment DP, fragment
+# backtraces, compaction
+KERNELS_PER_WSDTW_STEP = 5
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -761,6 +764,114 @@ def run_band(args):
     al.close()
 
 
+def run_wsdtw(args):
+    """WSDTW (Sec. II-C) of the 100000x12 query against the 126231x12 reference
+    of the long pair (tempo 0.6-1.6, 256 knots) with N = 32 fragments (the
+    paper's setting for the Mazurka data): one batched subsequence DP over all
+    fragments, the segment-level DP, the fragment backtraces.  value = La x Lb
+    frame-level cells per second."""
+    import numpy as np
+    import torch
+    ws_, rank, local = dist_env()
+    dev = torch.device("cuda", local if ws_ > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2607_15478_gb300 import pardtw, synth
+    wp = synth.config_pair(4, pair=rank, La=args.La, Lb=args.Lb)
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    N = args.nfrag
+    cells = La * Lb
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    A = torch.from_numpy(wp.A).to(dev)
+    B = torch.from_numpy(wp.B).to(dev)
+    path = torch.empty((La, 2), dtype=torch.int32, device=dev)
+    plen = torch.zeros(1, dtype=torch.int32, device=dev)
+    ends = torch.empty(N, dtype=torch.int32, device=dev)
+    tot = torch.zeros(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            pardtw.dtw_wsdtw(al.h, A, B, N, path, plen, ends, tot)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        step()
+    if int(plen.item()) <= 0:
+        raise RuntimeError(f"wsdtw failed: {pardtw.status_string(-int(plen.item()))}")
+    step_ms, dp_ms = [], []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(args.steps):
+            step_ms.append(step())
+            dp_ms.append(al.stage_times()[1])
+        clk.mark_end()
+    t = sum(step_ms) / 1e3
+    value = cells * args.steps / t / 1e9
+    # e2e: host features in, path out, through the public API
+    Ah = torch.from_numpy(wp.A).pin_memory()
+    Bh = torch.from_numpy(wp.B).pin_memory()
+    al.enable_timing(False)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            Ad = Ah.to(dev, non_blocking=True)
+            Bd = Bh.to(dev, non_blocking=True)
+        pth, _, _ = al.wsdtw(Ad, Bd, N)
+        ph = pth.cpu()
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = sum(e2e_t[args.warmup:])
+    peaks, src = measured_peaks()
+    clock = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6
+    ops_per_cell = D + 6
+    dp_avg = statistics.mean(dp_ms) / 1e3
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import wsdtw as ows
+        nf = 2  # two fragments of the same pair, the oracle's subsequence DP
+        r0, n0 = ows.fragments(La, N)[0]
+        a_rows = n0 * nf
+        t0 = time.perf_counter()
+        ows.wsdtw(wp.A[:a_rows], wp.B, nf)
+        dt = time.perf_counter() - t0
+        cpu = {"value": a_rows * Lb / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"WSDTW of the first {nf} fragments ({a_rows} rows) against all "
+                         f"{Lb} frames, FP64 numpy row sweep, single thread ({dt:.1f} s)"}
+    _rank0_line({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"WSDTW N={N}: query {La}x12 vs reference {Lb}x12 chroma-like, "
+                               f"warped (256 knots, tempo 0.6-1.6)",
+                   "La": La, "Lb": Lb, "D": D, "nfrag": N,
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU",
+                   "value_definition": "La x Lb frame-level cells over the step time"},
+        "roofline": {"bound": "alu", "achieved": cells * ops_per_cell / dp_avg / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "T FP32 lane-ops/s",
+                     "frac": cells * ops_per_cell / dp_avg / peak_ops, "traffic": None,
+                     "kernel": "k_dp_split subsequence mode over all fragments (one launch)",
+                     "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg},
+        "cpu_baseline": cpu,
+        "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": (La + Lb) * D * 4,
+                "d2h_bytes_per_step": int(ph.shape[0]) * 8},
+        "gpu_launches": KERNELS_PER_WSDTW_STEP * args.steps,
+        "clocks": clk.summary(),
+    })
+    al.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -771,10 +882,12 @@ def main():
     ap.add_argument("--La", type=int, default=None,
                     help="override the pair's lengths (same recipe; for profiling smaller cases)")
     ap.add_argument("--Lb", type=int, default=None)
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4],
+    ap.add_argument("--nfrag", type=int, default=32, help="WSDTW fragments (--config 5)")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 4, 5],
                     help="1: the 20000x25000 pair (default, the headline line); 2: the "
                          "256-pair batch; 3: the D = 128 pair with the BF16 cost; 4: the "
-                         "100000x(100000-130000) pair in the learned band")
+                         "100000x(100000-130000) pair in the learned band; 5: WSDTW of that "
+                         "pair with --nfrag fragments")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -786,6 +899,8 @@ def main():
         run_precision(args)
     elif args.config == 4:
         run_band(args)
+    elif args.config == 5:
+        run_wsdtw(args)
     else:
         run_ours(args)
 

@@ -186,6 +186,36 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
                      const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
                      int cap, int* path_len, float* total_cost, int* fell_back);
 
+/* ---- weakly-ordered Segmental DTW (Sec. II-C) ------------------------------ */
+/* WSDTW of the query A (La x D) against the reference B (Lb x D) with nfrag
+ * fragments of A:
+ *   1. fragment k holds rows floor(k La / nfrag) .. floor((k+1) La / nfrag) - 1;
+ *   2. subsequence DTW of every fragment against all of B: steps (query,
+ *      reference) (1,1), (1,2), (2,1) with weights 1, 1, 2, start anywhere in
+ *      B (D_k[0][j] = C_k[0][j]), end anywhere; FP32, the same cost, tie order
+ *      and kernels as dtw_align (the fragments run as one batch);
+ *   3. C_seg[k][j] = D_k[last row][j];
+ *   4. D_seg[k][j] = min(D_seg[k][j-1], D_seg[k-1][j - delta_k] + C_seg[k][j])
+ *      with delta_k = floor(len_k / 2) (the shortest match of a fragment of
+ *      len_k frames), D_seg[0][j] = min(D_seg[0][j-1], C_seg[0][j]); a match
+ *      replaces the skip only when strictly smaller;
+ *   5. every fragment's path from (last row, e_k) back to its first row.
+ *   path       : device int32 pairs (row of A, frame of B), cap >= La; the
+ *                fragments' paths one after another (each ascending), so the
+ *                frame may step back at a fragment boundary (Sec. II-C)
+ *   path_len   : device int; the number of pairs, or -status on a device-side
+ *                failure (DTW_ERR_UNREACHABLE when B is too short to place the
+ *                fragments in order)
+ *   ends       : device int32[nfrag], end frame e_k of every fragment (may be NULL)
+ *   total_cost : device float, D_seg[nfrag-1][Lb-1] (may be NULL)
+ * D <= 32, 1 <= nfrag <= La.  Asynchronous on the handle's stream. */
+int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, int nfrag,
+              int32_t* path, int cap, int* path_len, int32_t* ends, float* total_cost);
+
+/* C_seg of the last dtw_wsdtw call on this handle (nfrag x Lb floats, row-major,
+ * device), for inspection and tests; nfrag and Lb must be those of that call. */
+int dtw_wsdtw_cseg(dtw_handle* h, int nfrag, int Lb, float* cseg);
+
 /* ---- learned band ---------------------------------------------------------- */
 /* A band predicted by a small network instead of a fixed half-width.  The
  * paper names bands and multiscale DTW only as related ways to cut the

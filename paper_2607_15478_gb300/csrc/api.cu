@@ -39,6 +39,8 @@ struct dtw_handle {
     const int2* band_ranges = nullptr;
     char* enc = nullptr;         // band encoder activations and gradients
     size_t enc_cap = 0;
+    char* wsd = nullptr;         // WSDTW: last rows, segment DP, fragment paths
+    size_t wsd_cap = 0;
 };
 
 namespace {
@@ -257,6 +259,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     a.Bhat = Bhat;
     a.Bbf = Bbf;
     a.ranges = ranges;
+    a.lastrow = nullptr;
     a.bp = bp;
     a.gborder = h->border;
     a.ctl = ctl;
@@ -309,9 +312,19 @@ int validate(const float* A, int La, const float* B, int Lb, int D) {
 // The batched path of dtw_align_many (device inputs and outputs, D <= 32):
 // every pair of `idx` in one batched normalisation, one persistent DP launch
 // over a (pair, strip group) work queue and one batched backtrace.
+// Subsequence mode of align_batch (WSDTW): the DP of every pair in
+// subsequence form, its last row into lastrow + k * stride, no backtrace;
+// bts_out[k] receives pair k's backtrace geometry and control block.
+struct SubseqBatch {
+    float* lastrow;
+    size_t stride;
+    std::vector<BtArgs>* bts_out;
+};
+
 int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, const int* La,
                 const float* const* B, const int* Lb, int D, const dtw_options& o, int R,
-                int32_t* paths, const int64_t* path_off, int* path_len, float* cost) {
+                int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
+                const SubseqBatch* sub = nullptr) {
     const int m = (int)idx.size();
     if (m == 0) return DTW_OK;
     // The work queue runs the pairs with the longest sweeps first, so that the
@@ -401,6 +414,7 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         a.epoch = epoch;
         a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
         a.skip_publish = o.debug_skip_publish;
+        a.lastrow = sub ? sub->lastrow + (size_t)k * sub->stride : nullptr;
         BtArgs& bt = bts[q];
         bt.bp = bpw;
         bt.La = La[k];
@@ -411,11 +425,12 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         bt.ctl = ctl;
         bt.e_final = e_final;
         bt.mu = o.cost_shift;
-        bt.path = paths + 2 * path_off[k];
-        bt.path_len = path_len + k;
-        bt.total = cost ? cost + k : nullptr;
+        bt.path = sub ? nullptr : paths + 2 * path_off[k];
+        bt.path_len = sub ? nullptr : path_len + k;
+        bt.total = (cost && !sub) ? cost + k : nullptr;
         bt.scratch = base + L.off_bt;
         bt.ranges = nullptr;
+        if (sub) (*sub->bts_out)[k] = bt;
     }
     CU(cudaMemcpyAsync(ws + off_dp, dps.data(), sizeof(DpArgs) * m, cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(ws + off_norm, nas.data(), sizeof(NormArgs) * m, cudaMemcpyHostToDevice,
@@ -428,6 +443,17 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
     CU(launch_normalise_many(reinterpret_cast<const NormArgs*>(ws + off_norm), m, max_frames, D,
                              dp, ticket, s));
     if (h->timing) CU(cudaEventRecord(h->ev[1], s));
+    if (sub) {
+        CU(launch_dp_subseq_many(reinterpret_cast<const DpArgs*>(ws + off_dp),
+                                 reinterpret_cast<const int*>(ws + off_item), m, item0[m], ticket,
+                                 dp, h->num_sms, s));
+        if (h->timing) {
+            CU(cudaEventRecord(h->ev[2], s));
+            CU(cudaEventRecord(h->ev[3], s));
+            h->timed = true;
+        }
+        return DTW_OK;
+    }
     CU(launch_dp_split_many(reinterpret_cast<const DpArgs*>(ws + off_dp),
                             reinterpret_cast<const int*>(ws + off_item), m, item0[m], ticket, dp,
                             R, h->num_sms, s));
@@ -503,6 +529,7 @@ int dtw_destroy(dtw_handle* h) {
     if (h->border) cudaFree(h->border);
     if (h->band) cudaFree(h->band);
     if (h->enc) cudaFree(h->enc);
+    if (h->wsd) cudaFree(h->wsd);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->h_small) cudaFreeHost(h->h_small);
@@ -1053,6 +1080,99 @@ int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int
     if (rc != DTW_OK) return rc;
     return band_align(h, A, La, B, Lb, D, o, downsample, ef(h, eb.a.E), Lac, ef(h, eb.b.E), Lbc,
                       kEncEmbed, 0, ef(h, eb.a.HW), bb, path, path_len, total_cost, fell_back);
+}
+
+int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, int nfrag,
+              int32_t* path, int cap, int* path_len, int32_t* ends, float* total_cost) {
+    if (!h || !A || !B || !path || !path_len || La < 1 || Lb < 1 || D < 1 || nfrag < 1 ||
+        nfrag > La || cap < La)
+        return DTW_ERR_INVALID;
+    const int dp = padded_dim(D);
+    if (dp == 0 || !split_supported(dp, 3)) return DTW_ERR_UNSUPPORTED;
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(path) ||
+        !is_device_ptr(path_len) || (ends && !is_device_ptr(ends)) ||
+        (total_cost && !is_device_ptr(total_cost)))
+        return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    cudaStream_t s = h->stream;
+    const int N = nfrag;
+    // step 1: fragments k of rows floor(k La / N) .. floor((k+1) La / N) - 1
+    std::vector<const float*> Ap(N), Bp(N, B);
+    std::vector<int> Lap(N), Lbp(N, Lb), delta(N), idx(N);
+    std::vector<int> row0(N);
+    for (int k = 0; k < N; ++k) {
+        const int r0 = (int)((long long)k * La / N), r1 = (int)((long long)(k + 1) * La / N);
+        row0[k] = r0;
+        Ap[k] = A + (size_t)r0 * D;
+        Lap[k] = r1 - r0;
+        delta[k] = (r1 - r0) / 2;
+        idx[k] = k;
+    }
+    // buffers: last rows, D_seg, arg, ends, deltas, fragments, counts, the
+    // scratch path, total, control block
+    const size_t stride = (size_t)((Lb + kColsPerWord - 1) / kColsPerWord) * kColsPerWord;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    const size_t o_last = take(sizeof(float) * stride * N);
+    const size_t o_dseg = take(sizeof(float) * (size_t)Lb * N);
+    const size_t o_arg = take(sizeof(int) * (size_t)Lb * N);
+    const size_t o_ends = take(sizeof(int) * N);
+    const size_t o_delta = take(sizeof(int) * N);
+    const size_t o_frag = take(sizeof(WsFrag) * N);
+    const size_t o_cnt = take(sizeof(int) * N);
+    const size_t o_scr = take(sizeof(int32_t) * 2 * (size_t)La);
+    const size_t o_tot = take(sizeof(float));
+    const size_t o_ctl = take(sizeof(DevCtl));
+    int rc = grow(h, &h->wsd, &h->wsd_cap, o);
+    if (rc != DTW_OK) return rc;
+    char* w = h->wsd;
+    // step 2 (and the last rows of step 3): the batched subsequence DP
+    dtw_options opt = defaults();
+    std::vector<BtArgs> bts(N);
+    SubseqBatch sb{reinterpret_cast<float*>(w + o_last), stride, &bts};
+    rc = align_batch(h, idx, Ap.data(), Lap.data(), Bp.data(), Lbp.data(), D, opt, 3, nullptr,
+                     nullptr, nullptr, nullptr, &sb);
+    if (rc != DTW_OK) return rc;
+    std::vector<WsFrag> fr(N);
+    for (int k = 0; k < N; ++k) {
+        fr[k].bp = bts[k].bp;
+        fr[k].pctl = bts[k].ctl;
+        fr[k].row0 = row0[k];
+        fr[k].len = Lap[k];
+        fr[k].nchunk = bts[k].nchunk;
+        fr[k].rps = bts[k].rps;
+        fr[k].wpb = bts[k].wpb;
+    }
+    DevCtl* ctl = reinterpret_cast<DevCtl*>(w + o_ctl);
+    int* dends = reinterpret_cast<int*>(w + o_ends);
+    float* dtot = reinterpret_cast<float*>(w + o_tot);
+    CU(cudaMemcpyAsync(w + o_delta, delta.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(w + o_frag, fr.data(), sizeof(WsFrag) * N, cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+    // steps 3-4: the segment-level DP and the end frames; step 5: backtraces
+    const WsFrag* dfr = reinterpret_cast<const WsFrag*>(w + o_frag);
+    CU(launch_seg_dp(dfr, reinterpret_cast<const float*>(w + o_last), stride, N, Lb,
+                     reinterpret_cast<const int*>(w + o_delta), reinterpret_cast<float*>(w + o_dseg),
+                     reinterpret_cast<int*>(w + o_arg), dends, dtot, ctl, s));
+    CU(launch_bt_subseq(dfr, N, dends, reinterpret_cast<int32_t*>(w + o_scr),
+                        reinterpret_cast<int*>(w + o_cnt), path, path_len, ctl, s));
+    if (ends) CU(cudaMemcpyAsync(ends, dends, sizeof(int) * N, cudaMemcpyDeviceToDevice, s));
+    if (total_cost)
+        CU(cudaMemcpyAsync(total_cost, dtot, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return DTW_OK;
+}
+
+int dtw_wsdtw_cseg(dtw_handle* h, int nfrag, int Lb, float* cseg) {
+    if (!h || !cseg || nfrag < 1 || Lb < 1 || !h->wsd || !is_device_ptr(cseg))
+        return DTW_ERR_INVALID;
+    const size_t stride = (size_t)((Lb + kColsPerWord - 1) / kColsPerWord) * kColsPerWord;
+    if (sizeof(float) * stride * nfrag > h->wsd_cap) return DTW_ERR_INVALID;
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    CU(cudaMemcpy2DAsync(cseg, sizeof(float) * Lb, h->wsd, sizeof(float) * stride,
+                         sizeof(float) * Lb, nfrag, cudaMemcpyDeviceToDevice, h->stream));
+    return DTW_OK;
 }
 
 int dtw_band_cells(dtw_handle* h, long long* cells) {

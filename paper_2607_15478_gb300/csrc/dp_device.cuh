@@ -353,7 +353,9 @@ __device__ __forceinline__ float eq_as_float(float a, float b) {
 // field (see step_of_field) is added to fw[k] at bits 2u, 2u+1 by two FMAs
 // of exact powers of two, so the code costs two compares and no integer or
 // select instruction.
-template <int R>
+// kSubseq: the subsequence DTW of WSDTW (Sec. II-C), weights 1, 1, 2 for
+// (1,1), (1,2), (2,1) instead of 2, 3, 3 (w12 carries the (1,2) weight).
+template <int R, bool kSubseq = false>
 __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, const float* w12,
                                         bool ghost, float g0, float g1, bool origin_here,
                                         float mu, float* cur, float* prv, float& ylp, float* fw,
@@ -369,9 +371,10 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
         float x1p = (k == 0) ? ylp : prv[k - 1];                           // E[i-1][j-2]
         if (k == R - 2) x1p = ghost ? g0 : x1p;
         if (k == R - 1) x1p = ghost ? g1 : x1p;
-        const float c0 = fmaf(2.0f, cost[k], x1);    // from (i-1, j-1)
+        constexpr float w11 = kSubseq ? 1.0f : 2.0f, w21 = kSubseq ? 2.0f : 3.0f;
+        const float c0 = fmaf(w11, cost[k], x1);     // from (i-1, j-1)
         const float c1 = fmaf(w12[k], cost[k], x1p);  // from (i-1, j-2)
-        const float c2 = fmaf(3.0f, cost[k], x2);    // from (i-2, j-1)
+        const float c2 = fmaf(w21, cost[k], x2);     // from (i-2, j-1)
         float mk = min3f(c0, c1, c2);
         fw[k] = fmaf(eq_as_float(c0, mk), bit0, fw[k]);
         fw[k] = fmaf(eq_as_float(c1, mk), bit1, fw[k]);

@@ -405,11 +405,20 @@ __device__ __forceinline__ bool ring_used(const GroupRoles& r, int w) {
     return r.writer;
 }
 
+// cur[k] for a runtime k < R without indexing the register array.
+template <int R>
+__device__ __forceinline__ float pick_row(const float* cur, int k) {
+    float v = cur[0];
+#pragma unroll
+    for (int q = 1; q < R; ++q) v = (k == q) ? cur[q] : v;
+    return v;
+}
+
 // DP warp of `strip` (slot w of group g).  ring: the NS + 1 border rings;
 // bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
 // sub-chunk counts of the input and output rings at the start of this
 // group; csub: that of the cost ring.
-template <int R, int NS, bool kRM>
+template <int R, int NS, bool kRM, bool kSubseq = false>
 __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
@@ -431,9 +440,13 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
     const float mu = p.mu;
     float w12[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) w12[k] = (ghost && k >= R - 2) ? 0.0f : 3.0f;
+    for (int k = 0; k < R; ++k) w12[k] = (ghost && k >= R - 2) ? 0.0f : (kSubseq ? 1.0f : 3.0f);
     const int srcA = (lane + 31) & 31;
     const bool is_origin = (i0 == 0) && !ghost;
+    // subsequence DP: the lane and row slot of row La-1, if this strip holds it
+    const int rl = p.La - 1 - strip * kRows;
+    const bool has_last = kSubseq && rl >= 0 && rl < kRows && lane == rl / R;
+    const int kl = kSubseq ? rl - (rl / R) * R : 0;
     // this strip's sub-chunks, and those its border ring's producer publishes
     // (the strip above; for the first strip of a group the reader, which
     // publishes exactly this strip's range)
@@ -507,6 +520,8 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             }
 
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
+            float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
+            (void)ol;
             float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
 #pragma unroll
             for (int k = 0; k < R; ++k) fw[k] = 0.0f;
@@ -532,9 +547,11 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
-                               (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
-                               ylp, fw, o0[u], o1[u]);
+                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                            is_origin,
+                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
                 }
             } else {
                 // the last, partial sub-chunk (has_next is false)
@@ -544,9 +561,24 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
-                               (h == 0) && (u == 0) && (j0 == 0) && is_origin, mu, cur, prv,
-                               ylp, fw, o0[u], o1[u]);
+                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                            is_origin,
+                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+                }
+            }
+            if constexpr (kSubseq) {
+                if (has_last) {  // row La-1 of these columns
+                    float* dst = p.lastrow + js;
+                    if (nsteps == kSub) {
+                        reinterpret_cast<float4*>(dst)[0] = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                        reinterpret_cast<float4*>(dst)[1] = make_float4(ol[4], ol[5], ol[6], ol[7]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kSub; ++u)
+                            if (u < nsteps) dst[u] = ol[u];
+                    }
                 }
             }
 #pragma unroll
@@ -668,7 +700,7 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
 // group only ever waits on groups that started earlier.
 // kMany: the groups come from a work queue over many pairs (`many`, `item0`,
 // `ticket`; see launch_dp_split_many) instead of the pair `one`.
-template <int DP, int R, int NS, bool kMany, bool kBF>
+template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false>
 __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
                int nmany, int* ticket) {
@@ -782,7 +814,7 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
             }
         } else if (role == 1) {
             if (w < gr.nstrips_here)
-                run_dp<R, NS, kBF>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                run_dp<R, NS, kBF, kSubseq>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
                                    smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
                                    cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]));
         } else if (role == 2) {
@@ -811,26 +843,25 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     }
 }
 
-template <int DP, int R, bool kMany, bool kBF = false>
+template <int DP, int R, bool kMany, bool kBF = false, bool kSubseq = false>
 cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
                      int* ticket, int num_sms, cudaStream_t s) {
     constexpr int NS = kSplitStrips;
     constexpr int kThreads = (2 * NS + 2) * 32;
     const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
+    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq>;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_dp_split<DP, R, NS, kMany, kBF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm,
-                                                          k_dp_split<DP, R, NS, kMany, kBF>, kThreads,
-                                                          smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kThreads, smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int grid = blocks_per_sm * num_sms;
     if (grid > items) grid = items;
-    k_dp_split<DP, R, NS, kMany, kBF><<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
+    kern<<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
     return cudaGetLastError();
 }
 
@@ -874,6 +905,20 @@ cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, in
                                  int* ticket, int dp, int R, int num_sms, cudaStream_t s) {
     if (n <= 0 || total_items <= 0) return cudaSuccess;
     return launch_any<true>(DpArgs{}, many, item0, n, total_items, ticket, dp, R, num_sms, s);
+}
+
+cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, int total_items,
+                                  int* ticket, int dp, int num_sms, cudaStream_t s) {
+    if (n <= 0 || total_items <= 0) return cudaSuccess;
+    const DpArgs none{};
+    switch (dp) {
+        case 4: return launch_t<4, 3, true, false, true>(none, many, item0, n, total_items, ticket, num_sms, s);
+        case 8: return launch_t<8, 3, true, false, true>(none, many, item0, n, total_items, ticket, num_sms, s);
+        case 12: return launch_t<12, 3, true, false, true>(none, many, item0, n, total_items, ticket, num_sms, s);
+        case 16: return launch_t<16, 3, true, false, true>(none, many, item0, n, total_items, ticket, num_sms, s);
+        case 32: return launch_t<32, 3, true, false, true>(none, many, item0, n, total_items, ticket, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 bool split_bf16_supported(int dp) { return dp == 64 || dp == 128; }

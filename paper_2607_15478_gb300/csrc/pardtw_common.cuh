@@ -51,6 +51,8 @@ struct DpArgs {
     const int2* ranges;             // banded DP (warp-pair kernel): per strip the sub-chunks
                                     // [x, y) of 8 columns it sweeps (x even; x and y
                                     // non-decreasing in the strip); null = every column
+    float* lastrow;                 // subsequence DP (WSDTW): the cumulative cost of row
+                                    // La-1 at every column (nchunk * 16 floats), else null
 };
 
 // Backpointer word address of cell (i, j): strip-major, then 16-column chunk,
@@ -117,6 +119,10 @@ bool multirow_supported(int dp, int R);
 // Warp-specialised DP (dp_split.cu): a cost warp and a DP warp per strip,
 // kSplitStrips strips per CTA; R = 2, 3 or 4.
 cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
+// The subsequence DP of WSDTW over a batch (R = 3, dp <= 32): weights 1, 1, 2,
+// free start in row 0, row La-1 of every pair into its DpArgs::lastrow.
+cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, int total_items,
+                                  int* ticket, int dp, int num_sms, cudaStream_t s);
 bool split_supported(int dp, int R);
 // The same DP with the cost from BF16 features and FP32 accumulation on the
 // tensor cores (mma.sync m16n8k16): D padded to 64 or 128, R = 3.
@@ -187,6 +193,25 @@ cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, in
                                int2* ranges, cudaStream_t s);
 cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
                               const int2* ranges, int* touch, cudaStream_t s);
+
+// WSDTW (wsdtw.cu): one fragment of A, its backtrace matrix from the batched
+// subsequence DP and the control block of its DP.
+struct WsFrag {
+    const uint32_t* bp;
+    const DevCtl* pctl;
+    int row0, len;          // first row of A, rows
+    int nchunk, rps, wpb;   // backtrace matrix geometry (see bp_word_index)
+};
+// Segment-level DP over the fragments' last rows (stride floats apart) with
+// shortest matches delta[k]; end frames, total (D_seg[N-1][Lb-1]) and status.
+cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride, int N, int Lb,
+                          const int* delta, float* Dseg, int* arg, int* ends, float* total,
+                          DevCtl* ctl, cudaStream_t s);
+// Fragment backtraces from their end frames into `scratch` (2 La ints), then
+// the concatenated path into `path` and its length (or -status) into path_len.
+cudaError_t launch_bt_subseq(const WsFrag* fr, int N, const int* ends, int32_t* scratch,
+                             int* count, int32_t* path, int* path_len, DevCtl* ctl,
+                             cudaStream_t s);
 
 // Band encoder (encoder.cu).  Parameter offsets (floats) of the flat
 // parameter array for input dimension D; see pardtw.h for the layout.

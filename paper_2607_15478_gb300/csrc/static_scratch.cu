@@ -151,6 +151,7 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     a.Bhat = Bt;
     a.Bbf = nullptr;
     a.ranges = nullptr;
+    a.lastrow = nullptr;
     a.bp = bp;
     a.gborder = border;
     a.ctl = ctl;

@@ -36,7 +36,7 @@ EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destro
            "dtw_enable_timing", "dtw_stage_times", "dtw_align_static",
            "dtw_static_scratch_bytes", "dtw_align_banded", "dtw_encoder_param_count",
            "dtw_encode", "dtw_encoder_grad", "dtw_encoder_adam", "dtw_align_learned",
-           "dtw_band_cells")
+           "dtw_band_cells", "dtw_wsdtw", "dtw_wsdtw_cseg")
 
 # learned band (include/pardtw.h)
 DTW_BAND_WMIN = 256
@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dtw_align_learned.argtypes = [vp, vp, ci, vp, ci, ci, ctypes.POINTER(Options), vp, ci,
                                       ci, vp, ci, vp, vp, ctypes.POINTER(ci)]
     lib.dtw_band_cells.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.dtw_wsdtw.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, vp, vp]
+    lib.dtw_wsdtw_cseg.argtypes = [vp, ci, ci, vp]
     for name in EXPORTS:
         if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes",
                         "dtw_encoder_param_count"):
@@ -270,6 +272,21 @@ def dtw_align_learned(h: int, A, B, params, path, path_len, total=None, downsamp
     return bool(fb.value)
 
 
+def dtw_wsdtw(h: int, A, B, nfrag: int, path, path_len, ends=None, total=None) -> None:
+    """Weakly-ordered Segmental DTW of query A against reference B (include/pardtw.h)."""
+    A, B = _features(A), _features(B)
+    _check(load_library().dtw_wsdtw(
+        h, A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1], int(nfrag),
+        path.data_ptr(), path.shape[0], path_len.data_ptr(),
+        ends.data_ptr() if ends is not None else None,
+        total.data_ptr() if total is not None else None), "dtw_wsdtw")
+
+
+def dtw_wsdtw_cseg(h: int, nfrag: int, Lb: int, cseg) -> None:
+    _check(load_library().dtw_wsdtw_cseg(h, int(nfrag), int(Lb), cseg.data_ptr()),
+           "dtw_wsdtw_cseg")
+
+
 def dtw_band_cells(h: int) -> int:
     c = ctypes.c_longlong(0)
     _check(load_library().dtw_band_cells(h, ctypes.byref(c)), "dtw_band_cells")
@@ -429,6 +446,30 @@ class Aligner:
 
     def band_cells(self) -> int:
         return dtw_band_cells(self.h)
+
+    def wsdtw(self, A, B, nfrag: int):
+        """WSDTW; returns (path, ends, total)."""
+        import torch
+        A, B = _features(A), _features(B)
+        path = torch.empty((A.shape[0], 2), dtype=torch.int32, device=A.device)
+        plen = torch.zeros(1, dtype=torch.int32, device=A.device)
+        ends = torch.empty(nfrag, dtype=torch.int32, device=A.device)
+        tot = torch.zeros(1, dtype=torch.float32, device=A.device)
+        self._enter()
+        dtw_wsdtw(self.h, A, B, nfrag, path, plen, ends, tot)
+        self._leave()
+        n = int(plen.item())
+        if n < 0:
+            raise PardtwError(-n, "dtw_wsdtw (device)")
+        return path[:n], ends, float(tot.item())
+
+    def wsdtw_cseg(self, nfrag: int, Lb: int):
+        import torch
+        c = torch.empty((nfrag, Lb), dtype=torch.float32, device=self.device)
+        self._enter()
+        dtw_wsdtw_cseg(self.h, nfrag, Lb, c)
+        self._leave()
+        return c
 
     def align_many(self, As: List, Bs: List, **opts):
         """Align independent pairs; returns (list of paths or None, costs, statuses)."""
