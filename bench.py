@@ -272,7 +272,6 @@ def run_ours(args):
             step()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            dp_ms.append(al.stage_times()[1])
         torch.cuda.synchronize(dev)
         clk.mark_end()
         if ws > 1:
@@ -362,10 +361,13 @@ def _rank0_line(line):
 
 def run_batch(args):
     """The batching workload: 256 seeded pairs (La ~ U[500, 8000], Lb = La x
-    U[0.8, 1.25], D = 12) aligned by one dtw_align_many call (one batched
-    normalisation, one persistent DP launch over a (pair, strip group) work
-    queue, one batched backtrace).  N ranks split the pairs by cell count
-    (LPT) and align their shares independently (strong scaling)."""
+    U[0.8, 1.25], D = 12) as a planned batch (dtw_batch_create: the DP
+    schedule picked by the autotuner, the whole batch -- normalisation, one
+    persistent DP launch over a (pair, strip group) work queue, the batched
+    backtrace -- captured in one CUDA graph); a step is one graph replay.  The
+    same batch through dtw_align_many (no graph) is timed beside it.  N ranks
+    split the pairs by cell count (LPT) and align their shares independently
+    (strong scaling)."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -395,7 +397,7 @@ def run_batch(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     st = None
 
-    def step():
+    def step_many():
         nonlocal st
         with torch.cuda.stream(stream):
             flush.fill_(1)
@@ -403,12 +405,32 @@ def run_batch(args):
             _, _, st = al.align_many(As, Bs)
             ev1.record(stream)
 
+    # the same batch without a graph: its time and its DP launch time
+    many_ms, dp_ms = [], []
+    for k in range(args.warmup + 3):
+        step_many()
+        ev1.synchronize()
+        if k >= args.warmup:
+            many_ms.append(ev0.elapsed_time(ev1))
+            dp_ms.append(al.stage_times()[1])
+    if st is not None and (st != 0).any():
+        raise RuntimeError(f"batch alignment failed on rank {rank}")
+    plan = al.plan_batch(As, Bs, autotune=True)
+    R_tuned, tuned_ms = plan.info()
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            plan.run()
+            ev1.record(stream)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
-    if st is not None and (st != 0).any():
-        raise RuntimeError(f"batch alignment failed on rank {rank}")
-    step_ms, dp_ms = [], []
+    if (plan.path_len.cpu().numpy() <= 0).any():
+        raise RuntimeError(f"planned batch failed on rank {rank}")
+    step_ms = []
     with ClockSampler(dev.index) as clk:
         if ws > 1:
             dist.barrier()
@@ -441,9 +463,13 @@ def run_batch(args):
         stream.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            Ad = [a.to(dev, non_blocking=True) for a in Ah]
-            Bd = [b.to(dev, non_blocking=True) for b in Bh]
-            paths, costs, st2 = al.align_many(Ad, Bd)
+            # the plan's fixed input buffers refilled from pinned host memory
+            for a, ah in zip(As, Ah):
+                a.copy_(ah, non_blocking=True)
+            for b, bh in zip(Bs, Bh):
+                b.copy_(bh, non_blocking=True)
+            plan.run()
+            paths, costs, lens = plan.results()
             out = [q.cpu() for q in paths if q is not None]
         e2e_t.append(time.perf_counter() - t0)
         h2d = sum(a.numel() * 4 for a in Ah) + sum(b.numel() * 4 for b in Bh)
@@ -483,20 +509,29 @@ def run_batch(args):
                                    "chroma-like, warped (8 knots)",
                        "pairs": len(pairs_all), "cells": sum(cells_all), "D": 12,
                        "l2": "flushed between steps (512 MiB write)",
-                       "parallelism": f"pairs split by cell count over {ws} rank(s)"},
+                       "parallelism": f"pairs split by cell count over {ws} rank(s)",
+                       "graph": "one CUDA graph replay per step (dtw_batch_run)",
+                       "schedule": f"autotuned: {R_tuned} rows per lane"},
+            "batch": {"graph_ms": 1e3 * t_max / args.steps,
+                      "align_many_ms": statistics.median(many_ms),
+                      "autotune_rows_per_lane": R_tuned,
+                      "autotune_ms_by_rows_per_lane": {"2": tuned_ms[0], "3": tuned_ms[1],
+                                                       "4": tuned_ms[2]}},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": None,
-                         "kernel": "k_dp_split, batch mode (work queue over pairs)",
+                         "kernel": "k_dp_split, batch mode (work queue over pairs), "
+                                   "3 rows per lane (timed through dtw_align_many)",
                          "ops_per_cell": 18, "dp_ms": 1e3 * dp_avg,
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{clock:.0f} MHz (sm_max_mhz, {src})"},
             "cpu_baseline": cpu,
             "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": 7 * args.steps,
             "clocks": clk.summary(),
         })
+    plan.close()
     al.close()
     if ws > 1:
         dist.destroy_process_group()

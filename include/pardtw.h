@@ -186,6 +186,37 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
                      const dtw_options* opt, int downsample, int halfwidth, int32_t* path,
                      int cap, int* path_len, float* total_cost, int* fell_back);
 
+/* ---- planned batch (CUDA graph, autotuned schedule) ------------------------- */
+/* A batch that is aligned again and again with the same shapes and buffers
+ * (a serving loop refilling fixed staging buffers): dtw_batch_create lays out
+ * the batch once (its own workspace and border buffer), picks the DP schedule
+ * with an autotuner when flags has DTW_BATCH_AUTOTUNE (it aligns the batch with
+ * 2, 3 and 4 rows per lane, where D allows them, and keeps the fastest; every
+ * schedule gives the same result, bit for bit), and captures the whole batch
+ * (a new tag for the border entries, the batched normalisation, the
+ * persistent DP over the (pair, strip group) work queue, the batched
+ * backtrace) into one CUDA graph.  dtw_batch_run launches that graph on the
+ * handle's stream: it reads whatever A[k], B[k] hold at that time and writes
+ * the outputs as dtw_align_many does.  Creation itself aligns the batch (the
+ * outputs then hold its result) and synchronises the stream.
+ *   A[k], B[k], paths, path_len, cost (may be NULL): device memory that must
+ *     stay valid for the plan's life; path_off, lengths and D as in
+ *     dtw_align_many; every pair must be valid (else its status is returned)
+ *   D <= 32, FP32 cost, default options.
+ * A device-side failure of a pair (bounded wait) shows as path_len[k] < 0. */
+typedef struct dtw_batch dtw_batch;
+#define DTW_BATCH_AUTOTUNE 1
+int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
+                     const float* const* B, const int* Lb, int D, int32_t* paths,
+                     const int64_t* path_off, int* path_len, float* cost, int flags,
+                     dtw_batch** out);
+/* One replay of the plan's graph on the handle's stream (asynchronous). */
+int dtw_batch_run(dtw_batch* b);
+/* The chosen rows per lane and the autotuner's times in ms for 2, 3, 4 rows
+ * per lane (-1 where not tried); either pointer may be NULL. */
+int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, float* tuned_ms);
+int dtw_batch_destroy(dtw_batch* b);
+
 /* ---- weakly-ordered Segmental DTW (Sec. II-C) ------------------------------ */
 /* WSDTW of the query A (La x D) against the reference B (Lb x D) with nfrag
  * fragments of A:

@@ -321,69 +321,94 @@ struct SubseqBatch {
     std::vector<BtArgs>* bts_out;
 };
 
-int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, const int* La,
-                const float* const* B, const int* Lb, int D, const dtw_options& o, int R,
-                int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
-                const SubseqBatch* sub = nullptr) {
-    const int m = (int)idx.size();
-    if (m == 0) return DTW_OK;
-    // The work queue runs the pairs with the longest sweeps first, so that the
-    // last pairs to start are short and no long chain of strips is left alone
-    // at the end (the order does not change any result).
+// Layout of a batch in one workspace: the descriptors, one control block per
+// pair, then every pair's buffers; the border rows of all pairs in another.
+// The work queue runs the pairs with the longest sweeps first, so that the
+// last pairs to start are short and no long chain of strips is left alone at
+// the end (the order does not change any result).
+struct BatchSetup {
+    int m = 0, D = 0, dp = 0, R = 3, maxLa = 0, maxLb = 0, max_frames = 0;
+    std::vector<int> idx;  // pair indices in work-queue order
+    std::vector<Layout> Ls;
+    std::vector<size_t> off, boff;
+    std::vector<int> item0;
+    size_t off_dp = 0, off_norm = 0, off_bt = 0, off_item = 0, off_ctl = 0;
+    size_t ws_bytes = 0, border_bytes = 0;
+};
+
+BatchSetup batch_setup(std::vector<int> idx, const int* La, const int* Lb, int D, int R) {
+    BatchSetup b;
+    b.m = (int)idx.size();
+    b.R = R;
+    b.D = D;
+    b.dp = padded_dim(D);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
         return (long long)Lb[x] * 256 + La[x] > (long long)Lb[y] * 256 + La[y];
     });
-    const int dp = padded_dim(D);
+    b.idx = idx;
+    const int m = b.m;
     const DpPlan plan = {2, R, kSplitStrips};
-    std::vector<Layout> Ls(m);
-    std::vector<size_t> off(m), boff(m);
-    // descriptors, then one control block per pair, then every pair's buffers
+    b.Ls.resize(m);
+    b.off.resize(m);
+    b.boff.resize(m);
+    b.item0.assign(m + 1, 0);
     size_t o0 = 0;
-    const size_t off_dp = o0;
+    b.off_dp = o0;
     o0 = align256(o0 + sizeof(DpArgs) * m);
-    const size_t off_norm = o0;
+    b.off_norm = o0;
     o0 = align256(o0 + sizeof(NormArgs) * m);
-    const size_t off_bt = o0;
+    b.off_bt = o0;
     o0 = align256(o0 + sizeof(BtArgs) * m);
-    const size_t off_item = o0;
+    b.off_item = o0;
     o0 = align256(o0 + sizeof(int) * (m + 1) + 16);  // + the work-queue ticket
-    const size_t off_ctl = o0;
+    b.off_ctl = o0;
     o0 = align256(o0 + (size_t)256 * m);
     size_t border_total = 0;
-    int maxLa = 0, maxLb = 0, max_frames = 0;
-    std::vector<int> item0(m + 1, 0);
     for (int q = 0; q < m; ++q) {
         const int k = idx[q];
-        Ls[q] = make_layout(La[k], Lb[k], D, plan);
-        const Layout& L = Ls[q];
-        off[q] = o0;
+        b.Ls[q] = make_layout(La[k], Lb[k], D, plan);
+        const Layout& L = b.Ls[q];
+        b.off[q] = o0;
         o0 = align256(o0 + (L.off_stage_a - L.off_ahat));  // Ahat, Bhat, bp, band maps
-        boff[q] = border_total;
+        b.boff[q] = border_total;
         border_total += L.border_bytes;
-        item0[q + 1] = item0[q] + L.ngroups;
-        maxLa = std::max(maxLa, La[k]);
-        maxLb = std::max(maxLb, Lb[k]);
-        max_frames = std::max(max_frames, L.La_pad + L.nchunk * kColsPerWord);
+        b.item0[q + 1] = b.item0[q] + L.ngroups;
+        b.maxLa = std::max(b.maxLa, La[k]);
+        b.maxLb = std::max(b.maxLb, Lb[k]);
+        b.max_frames = std::max(b.max_frames, L.La_pad + L.nchunk * kColsPerWord);
     }
-    int rc = ensure_workspace(h, o0, border_total);
-    if (rc != DTW_OK) return rc;
-    char* ws = h->ws;
-    cudaStream_t s = h->stream;
-    unsigned epoch = ++h->epoch;
-    if (epoch == 0) epoch = ++h->epoch;
-    std::vector<DpArgs> dps(m);
-    std::vector<NormArgs> nas(m);
-    std::vector<BtArgs> bts(m);
+    b.ws_bytes = o0;
+    b.border_bytes = border_total;
+    return b;
+}
+
+// Host copies of the descriptors of a batch laid out in `ws` and `border`.
+struct BatchDesc {
+    std::vector<DpArgs> dps;
+    std::vector<NormArgs> nas;
+    std::vector<BtArgs> bts;
+};
+
+BatchDesc batch_descriptors(const BatchSetup& b, char* ws, unsigned long long* border,
+                            const float* const* A, const int* La, const float* const* B,
+                            const int* Lb, const dtw_options& o, unsigned epoch, int32_t* paths,
+                            const int64_t* path_off, int* path_len, float* cost,
+                            const SubseqBatch* sub) {
+    BatchDesc d;
+    const int m = b.m;
+    d.dps.resize(m);
+    d.nas.resize(m);
+    d.bts.resize(m);
     for (int q = 0; q < m; ++q) {
-        const int k = idx[q];
-        const Layout& L = Ls[q];
-        char* base = ws + off[q] - L.off_ahat;  // so that base + L.off_* addresses this pair
-        DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + off_ctl + (size_t)256 * q);
-        float* e_final = reinterpret_cast<float*>(ws + off_ctl + (size_t)256 * q + 16);
+        const int k = b.idx[q];
+        const Layout& L = b.Ls[q];
+        char* base = ws + b.off[q] - L.off_ahat;  // so that base + L.off_* addresses this pair
+        DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + b.off_ctl + (size_t)256 * q);
+        float* e_final = reinterpret_cast<float*>(ws + b.off_ctl + (size_t)256 * q + 16);
         float* Ahat = reinterpret_cast<float*>(base + L.off_ahat);
         float* Bhat = reinterpret_cast<float*>(base + L.off_bhat);
         uint32_t* bpw = reinterpret_cast<uint32_t*>(base + L.off_bp);
-        NormArgs& na = nas[q];
+        NormArgs& na = d.nas[q];
         na.A = A[k];
         na.La = La[k];
         na.La_pad = L.La_pad;
@@ -393,13 +418,13 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         na.Ahat = Ahat;
         na.Bt = Bhat;
         na.ctl = ctl;
-        DpArgs& a = dps[q];
+        DpArgs& a = d.dps[q];
         a.Ahat = Ahat;
         a.Bhat = Bhat;
         a.Bbf = nullptr;
         a.ranges = nullptr;
         a.bp = bpw;
-        a.gborder = h->border + boff[q] / sizeof(unsigned long long);
+        a.gborder = border + b.boff[q] / sizeof(unsigned long long);
         a.ctl = ctl;
         a.e_final = e_final;
         a.La = La[k];
@@ -415,7 +440,7 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
         a.skip_publish = o.debug_skip_publish;
         a.lastrow = sub ? sub->lastrow + (size_t)k * sub->stride : nullptr;
-        BtArgs& bt = bts[q];
+        BtArgs& bt = d.bts[q];
         bt.bp = bpw;
         bt.La = La[k];
         bt.Lb = Lb[k];
@@ -432,42 +457,78 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
         bt.ranges = nullptr;
         if (sub) (*sub->bts_out)[k] = bt;
     }
-    CU(cudaMemcpyAsync(ws + off_dp, dps.data(), sizeof(DpArgs) * m, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(ws + off_norm, nas.data(), sizeof(NormArgs) * m, cudaMemcpyHostToDevice,
+    return d;
+}
+
+int batch_upload(const BatchSetup& b, const BatchDesc& d, char* ws, cudaStream_t s) {
+    const int m = b.m;
+    CU(cudaMemcpyAsync(ws + b.off_dp, d.dps.data(), sizeof(DpArgs) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ws + b.off_norm, d.nas.data(), sizeof(NormArgs) * m, cudaMemcpyHostToDevice,
                        s));
-    CU(cudaMemcpyAsync(ws + off_bt, bts.data(), sizeof(BtArgs) * m, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(ws + off_item, item0.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice,
-                       s));
-    int* ticket = reinterpret_cast<int*>(ws + off_item + sizeof(int) * (m + 1));
-    if (h->timing) CU(cudaEventRecord(h->ev[0], s));
-    CU(launch_normalise_many(reinterpret_cast<const NormArgs*>(ws + off_norm), m, max_frames, D,
-                             dp, ticket, s));
-    if (h->timing) CU(cudaEventRecord(h->ev[1], s));
-    if (sub) {
-        CU(launch_dp_subseq_many(reinterpret_cast<const DpArgs*>(ws + off_dp),
-                                 reinterpret_cast<const int*>(ws + off_item), m, item0[m], ticket,
-                                 dp, h->num_sms, s));
-        if (h->timing) {
-            CU(cudaEventRecord(h->ev[2], s));
-            CU(cudaEventRecord(h->ev[3], s));
-            h->timed = true;
-        }
-        return DTW_OK;
-    }
-    CU(launch_dp_split_many(reinterpret_cast<const DpArgs*>(ws + off_dp),
-                            reinterpret_cast<const int*>(ws + off_item), m, item0[m], ticket, dp,
-                            R, h->num_sms, s));
-    if (h->timing) CU(cudaEventRecord(h->ev[2], s));
-    CU(launch_backtrace_bands_many(reinterpret_cast<const BtArgs*>(ws + off_bt), m, maxLa, maxLb,
-                                   s));
-    if (h->timing) {
-        CU(cudaEventRecord(h->ev[3], s));
-        h->timed = true;
-    }
+    CU(cudaMemcpyAsync(ws + b.off_bt, d.bts.data(), sizeof(BtArgs) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ws + b.off_item, b.item0.data(), sizeof(int) * (m + 1),
+                       cudaMemcpyHostToDevice, s));
     return DTW_OK;
 }
 
+// The launches of a batch whose descriptors are in `ws`: normalisation, the
+// persistent DP, and (unless subseq) the batched backtrace.  `ev` (4 events
+// or null) brackets the stages.
+int batch_launch(const BatchSetup& b, char* ws, bool subseq, int num_sms, cudaStream_t s,
+                 cudaEvent_t* ev) {
+    const int m = b.m;
+    int* ticket = reinterpret_cast<int*>(ws + b.off_item + sizeof(int) * (m + 1));
+    if (ev) CU(cudaEventRecord(ev[0], s));
+    CU(launch_normalise_many(reinterpret_cast<const NormArgs*>(ws + b.off_norm), m, b.max_frames,
+                             b.D, b.dp, ticket, s));
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    const DpArgs* dps = reinterpret_cast<const DpArgs*>(ws + b.off_dp);
+    const int* item0 = reinterpret_cast<const int*>(ws + b.off_item);
+    if (subseq)
+        CU(launch_dp_subseq_many(dps, item0, m, b.item0[m], ticket, b.dp, num_sms, s));
+    else
+        CU(launch_dp_split_many(dps, item0, m, b.item0[m], ticket, b.dp, b.R, num_sms, s));
+    if (ev) CU(cudaEventRecord(ev[2], s));
+    if (!subseq)
+        CU(launch_backtrace_bands_many(reinterpret_cast<const BtArgs*>(ws + b.off_bt), m, b.maxLa,
+                                       b.maxLb, s));
+    if (ev) CU(cudaEventRecord(ev[3], s));
+    return DTW_OK;
+}
+
+int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, const int* La,
+                const float* const* B, const int* Lb, int D, const dtw_options& o, int R,
+                int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
+                const SubseqBatch* sub = nullptr) {
+    if (idx.empty()) return DTW_OK;
+    const BatchSetup b = batch_setup(std::move(idx), La, Lb, D, R);
+    int rc = ensure_workspace(h, b.ws_bytes, b.border_bytes);
+    if (rc != DTW_OK) return rc;
+    unsigned epoch = ++h->epoch;
+    if (epoch == 0) epoch = ++h->epoch;
+    const BatchDesc d = batch_descriptors(b, h->ws, h->border, A, La, B, Lb, o, epoch, paths,
+                                          path_off, path_len, cost, sub);
+    rc = batch_upload(b, d, h->ws, h->stream);
+    if (rc != DTW_OK) return rc;
+    rc = batch_launch(b, h->ws, sub != nullptr, h->num_sms, h->stream,
+                      h->timing ? h->ev : nullptr);
+    if (rc == DTW_OK && h->timing) h->timed = true;
+    return rc;
+}
+
 }  // namespace
+
+// A planned, graph-captured batch (dtw_batch_create).
+struct dtw_batch {
+    dtw_handle* h = nullptr;
+    int n = 0, D = 0, R = 3;
+    char* ws = nullptr;
+    unsigned long long* border = nullptr;
+    BatchSetup setup;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float tuned_ms[3] = {-1.f, -1.f, -1.f};  // R = 2, 3, 4
+};
 
 extern "C" {
 
@@ -1124,6 +1185,8 @@ int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     const size_t o_scr = take(sizeof(int32_t) * 2 * (size_t)La);
     const size_t o_tot = take(sizeof(float));
     const size_t o_ctl = take(sizeof(DevCtl));
+    const size_t o_agg = take(seg_dp_scratch_bytes(Lb));
+    const size_t o_done = take(sizeof(unsigned));
     int rc = grow(h, &h->wsd, &h->wsd_cap, o);
     if (rc != DTW_OK) return rc;
     char* w = h->wsd;
@@ -1154,7 +1217,8 @@ int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     const WsFrag* dfr = reinterpret_cast<const WsFrag*>(w + o_frag);
     CU(launch_seg_dp(dfr, reinterpret_cast<const float*>(w + o_last), stride, N, Lb,
                      reinterpret_cast<const int*>(w + o_delta), reinterpret_cast<float*>(w + o_dseg),
-                     reinterpret_cast<int*>(w + o_arg), dends, dtot, ctl, s));
+                     reinterpret_cast<int*>(w + o_arg), w + o_agg,
+                     reinterpret_cast<unsigned*>(w + o_done), dends, dtot, ctl, s));
     CU(launch_bt_subseq(dfr, N, dends, reinterpret_cast<int32_t*>(w + o_scr),
                         reinterpret_cast<int*>(w + o_cnt), path, path_len, ctl, s));
     if (ends) CU(cudaMemcpyAsync(ends, dends, sizeof(int) * N, cudaMemcpyDeviceToDevice, s));
@@ -1172,6 +1236,154 @@ int dtw_wsdtw_cseg(dtw_handle* h, int nfrag, int Lb, float* cseg) {
     if (!g.ok) return DTW_ERR_CUDA;
     CU(cudaMemcpy2DAsync(cseg, sizeof(float) * Lb, h->wsd, sizeof(float) * stride,
                          sizeof(float) * Lb, nfrag, cudaMemcpyDeviceToDevice, h->stream));
+    return DTW_OK;
+}
+
+int dtw_batch_destroy(dtw_batch* b) {
+    if (!b) return DTW_ERR_INVALID;
+    DeviceGuard g(b->h->device);
+    cudaStreamSynchronize(b->h->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    if (b->border) cudaFree(b->border);
+    (void)cudaGetLastError();
+    delete b;
+    return DTW_OK;
+}
+
+int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
+                     const float* const* B, const int* Lb, int D, int32_t* paths,
+                     const int64_t* path_off, int* path_len, float* cost, int flags,
+                     dtw_batch** out) {
+    if (!out) return DTW_ERR_INVALID;
+    *out = nullptr;
+    if (!h || n < 1 || !A || !La || !B || !Lb || !paths || !path_off || !path_len)
+        return DTW_ERR_INVALID;
+    const int dp = padded_dim(D);
+    if (dp == 0 || !split_supported(dp, 3)) return DTW_ERR_UNSUPPORTED;
+    for (int k = 0; k < n; ++k) {
+        const int rc = validate(A[k], La[k], B[k], Lb[k], D);
+        if (rc != DTW_OK) return rc;
+    }
+    DeviceGuard g(h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    if (!is_device_ptr(paths) || !is_device_ptr(path_len) || (cost && !is_device_ptr(cost)))
+        return DTW_ERR_INVALID;
+    for (int k = 0; k < n; ++k)
+        if (!is_device_ptr(A[k]) || !is_device_ptr(B[k])) return DTW_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    const dtw_options o = defaults();
+    std::vector<int> idx(n);
+    for (int k = 0; k < n; ++k) idx[k] = k;
+    // candidate schedules: rows per lane of the warp-pair DP
+    std::vector<int> Rs;
+    if (flags & DTW_BATCH_AUTOTUNE) {
+        for (int R = 2; R <= 4; ++R)
+            if (split_supported(dp, R)) Rs.push_back(R);
+    } else {
+        Rs.push_back(3);
+    }
+    std::vector<BatchSetup> setups;
+    size_t ws_bytes = 0, border_bytes = 0;
+    for (int R : Rs) {
+        setups.push_back(batch_setup(idx, La, Lb, D, R));
+        ws_bytes = std::max(ws_bytes, setups.back().ws_bytes);
+        border_bytes = std::max(border_bytes, setups.back().border_bytes);
+    }
+    dtw_batch* b = new (std::nothrow) dtw_batch();
+    if (!b) return DTW_ERR_OOM;
+    b->h = h;
+    b->n = n;
+    b->D = D;
+    if (cudaMalloc(&b->ws, ws_bytes) != cudaSuccess ||
+        cudaMalloc(&b->border, border_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dtw_batch_destroy(b);
+        return DTW_ERR_OOM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t cs = nullptr;
+    int rc = DTW_OK;
+    unsigned epoch = 0;
+    auto fail = [&](int code) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (cs) cudaStreamDestroy(cs);
+        (void)cudaGetLastError();
+        dtw_batch_destroy(b);
+        return code;
+    };
+    if (cudaMemsetAsync(b->border, 0, border_bytes, s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(DTW_ERR_CUDA);
+    // the autotuner: every candidate twice, the second run timed (all
+    // candidates compute the same result, bit for bit)
+    int best = 0;
+    float best_ms = 0.f;
+    for (size_t c = 0; c < setups.size(); ++c) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            const BatchDesc d = batch_descriptors(setups[c], b->ws, b->border, A, La, B, Lb, o,
+                                                  ++epoch, paths, path_off, path_len, cost,
+                                                  nullptr);
+            rc = batch_upload(setups[c], d, b->ws, s);
+            if (rc != DTW_OK) return fail(rc);
+            if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) return fail(DTW_ERR_CUDA);
+            rc = batch_launch(setups[c], b->ws, false, h->num_sms, s, nullptr);
+            if (rc != DTW_OK) return fail(rc);
+            if (rep == 1 && (cudaEventRecord(e1, s) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                return fail(DTW_ERR_CUDA);
+        }
+        b->tuned_ms[setups[c].R - 2] = ms;
+        if (c == 0 || ms < best_ms) {
+            best = (int)c;
+            best_ms = ms;
+        }
+    }
+    b->setup = setups[best];
+    b->R = b->setup.R;
+    // the chosen schedule's descriptors stay in the plan's workspace; the
+    // graph bumps their epoch, then normalises, sweeps and backtraces
+    const BatchDesc d = batch_descriptors(b->setup, b->ws, b->border, A, La, B, Lb, o, ++epoch,
+                                          paths, path_off, path_len, cost, nullptr);
+    rc = batch_upload(b->setup, d, b->ws, s);
+    if (rc != DTW_OK) return fail(rc);
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(DTW_ERR_CUDA);
+    const bool ok_bump = launch_bump_epoch(reinterpret_cast<DpArgs*>(b->ws + b->setup.off_dp),
+                                           n, cs) == cudaSuccess;
+    const int rl = batch_launch(b->setup, b->ws, false, h->num_sms, cs, nullptr);
+    cudaGraph_t graph = nullptr;
+    const bool ok_end = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
+    b->graph = graph;
+    if (!ok_bump || rl != DTW_OK || !ok_end ||
+        cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        return fail(DTW_ERR_CUDA);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(cs);
+    *out = b;
+    return DTW_OK;
+}
+
+int dtw_batch_run(dtw_batch* b) {
+    if (!b || !b->exec) return DTW_ERR_INVALID;
+    DeviceGuard g(b->h->device);
+    if (!g.ok) return DTW_ERR_CUDA;
+    CU(cudaGraphLaunch(b->exec, b->h->stream));
+    return DTW_OK;
+}
+
+int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, float* tuned_ms) {
+    if (!b) return DTW_ERR_INVALID;
+    if (rows_per_lane) *rows_per_lane = b->R;
+    if (tuned_ms)
+        for (int k = 0; k < 3; ++k) tuned_ms[k] = b->tuned_ms[k];
     return DTW_OK;
 }
 

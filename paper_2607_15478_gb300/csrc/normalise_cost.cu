@@ -81,6 +81,20 @@ __global__ void k_normalise_many(const NormArgs* __restrict__ many, int D, int d
     normalise_frame(t, a.A, a.La, a.La_pad, a.B, a.Lb, a.Lb_pad, D, dp, a.Ahat, a.Bt, a.ctl);
 }
 
+// A replayed batch graph starts with this: a new tag for the border entries
+// of every pair (entries left by the previous replay carry the old one).
+__global__ void k_bump_epoch(DpArgs* many, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned e = many[k].epoch + 1u;
+    many[k].epoch = e == 0u ? 1u : e;
+}
+
+cudaError_t launch_bump_epoch(DpArgs* many, int n, cudaStream_t s) {
+    k_bump_epoch<<<(n + 127) / 128, 128, 0, s>>>(many, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_normalise(const float* A, int La, int La_pad, const float* B, int Lb,
                              int Lb_pad, int D, int dp, float* Ahat, float* Bt, DevCtl* ctl,
                              cudaStream_t s) {

@@ -112,6 +112,8 @@ cudaError_t launch_cost(const float* Ahat, int La, const float* Bt, int Lb, int 
 // also zeroes *ticket, the work queue of launch_dp_split_many.
 cudaError_t launch_normalise_many(const NormArgs* many, int n, int max_frames, int D, int dp,
                                   int* ticket, cudaStream_t s);
+// Every DpArgs::epoch of a batch in device memory += 1 (0 skipped).
+cudaError_t launch_bump_epoch(DpArgs* many, int n, cudaStream_t s);
 cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);           // R = 1
 cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 // Rows per lane the fused DP supports for a padded dimension (0 = none).
@@ -204,9 +206,11 @@ struct WsFrag {
 };
 // Segment-level DP over the fragments' last rows (stride floats apart) with
 // shortest matches delta[k]; end frames, total (D_seg[N-1][Lb-1]) and status.
+// agg: seg_dp_scratch_bytes(Lb) bytes; done: one zeroed counter.
 cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride, int N, int Lb,
-                          const int* delta, float* Dseg, int* arg, int* ends, float* total,
-                          DevCtl* ctl, cudaStream_t s);
+                          const int* delta, float* Dseg, int* arg, void* agg, unsigned* done,
+                          int* ends, float* total, DevCtl* ctl, cudaStream_t s);
+size_t seg_dp_scratch_bytes(int Lb);
 // Fragment backtraces from their end frames into `scratch` (2 La ints), then
 // the concatenated path into `path` and its length (or -status) into path_len.
 cudaError_t launch_bt_subseq(const WsFrag* fr, int N, const int* ends, int32_t* scratch,

@@ -4,13 +4,12 @@
 // leaves every fragment's last row of cumulative costs (C_seg, step 3) and its
 // 2-bit backtrace matrix.  Here:
 //
-//   k_seg_dp     step 4, one CTA: for fragment k = 0 .. N-1 in turn,
-//                  match[j]   = D_seg[k-1][j - delta_k] + C_seg[k][j]
+//   k_seg_tile,  step 4, fragment k = 0 .. N-1 in turn (two launches each):
+//   k_seg_fix      match[j]   = D_seg[k-1][j - delta_k] + C_seg[k][j]
 //                               (= C_seg[0][j] for k = 0; +inf for j < delta_k)
 //                  D_seg[k][j] = running minimum of match over j' <= j,
 //                  arg[k][j]   = the first j' attaining it,
-//                as a block-wide prefix minimum (per-thread runs, a scan of
-//                the run minima, a second pass); then the end frames
+//                as a tiled prefix scan; then the end frames
 //                e_{N-1} = arg[N-1][Lb-1], e_{k-1} = arg[k-1][e_k - delta_k].
 //   k_bt_subseq  step 5, one thread per fragment: the walk from (last row,
 //                e_k) back to row 0 through the fragment's backtrace matrix,
@@ -33,80 +32,127 @@ __device__ __forceinline__ MinArg better(MinArg a, MinArg b) {  // a is earlier
     return (b.v < a.v) ? b : a;
 }
 
-__global__ void __launch_bounds__(kSegThreads)
-    k_seg_dp(const WsFrag* __restrict__ fr, const float* __restrict__ lastrow, size_t stride,
-             int N, int Lb, const int* __restrict__ delta, float* __restrict__ Dseg, int* __restrict__ arg,
-             int* __restrict__ ends, float* __restrict__ total, DevCtl* ctl) {
-    __shared__ MinArg s_part[kSegThreads];
-    __shared__ int s_fail;
-    const int t = threadIdx.x;
-    // a fragment whose DP failed (e.g. a bounded wait expired) fails the call
-    if (t == 0) {
-        s_fail = 0;
-        for (int k = 0; k < N; ++k) {
-            const int st = fr[k].pctl->status;
-            if (st != 0) {
-                raise_status(ctl, st, 20);
-                s_fail = 1;
-                break;
-            }
+// Step 4 runs fragment by fragment; within fragment k the running minimum
+// over j is a prefix scan of (value, column) pairs (the earlier column wins
+// ties), done in tiles of kTile columns by two launches:
+//   k_seg_tile   every tile: its match values (coalesced), their minimum into
+//                agg[tile]; the last tile to finish (a counter, no waiting)
+//                turns agg into exclusive carries for all tiles;
+//   k_seg_fix    every tile: the block-wide inclusive scan of its match values
+//                from its carry, written as D_seg[k][*] and arg[k][*].
+constexpr int kTile = 1024;
+
+__device__ __forceinline__ float seg_match(const float* cs, const float* prev, int k, int dk,
+                                           int j) {
+    if (k == 0) return cs[j];
+    return j - dk >= 0 ? prev[j - dk] + cs[j] : INFINITY;
+}
+
+// Block-wide inclusive scan of one (value, column) per thread, earlier wins.
+__device__ __forceinline__ MinArg block_scan_min(MinArg v, MinArg* s_warp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        MinArg o;
+        o.v = __shfl_up_sync(0xffffffffu, v.v, off);
+        o.j = __shfl_up_sync(0xffffffffu, v.j, off);
+        if (lane >= off) v = better(o, v);
+    }
+    if (lane == 31) s_warp[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        MinArg x = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : MinArg{INFINITY, -1};
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            MinArg o;
+            o.v = __shfl_up_sync(0xffffffffu, x.v, off);
+            o.j = __shfl_up_sync(0xffffffffu, x.j, off);
+            if (lane >= off) x = better(o, x);
         }
+        s_warp[lane] = x;  // inclusive prefix over warps
     }
     __syncthreads();
-    if (s_fail) return;
-    const int per = (Lb + kSegThreads - 1) / kSegThreads;
-    const int j0 = min(t * per, Lb), j1 = min(j0 + per, Lb);
-    for (int k = 0; k < N; ++k) {
-        const float* cs = lastrow + (size_t)k * stride;
-        const float* prev = k > 0 ? Dseg + (size_t)(k - 1) * Lb : nullptr;
-        const int dk = k > 0 ? delta[k] : 0;
-        // pass 1: the run minimum of match over this thread's columns
-        MinArg m{INFINITY, -1};
-        for (int j = j0; j < j1; ++j) {
-            float mv;
-            if (k == 0)
-                mv = cs[j];
-            else
-                mv = (j - dk >= 0) ? prev[j - dk] + cs[j] : INFINITY;
-            m = better(m, MinArg{mv, j});
-        }
-        s_part[t] = m;
-        __syncthreads();
-        // inclusive scan of the run minima (Hillis-Steele over the block)
-        for (int off = 1; off < kSegThreads; off <<= 1) {
-            const MinArg o = t >= off ? s_part[t - off] : MinArg{INFINITY, -1};
-            __syncthreads();
-            if (t >= off) s_part[t] = better(o, s_part[t]);
-            __syncthreads();
-        }
-        MinArg run = t > 0 ? s_part[t - 1] : MinArg{INFINITY, -1};
-        // pass 2: the running minimum from the carry-in
-        float* drow = Dseg + (size_t)k * Lb;
-        int* arow = arg + (size_t)k * Lb;
-        for (int j = j0; j < j1; ++j) {
-            float mv;
-            if (k == 0)
-                mv = cs[j];
-            else
-                mv = (j - dk >= 0) ? prev[j - dk] + cs[j] : INFINITY;
-            run = better(run, MinArg{mv, j});
-            drow[j] = run.v;
-            arow[j] = run.j;
-        }
-        __syncthreads();  // row k is complete before row k+1 reads it
+    if (w > 0) v = better(s_warp[w - 1], v);
+    return v;
+}
+
+__global__ void __launch_bounds__(kTile)
+    k_seg_tile(const WsFrag* __restrict__ fr, const float* __restrict__ lastrow, size_t stride,
+               int N, int Lb, int k, const int* __restrict__ delta,
+               const float* __restrict__ Dseg, MinArg* __restrict__ agg,
+               unsigned* __restrict__ done, DevCtl* ctl) {
+    __shared__ MinArg s_warp[32];
+    __shared__ bool s_last;
+    const int ntile = gridDim.x;
+    const int j = blockIdx.x * kTile + threadIdx.x;
+    const float* cs = lastrow + (size_t)k * stride;
+    const float* prev = k > 0 ? Dseg + (size_t)(k - 1) * Lb : nullptr;
+    const int dk = k > 0 ? delta[k] : 0;
+    MinArg v{INFINITY, -1};
+    if (j < Lb) v = MinArg{seg_match(cs, prev, k, dk, j), j};
+    v = block_scan_min(v, s_warp);
+    if (threadIdx.x == blockDim.x - 1) {
+        agg[blockIdx.x] = v;
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == (unsigned)ntile - 1;
     }
-    if (t == 0) {
-        const float tot = Dseg[(size_t)(N - 1) * Lb + Lb - 1];
-        if (!(tot < INFINITY)) {
+    __syncthreads();
+    if (!s_last) return;
+    // the last tile: exclusive carries of all tiles, in tile order (a few
+    // hundred tiles at most), then the counter is reset for the next launch
+    __threadfence();
+    if (threadIdx.x == 0) {
+        // a fragment whose DP failed (a bounded wait expired) fails the call
+        if (k == 0)
+            for (int q = 0; q < N; ++q) {
+                const int st = fr[q].pctl->status;
+                if (st != 0) {
+                    raise_status(ctl, st, 20);
+                    break;
+                }
+            }
+        MinArg run{INFINITY, -1};
+        volatile MinArg* va = agg;  // written by the other tiles of this launch
+        for (int t = 0; t < ntile; ++t) {
+            const MinArg a{va[t].v, va[t].j};
+            va[t].v = run.v;  // carry into tile t
+            va[t].j = run.j;
+            run = better(run, a);
+        }
+        *done = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kTile)
+    k_seg_fix(const float* __restrict__ lastrow, size_t stride, int N, int Lb, int k,
+              const int* __restrict__ delta, float* __restrict__ Dseg, int* __restrict__ arg,
+              const MinArg* __restrict__ agg, int* __restrict__ ends, float* __restrict__ total,
+              DevCtl* ctl) {
+    __shared__ MinArg s_warp[32];
+    const int j = blockIdx.x * kTile + threadIdx.x;
+    const float* cs = lastrow + (size_t)k * stride;
+    const float* prev = k > 0 ? Dseg + (size_t)(k - 1) * Lb : nullptr;
+    const int dk = k > 0 ? delta[k] : 0;
+    MinArg v{INFINITY, -1};
+    if (j < Lb) v = MinArg{seg_match(cs, prev, k, dk, j), j};
+    v = better(agg[blockIdx.x], block_scan_min(v, s_warp));
+    if (j < Lb) {
+        Dseg[(size_t)k * Lb + j] = v.v;
+        arg[(size_t)k * Lb + j] = v.j;
+    }
+    // the last fragment's last column: the total and the end frames
+    if (k == N - 1 && j == Lb - 1) {
+        if (ctl->status != 0) return;
+        if (!(v.v < INFINITY)) {
             raise_status(ctl, DTW_ERR_UNREACHABLE, 21);
             return;
         }
-        *total = tot;
-        int e = arg[(size_t)(N - 1) * Lb + Lb - 1];
+        *total = v.v;
+        int e = v.j;
         ends[N - 1] = e;
-        for (int k = N - 1; k > 0; --k) {
-            e = arg[(size_t)(k - 1) * Lb + (e - delta[k])];
-            ends[k - 1] = e;
+        for (int q = N - 1; q > 0; --q) {
+            e = arg[(size_t)(q - 1) * Lb + (e - delta[q])];
+            ends[q - 1] = e;
         }
     }
 }
@@ -172,12 +218,21 @@ __global__ void __launch_bounds__(kSegThreads)
 }  // namespace
 
 cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride, int N, int Lb,
-                          const int* delta, float* Dseg, int* arg, int* ends, float* total,
-                          DevCtl* ctl, cudaStream_t s) {
-    k_seg_dp<<<1, kSegThreads, 0, s>>>(fr, lastrow, stride, N, Lb, delta, Dseg, arg, ends, total,
-                                       ctl);
-    return cudaGetLastError();
+                          const int* delta, float* Dseg, int* arg, void* agg, unsigned* done,
+                          int* ends, float* total, DevCtl* ctl, cudaStream_t s) {
+    const int ntile = (Lb + kTile - 1) / kTile;
+    cudaError_t e = cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    for (int k = 0; k < N && e == cudaSuccess; ++k) {
+        k_seg_tile<<<ntile, kTile, 0, s>>>(fr, lastrow, stride, N, Lb, k, delta, Dseg,
+                                           static_cast<MinArg*>(agg), done, ctl);
+        k_seg_fix<<<ntile, kTile, 0, s>>>(lastrow, stride, N, Lb, k, delta, Dseg, arg,
+                                          static_cast<const MinArg*>(agg), ends, total, ctl);
+        e = cudaGetLastError();
+    }
+    return e;
 }
+
+size_t seg_dp_scratch_bytes(int Lb) { return sizeof(MinArg) * (size_t)((Lb + kTile - 1) / kTile); }
 
 cudaError_t launch_bt_subseq(const WsFrag* fr, int N, const int* ends, int32_t* scratch,
                              int* count, int32_t* path, int* path_len, DevCtl* ctl,

@@ -36,7 +36,9 @@ EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destro
            "dtw_enable_timing", "dtw_stage_times", "dtw_align_static",
            "dtw_static_scratch_bytes", "dtw_align_banded", "dtw_encoder_param_count",
            "dtw_encode", "dtw_encoder_grad", "dtw_encoder_adam", "dtw_align_learned",
-           "dtw_band_cells", "dtw_wsdtw", "dtw_wsdtw_cseg")
+           "dtw_band_cells", "dtw_wsdtw", "dtw_wsdtw_cseg", "dtw_batch_create",
+           "dtw_batch_run", "dtw_batch_info", "dtw_batch_destroy")
+DTW_BATCH_AUTOTUNE = 1
 
 # learned band (include/pardtw.h)
 DTW_BAND_WMIN = 256
@@ -106,6 +108,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dtw_band_cells.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.dtw_wsdtw.argtypes = [vp, vp, ci, vp, ci, ci, ci, vp, ci, vp, vp, vp]
     lib.dtw_wsdtw_cseg.argtypes = [vp, ci, ci, vp]
+    lib.dtw_batch_create.argtypes = [vp, ci, vp, vp, vp, vp, ci, vp, vp, vp, vp, ci,
+                                     ctypes.POINTER(vp)]
+    lib.dtw_batch_run.argtypes = [vp]
+    lib.dtw_batch_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(cf)]
+    lib.dtw_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes",
                         "dtw_encoder_param_count"):
@@ -316,6 +323,65 @@ def dtw_static_scratch_bytes() -> int:
     return int(load_library().dtw_static_scratch_bytes())
 
 
+class BatchPlan:
+    """A planned batch (dtw_batch_create): fixed device inputs, outputs owned
+    here, the DP schedule chosen by the autotuner, one CUDA graph per run."""
+
+    def __init__(self, h: int, As: Sequence, Bs: Sequence, autotune: bool = True):
+        import torch
+        n = len(As)
+        self.As = [_features(a) for a in As]
+        self.Bs = [_features(b) for b in Bs]
+        dev = self.As[0].device
+        D = self.As[0].shape[1]
+        caps = [min(a.shape[0], b.shape[0]) for a, b in zip(self.As, self.Bs)]
+        self.off = np.concatenate([[0], np.cumsum(caps)[:-1]]).astype(np.int64)
+        self.paths = torch.empty((int(sum(caps)), 2), dtype=torch.int32, device=dev)
+        self.path_len = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.cost = torch.zeros(n, dtype=torch.float32, device=dev)
+        Ap = (ctypes.c_void_p * n)(*[a.data_ptr() for a in self.As])
+        Bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in self.Bs])
+        La = (ctypes.c_int * n)(*[a.shape[0] for a in self.As])
+        Lb = (ctypes.c_int * n)(*[b.shape[0] for b in self.Bs])
+        off = (ctypes.c_int64 * n)(*[int(x) for x in self.off])
+        b = ctypes.c_void_p(0)
+        _check(load_library().dtw_batch_create(
+            h, n, ctypes.cast(Ap, ctypes.c_void_p), ctypes.cast(La, ctypes.c_void_p),
+            ctypes.cast(Bp, ctypes.c_void_p), ctypes.cast(Lb, ctypes.c_void_p), D,
+            self.paths.data_ptr(), ctypes.cast(off, ctypes.c_void_p), self.path_len.data_ptr(),
+            self.cost.data_ptr(), DTW_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(b)),
+            "dtw_batch_create")
+        self.b = b.value
+
+    def run(self) -> None:
+        _check(load_library().dtw_batch_run(self.b), "dtw_batch_run")
+
+    def info(self):
+        """(rows per lane chosen, autotuner times in ms for 2, 3, 4 rows per lane)."""
+        R = ctypes.c_int(0)
+        t = (ctypes.c_float * 3)()
+        _check(load_library().dtw_batch_info(self.b, ctypes.byref(R), t), "dtw_batch_info")
+        return R.value, [float(x) for x in t]
+
+    def results(self):
+        """(list of paths, costs, path lengths) of the last run (synchronises)."""
+        lens = self.path_len.cpu().numpy()
+        out = [self.paths[self.off[k]:self.off[k] + lens[k]] if lens[k] > 0 else None
+               for k in range(len(lens))]
+        return out, self.cost.cpu().numpy(), lens
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            load_library().dtw_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- convenience wrapper --------------------------------------------------------------
 
 class Aligner:
@@ -470,6 +536,13 @@ class Aligner:
         dtw_wsdtw_cseg(self.h, nfrag, Lb, c)
         self._leave()
         return c
+
+    def plan_batch(self, As: List, Bs: List, autotune: bool = True) -> "BatchPlan":
+        """A graph-captured, autotuned plan of this batch (runs on this handle's stream)."""
+        self._enter()
+        plan = BatchPlan(self.h, As, Bs, autotune)
+        self._leave()
+        return plan
 
     def align_many(self, As: List, Bs: List, **opts):
         """Align independent pairs; returns (list of paths or None, costs, statuses)."""

@@ -108,3 +108,50 @@ def test_batch_config2_shapes_equal_single(aligner):
         single, total = aligner.align(As[k], Bs[k])
         np.testing.assert_array_equal(paths[k].cpu().numpy(), single.cpu().numpy())
         assert float(costs[k]) == total
+
+
+def test_planned_batch_equals_align_many_and_replays(aligner):
+    # the graph-captured, autotuned plan: the same result as dtw_align_many
+    # bit for bit, every replay identical, and a replay after the inputs
+    # changed in place aligns the new inputs (fresh border tags, reset queue)
+    pairs = uneven_pairs(95, 20, 40, 1800)
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    ref_paths, ref_costs, st = aligner.align_many(As, Bs)
+    assert (st == 0).all()
+    plan = aligner.plan_batch(As, Bs, autotune=True)
+    R, tuned = plan.info()
+    assert R in (2, 3, 4) and tuned[R - 2] > 0
+    for rep in range(3):
+        if rep:
+            plan.run()
+        paths, costs, lens = plan.results()
+        for k in range(len(pairs)):
+            np.testing.assert_array_equal(paths[k].cpu().numpy(), ref_paths[k].cpu().numpy())
+        np.testing.assert_array_equal(costs, ref_costs)
+    # new contents, same shapes: B of every pair replaced by another warp of A
+    new = [synth.warped_pair(synth.rng_for(96, k), p.A.shape[0], p.B.shape[0], 12, knots=4,
+                             tmin=0.7, tmax=1.4) for k, p in enumerate(pairs)]
+    for k, q in enumerate(new):
+        As[k].copy_(dev(q.A))
+        Bs[k].copy_(dev(q.B))
+    plan.run()
+    paths, costs, lens = plan.results()
+    for k, q in enumerate(new):
+        assert_oracle(q.A, q.B, paths[k], float(costs[k]))
+    ref2, c2, _ = aligner.align_many(As, Bs)
+    np.testing.assert_array_equal(costs, c2)
+    plan.close()
+
+
+def test_planned_batch_without_autotune(aligner):
+    pairs = uneven_pairs(97, 5, 100, 600)
+    As = [dev(p.A) for p in pairs]
+    Bs = [dev(p.B) for p in pairs]
+    plan = aligner.plan_batch(As, Bs, autotune=False)
+    R, tuned = plan.info()
+    assert R == 3 and tuned[0] == -1.0 and tuned[2] == -1.0
+    paths, costs, lens = plan.results()
+    for k, p in enumerate(pairs):
+        assert_oracle(p.A, p.B, paths[k], float(costs[k]))
+    plan.close()
