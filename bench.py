@@ -272,6 +272,7 @@ def run_ours(args):
             step()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
+            dp_ms.append(al.stage_times()[1])
         torch.cuda.synchronize(dev)
         clk.mark_end()
         if ws > 1:
@@ -416,7 +417,7 @@ def run_batch(args):
     if st is not None and (st != 0).any():
         raise RuntimeError(f"batch alignment failed on rank {rank}")
     plan = al.plan_batch(As, Bs, autotune=True)
-    R_tuned, tuned_ms = plan.info()
+    R_tuned, NS_tuned, tuned_ms = plan.info()
 
     def step():
         with torch.cuda.stream(stream):
@@ -440,7 +441,6 @@ def run_batch(args):
             step()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            dp_ms.append(al.stage_times()[1])
         torch.cuda.synchronize(dev)
         clk.mark_end()
         if ws > 1:
@@ -511,17 +511,19 @@ def run_batch(args):
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"pairs split by cell count over {ws} rank(s)",
                        "graph": "one CUDA graph replay per step (dtw_batch_run)",
-                       "schedule": f"autotuned: {R_tuned} rows per lane"},
+                       "schedule": f"autotuned: {R_tuned} rows per lane, {NS_tuned} strips "
+                                   f"per CTA"},
             "batch": {"graph_ms": 1e3 * t_max / args.steps,
                       "align_many_ms": statistics.median(many_ms),
-                      "autotune_rows_per_lane": R_tuned,
-                      "autotune_ms_by_rows_per_lane": {"2": tuned_ms[0], "3": tuned_ms[1],
-                                                       "4": tuned_ms[2]}},
+                      "autotune_rows_per_lane": R_tuned, "autotune_strips_per_cta": NS_tuned,
+                      "autotune_ms": {f"R{r}_NS{ns}": tuned_ms[(3 if ns == 4 else 0) + r - 2]
+                                      for ns in (2, 4) for r in (2, 3, 4)}},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": None,
                          "kernel": "k_dp_split, batch mode (work queue over pairs), "
-                                   "3 rows per lane (timed through dtw_align_many)",
+                                   "3 rows per lane, 4 strips per CTA (timed through "
+                                   "dtw_align_many)",
                          "ops_per_cell": 18, "dp_ms": 1e3 * dp_avg,
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{clock:.0f} MHz (sm_max_mhz, {src})"},

@@ -90,6 +90,11 @@ typedef struct dtw_options {
      * or DTW_SCHEDULE_SPLIT (2: a cost warp and a DP warp per strip;
      * rows_per_lane 2, 3 or 4).  Results do not depend on it. */
     int dp_schedule;
+    /* Strips per CTA of the cost/DP warp-pair DP: 0 (default: four when a
+     * pair has more two-strip groups than the GPU has SMs and the kernel has
+     * the four-strip form for D and rows_per_lane, else two), 2 or 4 (D <= 16,
+     * rows_per_lane 2 or 3; else two).  Results do not depend on it. */
+    int strips_per_cta;
 } dtw_options;
 
 #define DTW_SCHEDULE_AUTO 0
@@ -191,8 +196,9 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
  * (a serving loop refilling fixed staging buffers): dtw_batch_create lays out
  * the batch once (its own workspace and border buffer), picks the DP schedule
  * with an autotuner when flags has DTW_BATCH_AUTOTUNE (it aligns the batch with
- * 2, 3 and 4 rows per lane, where D allows them, and keeps the fastest; every
- * schedule gives the same result, bit for bit), and captures the whole batch
+ * 2, 3 and 4 rows per lane and two or four strips per CTA, where D allows
+ * them, and keeps the fastest; every schedule gives the same result, bit for
+ * bit), and captures the whole batch
  * (a new tag for the border entries, the batched normalisation, the
  * persistent DP over the (pair, strip group) work queue, the batched
  * backtrace) into one CUDA graph.  dtw_batch_run launches that graph on the
@@ -212,9 +218,14 @@ int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
                      dtw_batch** out);
 /* One replay of the plan's graph on the handle's stream (asynchronous). */
 int dtw_batch_run(dtw_batch* b);
-/* The chosen rows per lane and the autotuner's times in ms for 2, 3, 4 rows
- * per lane (-1 where not tried); either pointer may be NULL. */
-int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, float* tuned_ms);
+/* The chosen schedule (rows per lane, strips per CTA) and the autotuner's
+ * times in ms: tuned_ms[0..2] for 2, 3, 4 rows per lane with two strips per
+ * CTA, tuned_ms[3..5] with four (-1 where not tried or not supported); any
+ * pointer may be NULL. */
+int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, int* strips_per_cta,
+                   float* tuned_ms);
+/* Waits for the plan's last replay and frees it; needs only the plan (it may
+ * run after its handle was destroyed).  dtw_batch_run needs the handle alive. */
 int dtw_batch_destroy(dtw_batch* b);
 
 /* ---- weakly-ordered Segmental DTW (Sec. II-C) ------------------------------ */

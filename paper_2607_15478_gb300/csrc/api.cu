@@ -99,8 +99,6 @@ struct Layout {
 // kernel supports them (else one row per lane); the default is the cost/DP
 // warp pair with 3 rows per lane for D <= 32, one row per lane above.
 DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
-    (void)La;
-    (void)num_sms;
     const DpPlan one = {0, 1, kWarpsPerGroup};
     if (o.cost_precision == DTW_COST_BF16) return {2, 3, kSplitStrips, 1};
     const int req = o.rows_per_lane;
@@ -111,8 +109,15 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
         return one;
     }
     const int R = req == 0 ? 3 : req;
-    if (split_supported(dp, R)) return {2, R, kSplitStrips};
-    return one;
+    if (!split_supported(dp, R)) return one;
+    // Four strips per CTA when the two-strip groups would not all be resident
+    // at once (the DP is then bound by how many strips advance together, not
+    // by the chain of one strip after another)
+    if (o.strips_per_cta == 4 && split_supported(dp, R, 4)) return {2, R, 4};
+    if (o.strips_per_cta == 2) return {2, R, 2};
+    const int groups2 = (La + 2 * strip_rows(R) - 1) / (2 * strip_rows(R));
+    if (num_sms > 0 && groups2 > num_sms && split_supported(dp, R, 4)) return {2, R, 4};
+    return {2, R, kSplitStrips};
 }
 
 cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
@@ -122,7 +127,7 @@ cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int
         case 1: return launch_dp_multirow(a, dp, plan.R, num_sms, s);
         case 2:
             return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s)
-                             : launch_dp_split(a, dp, plan.R, num_sms, s);
+                             : launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -212,6 +217,7 @@ dtw_options defaults() {
     o.debug_skip_publish = -1;
     o.rows_per_lane = 0;
     o.dp_schedule = DTW_SCHEDULE_AUTO;
+    o.strips_per_cta = 0;
     return o;
 }
 
@@ -327,7 +333,7 @@ struct SubseqBatch {
 // last pairs to start are short and no long chain of strips is left alone at
 // the end (the order does not change any result).
 struct BatchSetup {
-    int m = 0, D = 0, dp = 0, R = 3, maxLa = 0, maxLb = 0, max_frames = 0;
+    int m = 0, D = 0, dp = 0, R = 3, NS = 2, maxLa = 0, maxLb = 0, max_frames = 0;
     std::vector<int> idx;  // pair indices in work-queue order
     std::vector<Layout> Ls;
     std::vector<size_t> off, boff;
@@ -336,10 +342,11 @@ struct BatchSetup {
     size_t ws_bytes = 0, border_bytes = 0;
 };
 
-BatchSetup batch_setup(std::vector<int> idx, const int* La, const int* Lb, int D, int R) {
+BatchSetup batch_setup(std::vector<int> idx, const int* La, const int* Lb, int D, int R, int NS) {
     BatchSetup b;
     b.m = (int)idx.size();
     b.R = R;
+    b.NS = NS;
     b.D = D;
     b.dp = padded_dim(D);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
@@ -347,7 +354,7 @@ BatchSetup batch_setup(std::vector<int> idx, const int* La, const int* Lb, int D
     });
     b.idx = idx;
     const int m = b.m;
-    const DpPlan plan = {2, R, kSplitStrips};
+    const DpPlan plan = {2, R, NS};
     b.Ls.resize(m);
     b.off.resize(m);
     b.boff.resize(m);
@@ -487,7 +494,7 @@ int batch_launch(const BatchSetup& b, char* ws, bool subseq, int num_sms, cudaSt
     if (subseq)
         CU(launch_dp_subseq_many(dps, item0, m, b.item0[m], ticket, b.dp, num_sms, s));
     else
-        CU(launch_dp_split_many(dps, item0, m, b.item0[m], ticket, b.dp, b.R, num_sms, s));
+        CU(launch_dp_split_many(dps, item0, m, b.item0[m], ticket, b.dp, b.R, b.NS, num_sms, s));
     if (ev) CU(cudaEventRecord(ev[2], s));
     if (!subseq)
         CU(launch_backtrace_bands_many(reinterpret_cast<const BtArgs*>(ws + b.off_bt), m, b.maxLa,
@@ -499,9 +506,9 @@ int batch_launch(const BatchSetup& b, char* ws, bool subseq, int num_sms, cudaSt
 int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, const int* La,
                 const float* const* B, const int* Lb, int D, const dtw_options& o, int R,
                 int32_t* paths, const int64_t* path_off, int* path_len, float* cost,
-                const SubseqBatch* sub = nullptr) {
+                const SubseqBatch* sub = nullptr, int NS = 2) {
     if (idx.empty()) return DTW_OK;
-    const BatchSetup b = batch_setup(std::move(idx), La, Lb, D, R);
+    const BatchSetup b = batch_setup(std::move(idx), La, Lb, D, R, NS);
     int rc = ensure_workspace(h, b.ws_bytes, b.border_bytes);
     if (rc != DTW_OK) return rc;
     unsigned epoch = ++h->epoch;
@@ -520,14 +527,17 @@ int align_batch(dtw_handle* h, std::vector<int> idx, const float* const* A, cons
 
 // A planned, graph-captured batch (dtw_batch_create).
 struct dtw_batch {
-    dtw_handle* h = nullptr;
-    int n = 0, D = 0, R = 3;
+    dtw_handle* h = nullptr;      // used by dtw_batch_run only
+    int device = 0;
+    cudaEvent_t done = nullptr;   // recorded after every replay (destroy waits on it)
+    int n = 0, D = 0, R = 3, NS = 2;
     char* ws = nullptr;
     unsigned long long* border = nullptr;
     BatchSetup setup;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    float tuned_ms[3] = {-1.f, -1.f, -1.f};  // R = 2, 3, 4
+    // R = 2, 3, 4 with two strips per CTA, then with four
+    float tuned_ms[6] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
 };
 
 extern "C" {
@@ -748,8 +758,11 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
         }
     }
     if (batched) {
+        // a batch fills the GPU: four strips per CTA where the kernel has them
+        // (unless the options ask for two)
+        const int NSb = (o.strips_per_cta != 2 && split_supported(dp, Rb, 4)) ? 4 : 2;
         const int rc = align_batch(h, valid, A, La, B, Lb, D, o, Rb, paths, path_off, path_len,
-                                   cost);
+                                   cost, nullptr, NSb);
         if (rc != DTW_OK) return rc;
     }
     for (int k = 0; k < n && !batched; ++k) {
@@ -1241,8 +1254,12 @@ int dtw_wsdtw_cseg(dtw_handle* h, int nfrag, int Lb, float* cseg) {
 
 int dtw_batch_destroy(dtw_batch* b) {
     if (!b) return DTW_ERR_INVALID;
-    DeviceGuard g(b->h->device);
-    cudaStreamSynchronize(b->h->stream);
+    // the plan's own device and event: the handle may already be gone
+    DeviceGuard g(b->device);
+    if (b->done) {
+        cudaEventSynchronize(b->done);
+        cudaEventDestroy(b->done);
+    }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->ws) cudaFree(b->ws);
@@ -1276,24 +1293,26 @@ int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
     const dtw_options o = defaults();
     std::vector<int> idx(n);
     for (int k = 0; k < n; ++k) idx[k] = k;
-    // candidate schedules: rows per lane of the warp-pair DP
-    std::vector<int> Rs;
+    // candidate schedules: rows per lane and strips per CTA of the warp-pair DP
+    std::vector<std::pair<int, int>> cands;
     if (flags & DTW_BATCH_AUTOTUNE) {
-        for (int R = 2; R <= 4; ++R)
-            if (split_supported(dp, R)) Rs.push_back(R);
+        for (int NS : {4, 2})
+            for (int R = 2; R <= 4; ++R)
+                if (split_supported(dp, R, NS)) cands.push_back({R, NS});
     } else {
-        Rs.push_back(3);
+        cands.push_back({3, split_supported(dp, 3, 4) ? 4 : 2});
     }
     std::vector<BatchSetup> setups;
     size_t ws_bytes = 0, border_bytes = 0;
-    for (int R : Rs) {
-        setups.push_back(batch_setup(idx, La, Lb, D, R));
+    for (auto [R, NS] : cands) {
+        setups.push_back(batch_setup(idx, La, Lb, D, R, NS));
         ws_bytes = std::max(ws_bytes, setups.back().ws_bytes);
         border_bytes = std::max(border_bytes, setups.back().border_bytes);
     }
     dtw_batch* b = new (std::nothrow) dtw_batch();
     if (!b) return DTW_ERR_OOM;
     b->h = h;
+    b->device = h->device;
     b->n = n;
     b->D = D;
     if (cudaMalloc(&b->ws, ws_bytes) != cudaSuccess ||
@@ -1315,7 +1334,8 @@ int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
         return code;
     };
     if (cudaMemsetAsync(b->border, 0, border_bytes, s) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
         return fail(DTW_ERR_CUDA);
     // the autotuner: every candidate twice, the second run timed (all
     // candidates compute the same result, bit for bit)
@@ -1337,7 +1357,7 @@ int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                 return fail(DTW_ERR_CUDA);
         }
-        b->tuned_ms[setups[c].R - 2] = ms;
+        b->tuned_ms[(setups[c].NS == 4 ? 3 : 0) + setups[c].R - 2] = ms;
         if (c == 0 || ms < best_ms) {
             best = (int)c;
             best_ms = ms;
@@ -1345,6 +1365,7 @@ int dtw_batch_create(dtw_handle* h, int n, const float* const* A, const int* La,
     }
     b->setup = setups[best];
     b->R = b->setup.R;
+    b->NS = b->setup.NS;
     // the chosen schedule's descriptors stay in the plan's workspace; the
     // graph bumps their epoch, then normalises, sweeps and backtraces
     const BatchDesc d = batch_descriptors(b->setup, b->ws, b->border, A, La, B, Lb, o, ++epoch,
@@ -1376,14 +1397,17 @@ int dtw_batch_run(dtw_batch* b) {
     DeviceGuard g(b->h->device);
     if (!g.ok) return DTW_ERR_CUDA;
     CU(cudaGraphLaunch(b->exec, b->h->stream));
+    CU(cudaEventRecord(b->done, b->h->stream));
     return DTW_OK;
 }
 
-int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, float* tuned_ms) {
+int dtw_batch_info(const dtw_batch* b, int* rows_per_lane, int* strips_per_cta,
+                   float* tuned_ms) {
     if (!b) return DTW_ERR_INVALID;
     if (rows_per_lane) *rows_per_lane = b->R;
+    if (strips_per_cta) *strips_per_cta = b->NS;
     if (tuned_ms)
-        for (int k = 0; k < 3; ++k) tuned_ms[k] = b->tuned_ms[k];
+        for (int k = 0; k < 6; ++k) tuned_ms[k] = b->tuned_ms[k];
     return DTW_OK;
 }
 

@@ -1,0 +1,873 @@
+// Exact DTW dynamic programming, warp-specialised: every strip of A has a
+// DP warp and a cost warp, and every CTA of NS strips a reader and a writer
+// warp for the border it shares with the neighbouring CTAs.  Same
+// recurrence, step set, weights and tie order as the other DP kernels
+// (Sec. V, Sec. II-D); only the division of labour differs.
+//
+//   - The strip geometry is that of the multi-row kernel: 31 R rows, lane t
+//     (0..30) of the DP warp holds rows R t .. R t + R - 1 of the strip,
+//     lane 31 is the ghost lane that carries the two bottom rows of the strip
+//     above (cost 1e30, weight 0 on the (1,2) candidate fed the border value).
+//   - The cost warp of the strip computes C' = (1 - mu) - a^_i . b^_j for the
+//     same rows, 8 columns at a time (one FMA per feature, in feature order,
+//     so the values are bit-identical to the other kernels'), reading the
+//     frames of B from its TMA-fed ring, and hands them to the DP warp
+//     through a ring of kCostSlots sub-chunks in shared memory with one
+//     full and one empty mbarrier per slot.  The DP warp loads the costs of
+//     the next sub-chunk half-way through the current one.
+//   - The DP warp runs only the recurrence: per column two shuffles, three
+//     FMAs, a three-way minimum and two compares per cell.
+//   - Every DP warp takes its top border from a ring of kRingBlk sub-chunks
+//     in shared memory and writes its two bottom rows into the next ring,
+//     with a full and an empty mbarrier per block.  The first strip's ring
+//     is filled by the reader warp from the global border that the CTA
+//     above publishes; the last strip's ring is drained by the writer warp
+//     into this CTA's global border.  The L2 round trips of that exchange
+//     thus never sit in a DP warp, and all DP warps do the same work per
+//     sub-chunk (in a chain of strips the slowest one sets the pace).
+//   - Every wait is bounded (DTW_ERR_TIMEOUT) and gives up when the call has
+//     failed elsewhere.
+#pragma once
+#include "dp_device.cuh"
+
+// The kernel templates are included by dp_split.cu (two strips per CTA) and
+// dp_split4.cu (four strips per CTA), which instantiate and launch them.
+namespace pardtw {
+namespace {
+
+constexpr int kGhostLane = 31;
+constexpr int kOutLane = 30;    // holds the strip's two bottom rows
+constexpr int kCostSlots = 4;   // sub-chunks of costs in flight per strip
+static_assert(kRingBlk >= 4, "the DP warp waits for output ring blocks four at a time");
+
+// One slot holds the 8 costs of each of a lane's R rows: float4 q of lane l
+// (q = 2 k + half) at [q][l], so a warp's 16-byte accesses are contiguous.
+template <int R>
+struct CostRing {
+    static constexpr int kF4 = 2 * R;
+    static constexpr int kSlotBytes = kF4 * kWarp * 16;
+    static constexpr int kBytes = kCostSlots * kSlotBytes;
+};
+
+// BF16 cost: one cost slot holds the 8 costs of each of the 32 R rows of the
+// strip row by row, kRowFloats floats per row (48-byte rows: the DP warp's
+// 16-byte loads of rows 3l+k then fall in distinct bank groups).
+constexpr int kRowFloats = 12;
+template <int R>
+struct CostRingRM {
+    static constexpr int kSlotBytes = 32 * R * kRowFloats * 4;
+    static constexpr int kBytes = kCostSlots * kSlotBytes;
+};
+// BF16 cost: the strip's rows of A as bf16 (32 R rows of kBfStride), and a
+// ring of kBfSlots blocks of 16 frames of B (one chunk each) filled by TMA.
+constexpr int kBfSlots = 4;
+constexpr int kBfBlkBytes = kColsPerWord * kBfStride * 2;
+
+template <int DP, int R, bool kBF>
+struct SplitSmem {
+    // per strip slot: the cost warp's operands (B stage, or A tile and B
+    // stage), then the cost ring
+    static constexpr int kOperandBytes =
+        kBF ? 32 * R * kBfStride * 2 + kBfSlots * kBfBlkBytes : BStage<DP>::kWarpBytes;
+    static constexpr int kStripBytes =
+        kOperandBytes + (kBF ? CostRingRM<R>::kBytes : CostRing<R>::kBytes);
+};
+
+// Barrier `slot` of an array of 8-byte mbarriers, and the phase parity a
+// waiter for the t-th (lifetime) use of a ring of n slots expects.
+__device__ __forceinline__ unsigned bar_at(unsigned base, unsigned slot) { return base + 8 * slot; }
+__device__ __forceinline__ unsigned use_parity(unsigned t, unsigned n) { return (t / n) & 1u; }
+
+// Sub-chunks [x, y) (columns 8x .. 8y-1) that `strip` sweeps: all of them
+// without a band, else the band's range of the strip.
+__device__ __forceinline__ int2 strip_range(const DpArgs& p, int strip) {
+    if (!p.ranges) return make_int2(0, (p.Lb + kSub - 1) / kSub);
+    return p.ranges[strip];
+}
+
+// Cost warp of `strip`: all sub-chunks of the sweep, in order.
+template <int DP, int R>
+__device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, unsigned cring,
+                                         unsigned cfull, unsigned cempty, unsigned csub,
+                                         BRing<DP>& br) {
+    using S = BStage<DP>;
+    using CR = CostRing<R>;
+    constexpr int kRows = 31 * R;
+    constexpr int kFG = 4;            // features per group of loads
+    constexpr int kNG = DP / kFG;     // DP is a multiple of 4
+    const bool ghost = lane == kGhostLane;
+    const int i0 = strip * kRows + lane * R;
+    float na[R][DP];  // -a^_i of the lane's rows (0 in the ghost lane)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4* s = reinterpret_cast<const float4*>(p.Ahat + (size_t)(i0 + k) * DP);
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+            const float4 v = ghost ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(s + q);
+            na[k][4 * q] = -v.x;
+            na[k][4 * q + 1] = -v.y;
+            na[k][4 * q + 2] = -v.z;
+            na[k][4 * q + 3] = -v.w;
+        }
+    }
+    const float kc = ghost ? kGhostCost : p.kcost;
+    const int Lb_pad = p.nchunk * kColsPerWord;
+    const int2 rg = strip_range(p, strip);  // sub-chunks rg.x .. rg.y-1
+    const int q0 = rg.x * kSub / S::kBlk;
+    br.begin(q0, min((rg.y * kSub + S::kBlk - 1) / S::kBlk, (Lb_pad + S::kBlk - 1) / S::kBlk));
+    br.top_up(q0, p.Bhat, Lb_pad, lane);
+    for (int n = rg.x; n < rg.y; ++n) {
+        const int js = n * kSub;
+        if (js % S::kBlk == 0 || n == rg.x) {
+            const int q = js / S::kBlk;
+            if (!br.wait(q, p.ctl, p.timeout_ns)) break;
+            br.top_up(q, p.Bhat, Lb_pad, lane);
+        }
+        const unsigned t = csub + (unsigned)(n - rg.x);
+        const unsigned slot = t % kCostSlots;
+        // the DP warp has read this slot's previous contents
+        if (!mbar_wait(bar_at(cempty, slot), use_parity(t, kCostSlots) ^ 1u, p.ctl, p.timeout_ns,
+                       6))
+            break;
+        // the 8 frames of the sub-chunk, feature-major (16 floats per feature)
+        const unsigned nb = br.chunk_s(js >> 4) + (unsigned)(js & kSub) * 4u;
+        float c[R][kSub];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int f = 0; f < kSub; ++f) c[k][f] = kc;
+        // loads of the next feature group are issued before the FMAs of the
+        // current one
+        float4 bv[2][2 * kFG];
+#pragma unroll
+        for (int e = 0; e < kFG; ++e) {
+            bv[0][2 * e] = lds128(nb + (unsigned)(e * kColsPerWord) * 4u);
+            bv[0][2 * e + 1] = lds128(nb + (unsigned)(e * kColsPerWord + 4) * 4u);
+        }
+#pragma unroll
+        for (int gi = 0; gi < kNG; ++gi) {
+            if (gi + 1 < kNG) {
+#pragma unroll
+                for (int e = 0; e < kFG; ++e) {
+                    const int d = (gi + 1) * kFG + e;
+                    bv[(gi + 1) & 1][2 * e] = lds128(nb + (unsigned)(d * kColsPerWord) * 4u);
+                    bv[(gi + 1) & 1][2 * e + 1] =
+                        lds128(nb + (unsigned)(d * kColsPerWord + 4) * 4u);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < kFG; ++e) {
+                const int d = gi * kFG + e;
+                const float4 b0 = bv[gi & 1][2 * e], b1 = bv[gi & 1][2 * e + 1];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    c[k][0] = fmaf(na[k][d], b0.x, c[k][0]);
+                    c[k][1] = fmaf(na[k][d], b0.y, c[k][1]);
+                    c[k][2] = fmaf(na[k][d], b0.z, c[k][2]);
+                    c[k][3] = fmaf(na[k][d], b0.w, c[k][3]);
+                    c[k][4] = fmaf(na[k][d], b1.x, c[k][4]);
+                    c[k][5] = fmaf(na[k][d], b1.y, c[k][5]);
+                    c[k][6] = fmaf(na[k][d], b1.z, c[k][6]);
+                    c[k][7] = fmaf(na[k][d], b1.w, c[k][7]);
+                }
+            }
+        }
+        const unsigned dst = cring + slot * CR::kSlotBytes + (unsigned)lane * 16u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            sts128(dst + (unsigned)(2 * k) * (kWarp * 16),
+                   make_float4(c[k][0], c[k][1], c[k][2], c[k][3]));
+            sts128(dst + (unsigned)(2 * k + 1) * (kWarp * 16),
+                   make_float4(c[k][4], c[k][5], c[k][6], c[k][7]));
+        }
+        mbar_arrive(bar_at(cfull, slot));
+    }
+    br.drain();
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+// d += a (16x16 bf16, row) * b (16x8 bf16, col), FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// BF16 cost warp of `strip` (DP = K = 64 or 128, R = 3 rows per lane): per
+// 16 columns one 96 x 16 x DP product on the tensor cores (6 x 2 tiles of
+// m16n8k16 per 16 features), costs C' = (1 - mu) - dot written row-major into
+// two cost slots; the ghost lane's rows get 1e30.  A's rows are converted to
+// bf16 into shared memory once per strip; B's bf16 frames arrive by TMA, one
+// chunk per block.
+template <int DP, int R>
+__device__ __forceinline__ void run_cost_bf16(const DpArgs& p, int strip, int lane, unsigned a_s,
+                                              unsigned b_s, unsigned bbar_s, unsigned& bbase,
+                                              unsigned cring, unsigned cfull, unsigned cempty,
+                                              unsigned csub) {
+    constexpr int kRows = 31 * R;       // real rows of the strip
+    constexpr int kM = 32 * R;          // rows of the product (6 tiles of 16)
+    constexpr int kMT = kM / 16;
+    constexpr int kKS = DP / 16;        // k-steps of 16 features
+    constexpr int kRowBytes = kBfStride * 2;
+    const int2 rg = strip_range(p, strip);  // sub-chunks rg.x (even) .. rg.y-1
+    const int c_lo = rg.x / 2, c_hi = (rg.y + 1) / 2;
+    const int nsub = rg.y;
+    // A: rows r = 0 .. kM-1 of the strip as bf16 (rows >= kRows are zero)
+    for (int r = lane; r < kM; r += kWarp) {
+        const float* src = p.Ahat + (size_t)(strip * kRows + r) * DP;
+#pragma unroll 4
+        for (int d = 0; d < DP; d += 8) {
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (r < kRows) {
+                v0 = __ldg(reinterpret_cast<const float4*>(src + d));
+                v1 = __ldg(reinterpret_cast<const float4*>(src + d + 4));
+            }
+            const uint32_t w0 = pack_bf16x2(v0.x, v0.y), w1 = pack_bf16x2(v0.z, v0.w);
+            const uint32_t w2 = pack_bf16x2(v1.x, v1.y), w3 = pack_bf16x2(v1.z, v1.w);
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             a_s + (unsigned)(r * kRowBytes + d * 2)),
+                         "r"(w0), "r"(w1), "r"(w2), "r"(w3)
+                         : "memory");
+        }
+    }
+    __syncwarp();
+    const char* gb = static_cast<const char*>(p.Bbf);
+    int issued = c_lo, waited = c_lo;
+    auto issue = [&](int c) {  // lane 0: chunk c of B into slot (bbase + c - c_lo) % kBfSlots
+        if (lane == 0) {
+            const unsigned t = bbase + (unsigned)(c - c_lo);
+            tma_load(b_s + (t % kBfSlots) * kBfBlkBytes, gb + (size_t)c * kBfBlkBytes,
+                     (unsigned)kBfBlkBytes, bbar_s + 8 * (t % kBfSlots));
+        }
+    };
+    while (issued < c_hi && issued < c_lo + kBfSlots - 1) issue(issued++);
+    const float kc = p.kcost;
+    const int g = lane >> 2, t4 = lane & 3;
+    bool ok = true;
+    for (int c = c_lo; c < c_hi && ok; ++c) {
+        // chunk c of B is in its slot
+        const unsigned tb = bbase + (unsigned)(c - c_lo);
+        if (!mbar_wait(bbar_s + 8 * (tb % kBfSlots), (tb / kBfSlots) & 1u, p.ctl, p.timeout_ns,
+                       4)) {
+            ok = false;
+            break;
+        }
+        waited = c + 1;
+        if (issued < c_hi) issue(issued++);
+        const int nj = (2 * c + 1 < nsub) ? 2 : 1;  // sub-chunks of this chunk
+        const unsigned t0 = csub + (unsigned)(2 * c - rg.x);
+        for (int j = 0; j < nj; ++j)
+            if (!mbar_wait(bar_at(cempty, (t0 + j) % kCostSlots),
+                           use_parity(t0 + j, kCostSlots) ^ 1u, p.ctl, p.timeout_ns, 6)) {
+                ok = false;
+                break;
+            }
+        if (!ok) break;
+        // B fragments of the chunk's 16 frames: n-tile j = frames 8j .. 8j+7
+        const unsigned bslot = b_s + (tb % kBfSlots) * kBfBlkBytes;
+        uint32_t bf[2][kKS][2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int kq = 0; kq < kKS / 2; ++kq)
+                ldsm_x4(bslot + (unsigned)((8 * j + (lane & 7)) * kRowBytes +
+                                           (32 * kq + 8 * (lane >> 3)) * 2),
+                        bf[j][2 * kq][0], bf[j][2 * kq][1], bf[j][2 * kq + 1][0],
+                        bf[j][2 * kq + 1][1]);
+        float acc[kMT][2][4];
+#pragma unroll
+        for (int mt = 0; mt < kMT; ++mt)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][j][e] = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < kMT; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < kKS; ++ks) {
+                uint32_t a[4];
+                ldsm_x4(a_s + (unsigned)((16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1)) *
+                                             kRowBytes +
+                                         (16 * ks + 8 * (lane >> 4)) * 2),
+                        a[0], a[1], a[2], a[3]);
+                mma_bf16(acc[mt][0], a, bf[0][ks]);
+                mma_bf16(acc[mt][1], a, bf[1][ks]);
+            }
+        // costs into the two slots: rows 16 mt + g (+8), columns 2 t4, 2 t4 + 1
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (j >= nj) break;
+            const unsigned slot = cring + ((t0 + j) % kCostSlots) * CostRingRM<R>::kSlotBytes;
+#pragma unroll
+            for (int mt = 0; mt < kMT; ++mt) {
+                const int r0 = 16 * mt + g, r1 = r0 + 8;
+                const float v00 = r0 < kRows ? kc - acc[mt][j][0] : kGhostCost;
+                const float v01 = r0 < kRows ? kc - acc[mt][j][1] : kGhostCost;
+                const float v10 = r1 < kRows ? kc - acc[mt][j][2] : kGhostCost;
+                const float v11 = r1 < kRows ? kc - acc[mt][j][3] : kGhostCost;
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(
+                                 slot + (unsigned)(r0 * kRowFloats * 4 + t4 * 8)),
+                             "f"(v00), "f"(v01)
+                             : "memory");
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(
+                                 slot + (unsigned)(r1 * kRowFloats * 4 + t4 * 8)),
+                             "f"(v10), "f"(v11)
+                             : "memory");
+            }
+            mbar_arrive(bar_at(cfull, (t0 + j) % kCostSlots));
+        }
+    }
+    // leave no copy in flight (bounded)
+    for (int c = waited; c < issued; ++c) {
+        const unsigned tb = bbase + (unsigned)(c - c_lo);
+        const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+        while (!__all_sync(kFull, mbar_try_wait(bbar_s + 8 * (tb % kBfSlots),
+                                                (tb / kBfSlots) & 1u))) {
+            if (__shfl_sync(kFull, global_ns(), 0) - t0 > 1000000000LL) break;
+        }
+    }
+    bbase += (unsigned)(issued - c_lo);
+}
+
+// The costs of lifetime sub-chunk t (its slot must be full) into c;
+// kRM: the row-major slot of the BF16 cost.
+template <int R, bool kRM>
+__device__ __forceinline__ void load_costs(unsigned cring, unsigned t, int lane,
+                                           float (*c)[kSub]) {
+    if constexpr (kRM) {
+        const unsigned src = cring + (t % kCostSlots) * CostRingRM<R>::kSlotBytes +
+                             (unsigned)(lane * R) * (kRowFloats * 4);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float4 v0 = lds128(src + (unsigned)k * (kRowFloats * 4));
+            const float4 v1 = lds128(src + (unsigned)k * (kRowFloats * 4) + 16);
+            c[k][0] = v0.x;
+            c[k][1] = v0.y;
+            c[k][2] = v0.z;
+            c[k][3] = v0.w;
+            c[k][4] = v1.x;
+            c[k][5] = v1.y;
+            c[k][6] = v1.z;
+            c[k][7] = v1.w;
+        }
+        return;
+    }
+    using CR = CostRing<R>;
+    const unsigned src = cring + (t % kCostSlots) * CR::kSlotBytes + (unsigned)lane * 16u;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4 v0 = lds128(src + (unsigned)(2 * k) * (kWarp * 16));
+        const float4 v1 = lds128(src + (unsigned)(2 * k + 1) * (kWarp * 16));
+        c[k][0] = v0.x;
+        c[k][1] = v0.y;
+        c[k][2] = v0.z;
+        c[k][3] = v0.w;
+        c[k][4] = v1.x;
+        c[k][5] = v1.y;
+        c[k][6] = v1.z;
+        c[k][7] = v1.w;
+    }
+}
+
+// Which rings of a CTA a strip group uses: ring w < NS feeds DP slot w (ring
+// 0 from the reader warp, which has nothing to read in group 0; ring w >= 1
+// from DP slot w-1, when strip w exists); ring NS takes the last DP slot's
+// bottom rows to the writer warp, when a group below needs them.  Producer
+// and consumer of a ring count its uses (in sub-chunks) the same way, which
+// keeps every barrier's phase in step across groups.
+struct GroupRoles {
+    int g, nstrips_here;
+    bool reader, writer;
+};
+template <int NS>
+__device__ __forceinline__ GroupRoles group_roles(const DpArgs& p, int g) {
+    GroupRoles r;
+    r.g = g;
+    r.nstrips_here = min(NS, p.nstrips - g * NS);
+    r.reader = g > 0;
+    r.writer = (g + 1 < p.ngroups) && (g != p.skip_publish);
+    return r;
+}
+template <int NS>
+__device__ __forceinline__ bool ring_used(const GroupRoles& r, int w) {
+    if (w == 0) return r.reader;
+    if (w < NS) return w < r.nstrips_here;
+    return r.writer;
+}
+
+// cur[k] for a runtime k < R without indexing the register array.
+template <int R>
+__device__ __forceinline__ float pick_row(const float* cur, int k) {
+    float v = cur[0];
+#pragma unroll
+    for (int q = 1; q < R; ++q) v = (k == q) ? cur[q] : v;
+    return v;
+}
+
+// DP warp of `strip` (slot w of group g).  ring: the NS + 1 border rings;
+// bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
+// sub-chunk counts of the input and output rings at the start of this
+// group; csub: that of the cost ring.
+template <int R, int NS, bool kRM, bool kSubseq = false>
+__device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
+                                       int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
+                                       unsigned bempty, unsigned rin, unsigned rout,
+                                       unsigned cring, unsigned cfull, unsigned cempty,
+                                       unsigned csub,
+                                       unsigned inf_blk) {
+    constexpr int kRows = 31 * R;
+    const bool ghost = lane == kGhostLane;
+    const int i0 = strip * kRows + lane * R;
+    const int Lb = p.Lb;
+    const bool from_ring = ring_used<NS>(gr, w);
+    const bool to_ring = ring_used<NS>(gr, w + 1);
+    float (*myring)[2][kSub] = ring[w];
+    float (*nextring)[2][kSub] = ring[w + 1];
+    const unsigned bfull_in = bfull + 8 * kRingBlk * w;
+    const unsigned bempty_in = bempty + 8 * kRingBlk * w;
+    const unsigned bfull_out = bfull + 8 * kRingBlk * (w + 1);
+    const unsigned bempty_out = bempty + 8 * kRingBlk * (w + 1);
+    const float mu = p.mu;
+    float w12[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) w12[k] = (ghost && k >= R - 2) ? 0.0f : (kSubseq ? 1.0f : 3.0f);
+    const int srcA = (lane + 31) & 31;
+    const bool is_origin = (i0 == 0) && !ghost;
+    // subsequence DP: the lane and row slot of row La-1, if this strip holds it
+    const int rl = p.La - 1 - strip * kRows;
+    const bool has_last = kSubseq && rl >= 0 && rl < kRows && lane == rl / R;
+    const int kl = kSubseq ? rl - (rl / R) * R : 0;
+    // this strip's sub-chunks, and those its border ring's producer publishes
+    // (the strip above; for the first strip of a group the reader, which
+    // publishes exactly this strip's range)
+    const int2 rg = strip_range(p, strip);
+    const int2 rp = w > 0 ? strip_range(p, strip - 1) : rg;
+    // blocks the strip above published before this strip's first column are
+    // consumed unread, so that the ring's producer and consumer stay in step
+    if (from_ring)
+        for (int n = rp.x; n < rg.x; ++n) {
+            const unsigned ti = rin + (unsigned)(n - rp.x);
+            if (!mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                           p.timeout_ns, 1))
+                return;
+            mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+        }
+
+    // costs of the first sub-chunk
+    float c[R][kSub];
+    if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
+                   p.timeout_ns, 7))
+        return;
+    load_costs<R, kRM>(cring, csub, lane, c);
+    mbar_arrive(bar_at(cempty, csub % kCostSlots));
+
+    float cur[R], prv[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) cur[k] = prv[k] = INFINITY;
+    float ylp = INFINITY;
+    // (no poll of the failure flag in the sweep: every wait checks it on its
+    // slow path, and a warp that never waits ends with its strip)
+    const int jend = min(rg.y * kSub, Lb);
+    for (int j0 = rg.x * kSub; j0 < jend; j0 += kColsPerWord) {
+        uint32_t word[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) word[k] = 0;
+        // the two sub-chunks of a backpointer word: not unrolled (half the
+        // code of the sweep loop; measured 4-5% faster on a long pair)
+#pragma unroll 1
+        for (int h = 0; h < kColsPerWord / kSub; ++h) {
+            const int js = j0 + h * kSub;
+            if (js >= jend) break;
+            const int n = js / kSub;
+            const int nsteps = min(kSub, Lb - js);
+            const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
+            const unsigned t = csub + (unsigned)(n - rg.x);
+
+            // border rows top-2, top-1 of columns js .. js+7 (the group's top
+            // border is +inf in group 0, and so are the columns the strip
+            // above did not sweep: block 0 of ring 0 holds +inf)
+            const bool have_in = from_ring && n < rp.y;
+            if (have_in && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk),
+                                      p.ctl, p.timeout_ns, 1))
+                return;
+            float gv0[kSub], gv1[kSub];
+            {
+                const unsigned s0 = have_in ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk;
+                const float4 a0 = lds128(s0), a1 = lds128(s0 + 16);
+                const float4 b0 = lds128(s0 + 32), b1 = lds128(s0 + 48);
+                gv0[0] = a0.x; gv0[1] = a0.y; gv0[2] = a0.z; gv0[3] = a0.w;
+                gv0[4] = a1.x; gv0[5] = a1.y; gv0[6] = a1.z; gv0[7] = a1.w;
+                gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
+                gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
+            }
+            if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+            // the output blocks must have been read below: the consumer
+            // empties them in order, so once the previous use of block to+3
+            // is consumed so are those of to .. to+2 (one wait per 4 blocks)
+            if (to_ring && ((n - rg.x) & 3) == 0) {
+                const unsigned tl = to + 3u;
+                if (!mbar_wait(bar_at(bempty_out, tl % kRingBlk), use_parity(tl, kRingBlk) ^ 1u,
+                               p.ctl, p.timeout_ns, 2))
+                    return;
+            }
+
+            float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
+            float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
+            (void)ol;
+            float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
+#pragma unroll
+            for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+            const bool has_next = js + kSub < jend;
+            float cn[R][kSub];
+            if (nsteps == kSub) {
+                unsigned ready = 1;
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    // the next sub-chunk's costs: test at step 2, load at step 4
+                    if (u == 2 && has_next)
+                        ready = mbar_test_wait(bar_at(cfull, (t + 1) % kCostSlots),
+                                               use_parity(t + 1, kCostSlots));
+                    if (u == 4 && has_next) {
+                        if (!__all_sync(kFull, ready) &&
+                            !mbar_wait_slow(bar_at(cfull, (t + 1) % kCostSlots),
+                                            use_parity(t + 1, kCostSlots), p.ctl, p.timeout_ns,
+                                            7))
+                            return;
+                        load_costs<R, kRM>(cring, t + 1, lane, cn);
+                        mbar_arrive(bar_at(cempty, (t + 1) % kCostSlots));
+                    }
+                    float cu[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                            is_origin,
+                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+                }
+            } else {
+                // the last, partial sub-chunk (has_next is false)
+#pragma unroll
+                for (int u = 0; u < kSub; ++u) {
+                    if (u >= nsteps) break;
+                    float cu[R];
+#pragma unroll
+                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                            is_origin,
+                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+                }
+            }
+            if constexpr (kSubseq) {
+                if (has_last) {  // row La-1 of these columns
+                    float* dst = p.lastrow + js;
+                    if (nsteps == kSub) {
+                        reinterpret_cast<float4*>(dst)[0] = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                        reinterpret_cast<float4*>(dst)[1] = make_float4(ol[4], ol[5], ol[6], ol[7]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kSub; ++u)
+                            if (u < nsteps) dst[u] = ol[u];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], h);
+            if (to_ring && lane == kOutLane) {
+                const unsigned d0 = smem_u32(&nextring[to % kRingBlk][0][0]);
+                sts128(d0, make_float4(o0[0], o0[1], o0[2], o0[3]));
+                sts128(d0 + 16, make_float4(o0[4], o0[5], o0[6], o0[7]));
+                sts128(d0 + 32, make_float4(o1[0], o1[1], o1[2], o1[3]));
+                sts128(d0 + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
+                mbar_arrive(bar_at(bfull_out, to % kRingBlk));
+            }
+            if (has_next) {
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+#pragma unroll
+                    for (int f = 0; f < kSub; ++f) c[k][f] = cn[k][f];
+            }
+        }
+        store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
+                           (size_t)lane * R,
+                       word);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (!ghost && i0 + k == p.La - 1) *p.e_final = cur[k];
+}
+
+// Reader warp (groups g > 0): the bottom rows of group g-1 from the global
+// border into ring 0.  Lane v < 16 carries value v of every sub-chunk
+// (column v % 8, row v / 8); loads run kAheadSub sub-chunks ahead, and a
+// value whose tag is not yet this call's is re-polled (bounded).
+constexpr int kAheadSub = 4;
+__device__ __forceinline__ void run_reader(const DpArgs& p, int g, int lane, float (*ring0)[2][kSub],
+                                           unsigned bfull0, unsigned bempty0, unsigned rbase,
+                                           int nfirst, int nsub, int clo, int chi) {
+    // blocks nfirst .. nsub-1 (this group's first strip's range); only columns
+    // clo .. chi-1 were published above (the others read as +inf)
+    const int Lb = p.Lb;
+    clo = max(clo, 0);
+    chi = min(chi, Lb);
+    const unsigned long long* gin = p.gborder + (size_t)(g - 1) * Lb * 2;
+    const unsigned epoch = p.epoch;
+    const bool act_lane = lane < 2 * kSub;
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    unsigned long long pend[kAheadSub];
+#pragma unroll
+    for (int q = 0; q < kAheadSub; ++q) {
+        const int col = (nfirst + q) * kSub + cofs;
+        pend[q] = (act_lane && col >= clo && col < chi) ? ldg1(gin + (size_t)col * 2 + row) : 0ull;
+    }
+    for (int n0 = nfirst; n0 < nsub; n0 += kAheadSub) {
+#pragma unroll
+        for (int q = 0; q < kAheadSub; ++q) {
+            const int n = n0 + q;
+            if (n >= nsub) break;
+            const int col = n * kSub + cofs;
+            const bool act = act_lane && col >= clo && col < chi;
+            int ok = !act || tag_of(pend[q]) == epoch;
+            if (!__all_sync(kFull, ok)) {
+                // each poll is a round trip to L2; status and deadline every 16 polls
+                const long long t0 = __shfl_sync(kFull, global_ns(), 0);
+                for (int poll = 1;; ++poll) {
+                    if (!ok) {
+                        pend[q] = ldg1(gin + (size_t)col * 2 + row);
+                        ok = tag_of(pend[q]) == epoch;
+                    }
+                    if (__all_sync(kFull, ok)) break;
+                    if ((poll & 15) == 0) {
+                        if (__shfl_sync(kFull, read_status(p.ctl), 0) != 0) return;
+                        const long long now = __shfl_sync(kFull, global_ns(), 0);
+                        if (now - t0 > p.timeout_ns) {
+                            if (lane == 0) raise_status(p.ctl, DTW_ERR_TIMEOUT, 3);
+                            return;
+                        }
+                    }
+                }
+            }
+            const unsigned t = rbase + (unsigned)(n - nfirst);
+            if (!mbar_wait(bar_at(bempty0, t % kRingBlk), use_parity(t, kRingBlk) ^ 1u, p.ctl,
+                           p.timeout_ns, 8))
+                return;
+            if (act_lane) ring0[t % kRingBlk][row][cofs] = act ? val_of(pend[q]) : INFINITY;
+            mbar_arrive(bar_at(bfull0, t % kRingBlk));
+            const int ncol = col + kAheadSub * kSub;
+            if (act_lane && ncol >= clo && ncol < chi) pend[q] = ldg1(gin + (size_t)ncol * 2 + row);
+        }
+    }
+}
+
+// Writer warp: the last DP slot's bottom rows from ring NS to the global
+// border of group g, as (value, epoch) words; lanes 0..15 store one
+// coalesced 128-byte line per sub-chunk.
+__device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
+                                           float (*ringo)[2][kSub], unsigned bfullo,
+                                           unsigned bemptyo, unsigned rbase, int nfirst,
+                                           int nsub) {
+    const int Lb = p.Lb;
+    unsigned long long* gout = p.gborder + (size_t)g * Lb * 2;
+    const unsigned epoch = p.epoch;
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    for (int n = nfirst; n < nsub; ++n) {
+        const unsigned t = rbase + (unsigned)(n - nfirst);
+        if (!mbar_wait(bar_at(bfullo, t % kRingBlk), use_parity(t, kRingBlk), p.ctl, p.timeout_ns,
+                       9))
+            return;
+        const float v = ringo[t % kRingBlk][row][cofs];
+        mbar_arrive(bar_at(bemptyo, t % kRingBlk));
+        const int col = n * kSub + cofs;
+        if (lane < 2 * kSub && col < Lb) stg1(gout + (size_t)col * 2 + row, pack(v, epoch));
+    }
+}
+
+// NS strips per CTA.  Warps 0..NS-1: the strips' cost warps; NS..2NS-1:
+// their DP warps; 2NS: the reader; 2NS+1: the writer.  Warp w runs on SM
+// sub-partition w % 4, so for NS = 2 each DP warp has a sub-partition of its
+// own and the helpers share those of the cost warps.  Persistent: a CTA
+// takes strip groups from the ticket counter until none are left, so a
+// group only ever waits on groups that started earlier.
+// kMany: the groups come from a work queue over many pairs (`many`, `item0`,
+// `ticket`; see launch_dp_split_many) instead of the pair `one`.
+template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false>
+__global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
+    k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
+               int nmany, int* ticket) {
+    using S = BStage<DP>;
+    using M = SplitSmem<DP, R, kBF>;
+    __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
+    __shared__ __align__(8) unsigned long long bbar[NS][S::kSlots];
+    __shared__ __align__(8) unsigned long long cfull[NS][kCostSlots];
+    __shared__ __align__(8) unsigned long long cempty[NS][kCostSlots];
+    __shared__ __align__(8) unsigned long long bfull[NS + 1][kRingBlk];
+    __shared__ __align__(8) unsigned long long bempty[NS + 1][kRingBlk];
+    __shared__ __align__(16) float s_inf[2][kSub];  // +inf border block, never written after
+    __shared__ int s_group, s_pair;
+    extern __shared__ __align__(128) unsigned char dyn[];  // NS * M::kStripBytes
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
+    const int w = role == 0 ? wid : (role == 1 ? wid - NS : 0);  // strip slot
+    unsigned char* mine = dyn + (size_t)w * M::kStripBytes;
+    const unsigned cring_s = smem_u32(mine + M::kOperandBytes);
+    const unsigned a_s = smem_u32(mine);                                  // kBF: A tile
+    const unsigned b_s = smem_u32(mine + 32 * R * kBfStride * 2);         // kBF: B ring
+    unsigned bbase = 0;  // kBF: lifetime count of this cost warp's B blocks
+    const unsigned cfull_s = smem_u32(&cfull[w][0]);
+    const unsigned cempty_s = smem_u32(&cempty[w][0]);
+
+    BRing<DP> br;
+    br.stage = reinterpret_cast<const float*>(mine);
+    br.stage_s = smem_u32(mine);
+    br.bar_s = smem_u32(&bbar[w][0]);
+    br.base = 0;
+    br.first = 0;
+    br.nblk = 0;
+    br.issued = br.waited = 0;
+    if (threadIdx.x < 2 * kSub) (&s_inf[0][0])[threadIdx.x] = INFINITY;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            for (int k = 0; k < S::kSlots; ++k) mbar_init(smem_u32(&bbar[s][k]), 1);
+            for (int k = 0; k < kCostSlots; ++k) {
+                mbar_init(smem_u32(&cfull[s][k]), kWarp);   // the cost warp's lanes
+                mbar_init(smem_u32(&cempty[s][k]), kWarp);  // the DP warp's lanes
+            }
+        }
+        for (int s = 0; s <= NS; ++s)
+            for (int k = 0; k < kRingBlk; ++k) {
+                // ring 0 is filled by the reader's lanes, the others by lane 30
+                // of the DP warp above; every ring is emptied by a whole warp
+                mbar_init(smem_u32(&bfull[s][k]), s == 0 ? kWarp : 1);
+                mbar_init(smem_u32(&bempty[s][k]), kWarp);
+            }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // Lifetime sub-chunk counts of the cost rings and the border rings.
+    unsigned csub[NS], rsub[NS + 1];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) csub[s] = 0;
+#pragma unroll
+    for (int s = 0; s <= NS; ++s) rsub[s] = 0;
+
+    for (;;) {
+        __syncthreads();  // every warp finished the previous group
+        if (threadIdx.x == 0) {
+            if (kMany) {
+                // item t -> (pair, group): the last pair whose first item is <= t
+                const int t = atomicAdd(ticket, 1);
+                int pi = -1, gi = 0;
+                if (t < item0[nmany]) {
+                    int lo = 0, hi = nmany - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (item0[mid] <= t)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    pi = lo;
+                    gi = t - item0[lo];
+                    if (read_status(many[pi].ctl) != 0) gi = -1;  // the pair has failed
+                }
+                s_pair = pi;
+                s_group = gi;
+            } else {
+                s_pair = 0;
+                s_group =
+                    read_status(one.ctl) != 0 ? one.ngroups : atomicAdd(&one.ctl->ticket, 1);
+            }
+        }
+        // +inf border: the top rows of group 0
+        float* rf = &ring[0][0][0][0];
+        for (int k = threadIdx.x; k < kRing * 2; k += blockDim.x) rf[k] = INFINITY;
+        __syncthreads();
+        if (kMany && s_pair < 0) return;
+        if (kMany && s_group < 0) continue;  // nothing of a failed pair runs
+        const DpArgs p = kMany ? many[s_pair] : one;
+        const int g = s_group;
+        if (g >= p.ngroups) return;
+        const GroupRoles gr = group_roles<NS>(p, g);
+        const int strip = g * NS + w;
+        // the sub-chunk ranges of the group's strips (all columns without a band)
+        int2 rgs[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            rgs[q] = q < gr.nstrips_here ? strip_range(p, g * NS + q) : make_int2(0, 0);
+        if (role == 0) {
+            if (w < gr.nstrips_here)
+            {
+                if constexpr (kBF)
+                    run_cost_bf16<DP, R>(p, strip, lane, a_s, b_s, smem_u32(&bbar[w][0]), bbase,
+                                         cring_s, cfull_s, cempty_s, csub[w]);
+                else
+                    run_cost<DP, R>(p, strip, lane, cring_s, cfull_s, cempty_s, csub[w], br);
+            }
+        } else if (role == 1) {
+            if (w < gr.nstrips_here)
+                run_dp<R, NS, kBF, kSubseq>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                                   smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
+                                   cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]));
+        } else if (role == 2) {
+            if (gr.reader) {
+                // the first strip's blocks; the strip above (last of the group
+                // above) published its own range's columns
+                const int2 above = strip_range(p, g * NS - 1);
+                run_reader(p, g, lane, ring[0], smem_u32(&bfull[0][0]), smem_u32(&bempty[0][0]),
+                           rsub[0], rgs[0].x, rgs[0].y, above.x * kSub, above.y * kSub);
+            }
+        } else {
+            if (gr.writer)
+                run_writer(p, g, lane, ring[NS], smem_u32(&bfull[NS][0]),
+                           smem_u32(&bempty[NS][0]), rsub[NS], rgs[NS - 1].x, rgs[NS - 1].y);
+        }
+        // ring uses of this group, in blocks of 8 columns: a cost ring the
+        // strip's range; ring 0 the first strip's range; ring w (1 <= w < NS)
+        // and ring NS the range of the strip that fills them
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            if (q < gr.nstrips_here) csub[q] += (unsigned)(rgs[q].y - rgs[q].x);
+        if (ring_used<NS>(gr, 0)) rsub[0] += (unsigned)(rgs[0].y - rgs[0].x);
+#pragma unroll
+        for (int q = 1; q <= NS; ++q)
+            if (ring_used<NS>(gr, q)) rsub[q] += (unsigned)(rgs[q - 1].y - rgs[q - 1].x);
+    }
+}
+
+template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = false>
+cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
+                     int* ticket, int num_sms, cudaStream_t s) {
+    constexpr int kThreads = (2 * NS + 2) * 32;
+    const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
+    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq>;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int grid = blocks_per_sm * num_sms;
+    if (grid > items) grid = items;
+    kern<<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace pardtw

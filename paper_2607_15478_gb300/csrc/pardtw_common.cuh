@@ -118,14 +118,18 @@ cudaError_t launch_dp(const DpArgs& a, int dp, int num_sms, cudaStream_t s);    
 cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
 // Rows per lane the fused DP supports for a padded dimension (0 = none).
 bool multirow_supported(int dp, int R);
-// Warp-specialised DP (dp_split.cu): a cost warp and a DP warp per strip,
-// kSplitStrips strips per CTA; R = 2, 3 or 4.
-cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int num_sms, cudaStream_t s);
+// Warp-specialised DP (dp_split.cu, dp_split4.cu): a cost warp and a DP warp
+// per strip, ns = 2 or 4 strips per CTA; R = 2, 3 or 4 rows per lane.
+cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int ns, int num_sms, cudaStream_t s);
+bool split4_supported(int dp, int R);
+cudaError_t launch_dp_split4(const DpArgs& a, const DpArgs* many, const int* item0, int n,
+                             int items, int* ticket, int dp, int R, int num_sms, cudaStream_t s);
 // The subsequence DP of WSDTW over a batch (R = 3, dp <= 32): weights 1, 1, 2,
 // free start in row 0, row La-1 of every pair into its DpArgs::lastrow.
 cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, int total_items,
                                   int* ticket, int dp, int num_sms, cudaStream_t s);
-bool split_supported(int dp, int R);
+// ns strips per CTA: 2 (every dp <= 32) or 4 (dp <= 16, R = 2, 3).
+bool split_supported(int dp, int R, int ns = 2);
 // The same DP with the cost from BF16 features and FP32 accumulation on the
 // tensor cores (mma.sync m16n8k16): D padded to 64 or 128, R = 3.
 cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s);
@@ -140,7 +144,7 @@ cudaError_t launch_pack_b_bf16(const float* B, int Lb, int Lb_pad, int D, void* 
 // groups of its own pair that were taken earlier.  Each pair's failures stay
 // in its own control block.
 cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, int total_items,
-                                 int* ticket, int dp, int R, int num_sms, cudaStream_t s);
+                                 int* ticket, int dp, int R, int ns, int num_sms, cudaStream_t s);
 
 // Which DP kernel runs a problem: kind 0 = one row per lane (dp_kernel.cu),
 // 1 = fused multi-row (dp_multirow.cu), 2 = cost/DP warp pairs (dp_split.cu);

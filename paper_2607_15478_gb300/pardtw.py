@@ -58,7 +58,8 @@ class PardtwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("cost_precision", ctypes.c_int), ("cost_shift", ctypes.c_float),
                 ("wait_limit", ctypes.c_int), ("debug_skip_publish", ctypes.c_int),
-                ("rows_per_lane", ctypes.c_int), ("dp_schedule", ctypes.c_int)]
+                ("rows_per_lane", ctypes.c_int), ("dp_schedule", ctypes.c_int),
+                ("strips_per_cta", ctypes.c_int)]
 
 SCHEDULE_AUTO, SCHEDULE_FUSED, SCHEDULE_SPLIT = 0, 1, 2
 
@@ -111,7 +112,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dtw_batch_create.argtypes = [vp, ci, vp, vp, vp, vp, ci, vp, vp, vp, vp, ci,
                                      ctypes.POINTER(vp)]
     lib.dtw_batch_run.argtypes = [vp]
-    lib.dtw_batch_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(cf)]
+    lib.dtw_batch_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(cf)]
     lib.dtw_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("dtw_default_options", "dtw_status_string", "dtw_static_scratch_bytes",
@@ -127,7 +128,8 @@ def status_string(status: int) -> str:
 
 def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
                  debug_skip_publish: int = -1, rows_per_lane: int = 0,
-                 dp_schedule: int = SCHEDULE_AUTO, cost_precision: int = DTW_COST_FP32) -> Options:
+                 dp_schedule: int = SCHEDULE_AUTO, cost_precision: int = DTW_COST_FP32,
+                 strips_per_cta: int = 0) -> Options:
     o = Options()
     load_library().dtw_default_options(ctypes.byref(o))
     o.cost_precision = int(cost_precision)
@@ -136,6 +138,7 @@ def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
     o.debug_skip_publish = int(debug_skip_publish)
     o.rows_per_lane = int(rows_per_lane)
     o.dp_schedule = int(dp_schedule)
+    o.strips_per_cta = int(strips_per_cta)
     return o
 
 
@@ -357,11 +360,13 @@ class BatchPlan:
         _check(load_library().dtw_batch_run(self.b), "dtw_batch_run")
 
     def info(self):
-        """(rows per lane chosen, autotuner times in ms for 2, 3, 4 rows per lane)."""
-        R = ctypes.c_int(0)
-        t = (ctypes.c_float * 3)()
-        _check(load_library().dtw_batch_info(self.b, ctypes.byref(R), t), "dtw_batch_info")
-        return R.value, [float(x) for x in t]
+        """(rows per lane, strips per CTA, autotuner times in ms: 2, 3, 4 rows per
+        lane with two strips per CTA, then with four; -1 where not tried)."""
+        R, NS = ctypes.c_int(0), ctypes.c_int(0)
+        t = (ctypes.c_float * 6)()
+        _check(load_library().dtw_batch_info(self.b, ctypes.byref(R), ctypes.byref(NS), t),
+               "dtw_batch_info")
+        return R.value, NS.value, [float(x) for x in t]
 
     def results(self):
         """(list of paths, costs, path lengths) of the last run (synchronises)."""
@@ -394,6 +399,8 @@ class Aligner:
         self.h = dtw_create(device, stream)
 
     def close(self):
+        for plan in list(getattr(self, "_plans", ())):
+            plan.close()
         if getattr(self, "h", None):
             dtw_destroy(self.h)
             self.h = None
@@ -538,10 +545,15 @@ class Aligner:
         return c
 
     def plan_batch(self, As: List, Bs: List, autotune: bool = True) -> "BatchPlan":
-        """A graph-captured, autotuned plan of this batch (runs on this handle's stream)."""
+        """A graph-captured, autotuned plan of this batch (runs on this handle's
+        stream; closed with this Aligner at the latest)."""
+        import weakref
         self._enter()
         plan = BatchPlan(self.h, As, Bs, autotune)
         self._leave()
+        if not hasattr(self, "_plans"):
+            self._plans = weakref.WeakSet()
+        self._plans.add(plan)
         return plan
 
     def align_many(self, As: List, Bs: List, **opts):

@@ -75,17 +75,21 @@ def test_batch_of_one_and_tiny_pairs(aligner):
             assert_oracle(p.A, p.B, paths[k], float(costs[k]))
 
 
-def test_batch_failure_stays_with_its_pair(aligner):
+@pytest.mark.parametrize("ns", [2, 4])
+def test_batch_failure_stays_with_its_pair(aligner, ns):
     # group 0 of every pair never publishes its border: pairs with more than
-    # one strip group (La > 186 rows at 3 rows per lane) time out after ~20 ms,
-    # single-group pairs are unaffected, and the handle keeps working
+    # one strip group (La > ns x 93 rows at 3 rows per lane) time out after
+    # ~20 ms, single-group pairs are unaffected, and the handle keeps working
     from paper_2607_15478_gb300 import pardtw
-    pairs = uneven_pairs(91, 12, 60, 700)
+    pairs = uneven_pairs(91, 12, 60, 900)
     As = [dev(p.A) for p in pairs]
     Bs = [dev(p.B) for p in pairs]
-    paths, costs, st = aligner.align_many(As, Bs, wait_limit_us=20000, debug_skip_publish=0)
+    paths, costs, st = aligner.align_many(As, Bs, wait_limit_us=20000, debug_skip_publish=0,
+                                          strips_per_cta=ns)
+    assert any(p.A.shape[0] > ns * 93 for p in pairs)
+    assert any(p.A.shape[0] <= ns * 93 for p in pairs)
     for k, p in enumerate(pairs):
-        if p.A.shape[0] > 186:
+        if p.A.shape[0] > ns * 93:
             assert st[k] == pardtw.DTW_ERR_TIMEOUT, (k, st[k])
         else:
             assert st[k] == 0
@@ -120,8 +124,9 @@ def test_planned_batch_equals_align_many_and_replays(aligner):
     ref_paths, ref_costs, st = aligner.align_many(As, Bs)
     assert (st == 0).all()
     plan = aligner.plan_batch(As, Bs, autotune=True)
-    R, tuned = plan.info()
-    assert R in (2, 3, 4) and tuned[R - 2] > 0
+    R, NS, tuned = plan.info()
+    assert R in (2, 3, 4) and NS in (2, 4) and tuned[(3 if NS == 4 else 0) + R - 2] > 0
+    assert sum(t > 0 for t in tuned) == 5  # R 2, 3, 4 at two strips; R 2, 3 at four
     for rep in range(3):
         if rep:
             plan.run()
@@ -149,8 +154,10 @@ def test_planned_batch_without_autotune(aligner):
     As = [dev(p.A) for p in pairs]
     Bs = [dev(p.B) for p in pairs]
     plan = aligner.plan_batch(As, Bs, autotune=False)
-    R, tuned = plan.info()
-    assert R == 3 and tuned[0] == -1.0 and tuned[2] == -1.0
+    R, NS, tuned = plan.info()
+    # no autotuning: the default schedule only (3 rows per lane, four strips per CTA)
+    assert R == 3 and NS == 4 and tuned[4] > 0
+    assert all(t == -1.0 for k, t in enumerate(tuned) if k != 4)
     paths, costs, lens = plan.results()
     for k, p in enumerate(pairs):
         assert_oracle(p.A, p.B, paths[k], float(costs[k]))

@@ -224,13 +224,16 @@ def test_align_many_matches_single(aligner):
         assert_parity(p.A, p.B, paths[idx], float(costs[idx]))
 
 
-# (rows per lane, schedule): one row per lane; the fused multi-row kernel;
-# the cost/DP warp pairs
-DECOMPOSITIONS = [(1, 0), (2, 1), (4, 1), (2, 2), (3, 2), (4, 2)]
+# (rows per lane, schedule, strips per CTA): one row per lane; the fused
+# multi-row kernel; the cost/DP warp pairs with two and four strips per CTA
+DECOMPOSITIONS = [(1, 0, 0), (2, 1, 0), (4, 1, 0), (2, 2, 2), (3, 2, 2), (4, 2, 2), (2, 2, 4),
+                  (3, 2, 4)]
 
 
 @pytest.mark.parametrize("La,Lb", [(61, 70), (62, 100), (63, 64), (92, 120), (93, 93),
                                    (94, 150), (124, 150), (125, 200), (186, 250), (187, 190),
+                                   (247, 300), (248, 250), (249, 400), (371, 400), (372, 380),
+                                   (373, 500), (744, 800), (745, 900),
                                    (500, 620), (1000, 1200), (3001, 2500)])
 def test_rows_per_lane_decompositions_agree(aligner, La, Lb):
     # the row decomposition and the division of labour between warps only
@@ -240,14 +243,16 @@ def test_rows_per_lane_decompositions_agree(aligner, La, Lb):
     wp = synth.warped_pair(synth.rng_for(55, La + Lb), La, Lb, 12, knots=4, tmin=0.5, tmax=2.0)
     A, B = dev(wp.A), dev(wp.B)
     ref = None
-    for R, sched in DECOMPOSITIONS:
-        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched)
+    for R, sched, ns in DECOMPOSITIONS:
+        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched,
+                                    strips_per_cta=ns)
         if ref is None:
             ref = (path.cpu().numpy(), total)
             assert_parity(wp.A, wp.B, path, total)
         else:
-            np.testing.assert_array_equal(path.cpu().numpy(), ref[0], err_msg=f"R={R} s={sched}")
-            assert total == ref[1], (R, sched)
+            np.testing.assert_array_equal(path.cpu().numpy(), ref[0],
+                                          err_msg=f"R={R} s={sched} ns={ns}")
+            assert total == ref[1], (R, sched, ns)
 
 
 @pytest.mark.parametrize("D", [4, 8, 16, 32])
@@ -255,10 +260,11 @@ def test_decompositions_agree_feature_dims(aligner, D):
     wp = synth.warped_pair(synth.rng_for(56, D), 400, 450, D, knots=4, tmin=0.5, tmax=2.0)
     A, B = dev(wp.A), dev(wp.B)
     ref = None
-    for R, sched in DECOMPOSITIONS:
+    for R, sched, ns in DECOMPOSITIONS:
         if R == 4 and D > 16:
             continue
-        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched)
+        path, total = aligner.align(A, B, rows_per_lane=R, dp_schedule=sched,
+                                    strips_per_cta=ns)
         if ref is None:
             ref = (path.cpu().numpy(), total)
             assert_parity(wp.A, wp.B, path, total)
@@ -267,12 +273,13 @@ def test_decompositions_agree_feature_dims(aligner, D):
             assert total == ref[1], (R, sched)
 
 
-@pytest.mark.parametrize("R,sched", DECOMPOSITIONS)
-def test_exact_ties_every_decomposition(aligner, R, sched):
+@pytest.mark.parametrize("R,sched,ns", DECOMPOSITIONS)
+def test_exact_ties_every_decomposition(aligner, R, sched, ns):
     rng = np.random.default_rng(77)
     A = np.eye(3, dtype=np.float32)[rng.integers(0, 3, 700)]
     B = np.eye(3, dtype=np.float32)[rng.integers(0, 3, 900)]
-    path, total = aligner.align(dev(A), dev(B), rows_per_lane=R, dp_schedule=sched)
+    path, total = aligner.align(dev(A), dev(B), rows_per_lane=R, dp_schedule=sched,
+                                strips_per_cta=ns)
     po, to = oracle.dtw(A, B)
     assert total == to
     np.testing.assert_array_equal(path.cpu().numpy(), po)
