@@ -95,7 +95,19 @@ typedef struct dtw_options {
      * the four-strip form for D and rows_per_lane, else two), 2 or 4 (D <= 16,
      * rows_per_lane 2 or 3; else two).  Results do not depend on it. */
     int strips_per_cta;
+    /* DTW_TRANSPOSE_AUTO (0, default): the DP sweeps the transposed pair
+     * (B's frames as rows) when a model of the sweep's time (waves of strip
+     * groups x columns + the chain of strips) says it is faster, e.g. a pair
+     * with B longer that fits one wave of strip groups; DTW_TRANSPOSE_NEVER
+     * (1); DTW_TRANSPOSE_ALWAYS (2).
+     * Applies to the default warp-pair DP at 3 rows per lane (FP32 or BF16
+     * cost); the tie order is mapped so that results do not depend on it. */
+    int transpose;
 } dtw_options;
+
+#define DTW_TRANSPOSE_AUTO 0
+#define DTW_TRANSPOSE_NEVER 1
+#define DTW_TRANSPOSE_ALWAYS 2
 
 #define DTW_SCHEDULE_AUTO 0
 #define DTW_SCHEDULE_FUSED 1

@@ -121,15 +121,44 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
 }
 
 cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool transposed) {
+    if (transposed && (plan.kind != 2 || plan.R != 3)) return cudaErrorInvalidValue;
     switch (plan.kind) {
         case 0: return launch_dp(a, dp, num_sms, s);
         case 1: return launch_dp_multirow(a, dp, plan.R, num_sms, s);
         case 2:
-            return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s)
-                             : launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s);
+            return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s, transposed)
+                             : launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s, transposed);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Which way to sweep a pair.  The persistent warp-pair DP runs its strip
+// groups in waves of one group per SM: a CTA sweeps all columns of a group
+// before it takes the next, and the next group in the chain starts a few
+// blocks behind the one above.  So the time is about
+//   ceil(groups / SMs) x columns  +  strips x (lag of one strip, ~18 columns)
+// column steps; the transposed sweep (B's frames as rows) wins when that is
+// smaller for (Lb rows, La columns), e.g. a pair that fits one wave with B
+// longer: its chain then runs over La columns instead of Lb.  Only the
+// warp-pair DP at 3 rows per lane has the transposed tie order.
+namespace {
+double sweep_estimate(int rows, int cols, int dp, const dtw_options& o, int num_sms) {
+    const DpPlan p = choose_plan(rows, dp, o, num_sms);
+    const int rps = strip_rows(p.R);
+    const long long strips = (rows + rps - 1) / rps;
+    const long long groups = (strips + p.spg - 1) / p.spg;
+    const long long waves = num_sms > 0 ? (groups + num_sms - 1) / num_sms : 1;
+    return (double)waves * cols + 18.0 * (double)strips;
+}
+}  // namespace
+
+bool pardtw::transpose_pair(int La, int Lb, int dp, const dtw_options& o, int num_sms) {
+    if (o.transpose == DTW_TRANSPOSE_NEVER) return false;
+    const DpPlan pt = choose_plan(Lb, dp, o, num_sms);  // the plan the transposed pair gets
+    if (pt.kind != 2 || pt.R != 3) return false;
+    if (o.transpose == DTW_TRANSPOSE_ALWAYS) return true;
+    return sweep_estimate(Lb, La, dp, o, num_sms) < sweep_estimate(La, Lb, dp, o, num_sms);
 }
 
 namespace {
@@ -218,6 +247,7 @@ dtw_options defaults() {
     o.rows_per_lane = 0;
     o.dp_schedule = DTW_SCHEDULE_AUTO;
     o.strips_per_cta = 0;
+    o.transpose = DTW_TRANSPOSE_AUTO;
     return o;
 }
 
@@ -225,7 +255,15 @@ dtw_options defaults() {
 // `out_len`, `out_total` are device pointers (out_total may be null).
 int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
                  const dtw_options& o, int32_t* out_path, int* out_len, float* out_total,
-                 const int2* ranges = nullptr) {
+                 const int2* ranges = nullptr, int transpose = -1) {
+    // transpose < 0: decide here; a band's ranges come with the caller's
+    // decision (they are per strip of the swept rows)
+    const bool tr = transpose >= 0 ? transpose != 0
+                                   : transpose_pair(La, Lb, padded_dim(D), o, h->num_sms);
+    if (tr) {
+        std::swap(A, B);
+        std::swap(La, Lb);
+    }
     // a band (per-strip column ranges) needs the warp-pair kernel at 3 rows
     // per lane, FP32 cost
     const DpPlan plan = ranges ? DpPlan{2, 3, kSplitStrips}
@@ -283,7 +321,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     if (a.epoch == 0) a.epoch = ++h->epoch;
     a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
     a.skip_publish = o.debug_skip_publish;
-    CU(launch_plan(L.plan, a, L.dp, h->num_sms, s));
+    CU(launch_plan(L.plan, a, L.dp, h->num_sms, s, tr));
     if (h->timing) CU(cudaEventRecord(h->ev[2], s));
     BtArgs bt;
     bt.bp = bp;
@@ -300,6 +338,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     bt.total = out_total;
     bt.scratch = ws + L.off_bt;
     bt.ranges = ranges;
+    bt.transposed = tr ? 1 : 0;
     CU(launch_backtrace_bands(bt, s));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
@@ -864,11 +903,21 @@ BandBuf band_buf(int Lac, int Lbc, int D, int nstrips, bool pooled) {
 // DP when the banded path meets a side of the band.
 int band_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
                const dtw_options& o, int ds, const float* cA, int Lac, const float* cB, int Lbc,
-               int Dc, int w, const float* wrow, const BandBuf& bb, int32_t* path, int* path_len,
-               float* total_cost, int* fell_back) {
+               int Dc, int w, const float* wrowA, const float* wrowB, const BandBuf& bb,
+               int32_t* path, int* path_len, float* total_cost, int* fell_back) {
     cudaStream_t s = h->stream;
     const int rps = strip_rows(3);
-    const int nstrips = (La + rps - 1) / rps;
+    // the fine DP may sweep the transposed pair (B's frames as rows): the
+    // strips, their ranges and the band test are then over B.  A band is one
+    // chain of strips over all columns whatever its size, so the sweep runs
+    // over the shorter sequence's frames
+    dtw_options ob = o;
+    if (ob.transpose == DTW_TRANSPOSE_AUTO)
+        ob.transpose = Lb > La ? DTW_TRANSPOSE_ALWAYS : DTW_TRANSPOSE_NEVER;
+    const bool tr = transpose_pair(La, Lb, padded_dim(D), ob, h->num_sms);
+    const int Lr = tr ? Lb : La, Lc = tr ? La : Lb, Lrc = tr ? Lbc : Lac;
+    const float* wrow = tr ? wrowB : wrowA;
+    const int nstrips = (Lr + rps - 1) / rps;
     int32_t* cpath = reinterpret_cast<int32_t*>(h->band + bb.cp);
     int* clen = reinterpret_cast<int*>(h->band + bb.cl);
     int2* ranges = reinterpret_cast<int2*>(h->band + bb.rg);
@@ -878,14 +927,16 @@ int band_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, in
     oc.dp_schedule = DTW_SCHEDULE_AUTO;
     int rc = align_device(h, cA, Lac, cB, Lbc, Dc, oc, cpath, clen, nullptr);
     if (rc != DTW_OK) return rc;
-    CU(launch_band_ranges(cpath, clen, ds, w, wrow, Lac, La, Lb, nstrips, rps, ranges, s));
+    CU(launch_band_ranges(cpath, clen, ds, w, wrow, Lrc, Lr, Lc, nstrips, rps, tr ? 1 : 0,
+                          ranges, s));
     h->band_nstrips = nstrips;
     h->band_rps = rps;
-    h->band_Lb = Lb;
+    h->band_Lb = Lc;
     h->band_ranges = ranges;
-    rc = align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost, ranges);
+    rc = align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost, ranges, tr ? 1 : 0);
     if (rc != DTW_OK) return rc;
-    CU(launch_band_touch(path, path_len, std::min(La, Lb), Lb, rps, ranges, touch, s));
+    CU(launch_band_touch(path, path_len, std::min(La, Lb), Lc, rps, ranges, tr ? 1 : 0, touch,
+                         s));
     CU(cudaMemcpyAsync(h->h_small + 2, touch, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (h->h_small[2]) {
@@ -1020,7 +1071,7 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
         if (fell_back) *fell_back = 1;
         return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
     }
-    const int nstrips = (La + strip_rows(3) - 1) / strip_rows(3);
+    const int nstrips = (std::max(La, Lb) + strip_rows(3) - 1) / strip_rows(3);
     const BandBuf bb = band_buf(Lac, Lbc, D, nstrips, true);
     rc = grow(h, &h->band, &h->band_cap, bb.total);
     if (rc != DTW_OK) return rc;
@@ -1029,7 +1080,7 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
     CU(launch_pool(A, La, D, downsample, pa, h->stream));
     CU(launch_pool(B, Lb, D, downsample, pb, h->stream));
     return band_align(h, A, La, B, Lb, D, o, downsample, pa, Lac, pb, Lbc, D, halfwidth, nullptr,
-                      bb, path, path_len, total_cost, fell_back);
+                      nullptr, bb, path, path_len, total_cost, fell_back);
 }
 
 size_t dtw_encoder_param_count(int D) {
@@ -1144,7 +1195,7 @@ int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int
     const EncBuf eb = enc_buf(Lac, Lbc, D);
     rc = grow(h, &h->enc, &h->enc_cap, eb.total);
     if (rc != DTW_OK) return rc;
-    const int nstrips = (La + strip_rows(3) - 1) / strip_rows(3);
+    const int nstrips = (std::max(La, Lb) + strip_rows(3) - 1) / strip_rows(3);
     const BandBuf bb = band_buf(Lac, Lbc, kEncEmbed, nstrips, false);
     rc = grow(h, &h->band, &h->band_cap, bb.total);
     if (rc != DTW_OK) return rc;
@@ -1153,7 +1204,8 @@ int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int
     if (rc == DTW_OK) rc = enc_forward(h, params, pl, D, B, Lb, downsample, bf16 != 0, eb.b);
     if (rc != DTW_OK) return rc;
     return band_align(h, A, La, B, Lb, D, o, downsample, ef(h, eb.a.E), Lac, ef(h, eb.b.E), Lbc,
-                      kEncEmbed, 0, ef(h, eb.a.HW), bb, path, path_len, total_cost, fell_back);
+                      kEncEmbed, 0, ef(h, eb.a.HW), ef(h, eb.b.HW), bb, path, path_len,
+                      total_cost, fell_back);
 }
 
 int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, int nfrag,

@@ -32,9 +32,14 @@ __global__ void k_pool(const float* __restrict__ X, int L, int D, int ds, float*
 }
 
 // One thread per strip (k_band_monotone then widens the ranges to monotone).
+// swap: the fine DP sweeps the transposed pair, so a strip's rows are frames
+// of B: the coarse path's entries are read as (column, row).  La, Lb, Lac are
+// the swept pair's (rows, columns, coarse rows).
 __global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __restrict__ clen,
                               int ds, int w, const float* __restrict__ wrow, int Lac, int La,
-                              int Lb, int nstrips, int rps, int2* __restrict__ ranges) {
+                              int Lb, int nstrips, int rps, int swap,
+                              int2* __restrict__ ranges) {
+    const int ri = swap ? 1 : 0, ci = 1 - ri;
     const int n = *clen;
     const int nsub = (Lb + 7) / 8;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,15 +54,15 @@ __global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __re
         int lo = 0, hi = n;  // first path entry with row >= icl
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (cpath[2 * mid] < icl)
+            if (cpath[2 * mid + ri] < icl)
                 lo = mid + 1;
             else
                 hi = mid;
         }
         int jmin = 0x7fffffff, jmax = -1;
-        for (int k = lo; k < n && cpath[2 * k] <= ich; ++k) {
-            jmin = min(jmin, cpath[2 * k + 1]);
-            jmax = max(jmax, cpath[2 * k + 1]);
+        for (int k = lo; k < n && cpath[2 * k + ri] <= ich; ++k) {
+            jmin = min(jmin, cpath[2 * k + ci]);
+            jmax = max(jmax, cpath[2 * k + ci]);
         }
         if (jmax < 0) {  // cannot happen for a path covering every coarse row
             jmin = 0;
@@ -87,13 +92,14 @@ __global__ void k_band_monotone(int nstrips, int2* __restrict__ ranges) {
 }
 
 __global__ void k_band_touch(const int32_t* __restrict__ path, const int* __restrict__ plen,
-                             int Lb, int rps, const int2* __restrict__ ranges,
+                             int Lb, int rps, const int2* __restrict__ ranges, int swap,
                              int* __restrict__ touch) {
     const int n = *plen;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0 && n <= 0) atomicOr(touch, 1);  // no path inside the band
     if (k >= n) return;
-    const int i = path[2 * k], j = path[2 * k + 1];
+    // (row, column) of the swept pair (the path is always the problem's (i, j))
+    const int i = path[2 * k + (swap ? 1 : 0)], j = path[2 * k + (swap ? 0 : 1)];
     const int2 r = ranges[i / rps];
     const int x8 = r.x * 8, y8 = min(r.y * 8, Lb);
     if ((x8 > 0 && j < x8 + 8) || (y8 < Lb && j >= y8 - 8)) atomicOr(touch, 1);
@@ -109,20 +115,20 @@ cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStre
 
 cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w,
                                const float* wrow, int Lac, int La, int Lb, int nstrips, int rps,
-                               int2* ranges, cudaStream_t s) {
+                               int swap, int2* ranges, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (nstrips + threads - 1) / threads;
     k_band_ranges<<<blocks, threads, 0, s>>>(cpath, clen, ds, w, wrow, Lac, La, Lb, nstrips, rps,
-                                             ranges);
+                                             swap, ranges);
     k_band_monotone<<<1, 32, 0, s>>>(nstrips, ranges);
     return cudaGetLastError();
 }
 
 cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
-                              const int2* ranges, int* touch, cudaStream_t s) {
+                              const int2* ranges, int swap, int* touch, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(touch, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_band_touch<<<(cap + 255) / 256, 256, 0, s>>>(path, plen, Lb, rps, ranges, touch);
+    k_band_touch<<<(cap + 255) / 256, 256, 0, s>>>(path, plen, Lb, rps, ranges, swap, touch);
     return cudaGetLastError();
 }
 

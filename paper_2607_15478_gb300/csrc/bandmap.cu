@@ -362,8 +362,8 @@ __global__ void k_bt_emit(const BtArgs one, const BtArgs* __restrict__ many) {
         const int base = s_off[b];
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int2 c = seg[(size_t)b * band + (n - 1 - k)];
-            path[2 * (base + k)] = c.x;
-            path[2 * (base + k) + 1] = c.y;
+            path[2 * (base + k)] = a.transposed ? c.y : c.x;
+            path[2 * (base + k) + 1] = a.transposed ? c.x : c.y;
         }
     }
 }

@@ -355,7 +355,12 @@ __device__ __forceinline__ float eq_as_float(float a, float b) {
 // select instruction.
 // kSubseq: the subsequence DTW of WSDTW (Sec. II-C), weights 1, 1, 2 for
 // (1,1), (1,2), (2,1) instead of 2, 3, 3 (w12 carries the (1,2) weight).
-template <int R, bool kSubseq = false>
+// kT: the pair is swept transposed (rows of the kernel = frames of B), so
+// the kernel's (1,2) candidate is the problem's (2,1) and vice versa; the
+// problem's tie order (1,1), (1,2), (2,1) is then the kernel's c0, c2, c1,
+// and the field keeps the kernel's decoding: bit 1 only when c1 attains the
+// minimum and c2 does not.  Same cells, same values, same path.
+template <int R, bool kSubseq = false, bool kT = false>
 __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, const float* w12,
                                         bool ghost, float g0, float g1, bool origin_here,
                                         float mu, float* cur, float* prv, float& ylp, float* fw,
@@ -377,7 +382,12 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
         const float c2 = fmaf(w21, cost[k], x2);     // from (i-2, j-1)
         float mk = min3f(c0, c1, c2);
         fw[k] = fmaf(eq_as_float(c0, mk), bit0, fw[k]);
-        fw[k] = fmaf(eq_as_float(c1, mk), bit1, fw[k]);
+        if constexpr (kT) {
+            const float e1 = eq_as_float(c1, mk);
+            fw[k] = fmaf(fmaf(-e1, eq_as_float(c2, mk), e1), bit1, fw[k]);
+        } else {
+            fw[k] = fmaf(eq_as_float(c1, mk), bit1, fw[k]);
+        }
         if (k == 0) mk = origin_here ? cost[0] + mu : mk;  // E[0][0] = C[0][0]
         m[k] = mk;
     }

@@ -41,9 +41,21 @@ bool split_supported(int dp, int R, int ns) {
     return false;
 }
 
-cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int ns, int num_sms, cudaStream_t s) {
+cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int ns, int num_sms, cudaStream_t s,
+                            bool transposed) {
     if (ns == 4) return launch_dp_split4(a, nullptr, nullptr, 1, a.ngroups, nullptr, dp, R,
-                                         num_sms, s);
+                                         num_sms, s, transposed);
+    if (transposed) {
+        if (R != 3) return cudaErrorInvalidValue;
+        switch (dp) {
+            case 4: return launch_t<4, 3, 2, false, false, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s);
+            case 8: return launch_t<8, 3, 2, false, false, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s);
+            case 12: return launch_t<12, 3, 2, false, false, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s);
+            case 16: return launch_t<16, 3, 2, false, false, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s);
+            case 32: return launch_t<32, 3, 2, false, false, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     return launch_any2<false>(a, nullptr, nullptr, 1, a.ngroups, nullptr, dp, R, num_sms, s);
 }
 
@@ -51,7 +63,7 @@ cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, in
                                  int* ticket, int dp, int R, int ns, int num_sms, cudaStream_t s) {
     if (n <= 0 || total_items <= 0) return cudaSuccess;
     if (ns == 4) return launch_dp_split4(DpArgs{}, many, item0, n, total_items, ticket, dp, R,
-                                         num_sms, s);
+                                         num_sms, s, false);
     return launch_any2<true>(DpArgs{}, many, item0, n, total_items, ticket, dp, R, num_sms, s);
 }
 
@@ -71,13 +83,18 @@ cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, i
 
 bool split_bf16_supported(int dp) { return dp == 64 || dp == 128; }
 
-cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s) {
+cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s,
+                                 bool transposed) {
     if (dp == 64)
-        return launch_t<64, 3, 2, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr,
-                                               num_sms, s);
+        return transposed ? launch_t<64, 3, 2, false, true, false, true>(
+                                a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s)
+                          : launch_t<64, 3, 2, false, true>(a, nullptr, nullptr, 1, a.ngroups,
+                                                            nullptr, num_sms, s);
     if (dp == 128)
-        return launch_t<128, 3, 2, false, true>(a, nullptr, nullptr, 1, a.ngroups, nullptr,
-                                                num_sms, s);
+        return transposed ? launch_t<128, 3, 2, false, true, false, true>(
+                                a, nullptr, nullptr, 1, a.ngroups, nullptr, num_sms, s)
+                          : launch_t<128, 3, 2, false, true>(a, nullptr, nullptr, 1, a.ngroups,
+                                                             nullptr, num_sms, s);
     return cudaErrorInvalidValue;
 }
 

@@ -421,7 +421,7 @@ __device__ __forceinline__ float pick_row(const float* cur, int k) {
 // bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
 // sub-chunk counts of the input and output rings at the start of this
 // group; csub: that of the cost ring.
-template <int R, int NS, bool kRM, bool kSubseq = false>
+template <int R, int NS, bool kRM, bool kSubseq = false, bool kT = false>
 __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
@@ -552,7 +552,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                    dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
                                         (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
                                             is_origin,
                                         mu, cur, prv, ylp, fw, o0[u], o1[u]);
@@ -566,7 +566,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R, kSubseq>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                    dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
                                         (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
                                             is_origin,
                                         mu, cur, prv, ylp, fw, o0[u], o1[u]);
@@ -705,7 +705,7 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
 // group only ever waits on groups that started earlier.
 // kMany: the groups come from a work queue over many pairs (`many`, `item0`,
 // `ticket`; see launch_dp_split_many) instead of the pair `one`.
-template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false>
+template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false, bool kT = false>
 __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
                int nmany, int* ticket) {
@@ -819,7 +819,7 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
             }
         } else if (role == 1) {
             if (w < gr.nstrips_here)
-                run_dp<R, NS, kBF, kSubseq>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                run_dp<R, NS, kBF, kSubseq, kT>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
                                    smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
                                    cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]));
         } else if (role == 2) {
@@ -848,12 +848,13 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
     }
 }
 
-template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = false>
+template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = false,
+          bool kT = false>
 cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
                      int* ticket, int num_sms, cudaStream_t s) {
     constexpr int kThreads = (2 * NS + 2) * 32;
     const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
-    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq>;
+    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq, kT>;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         cudaError_t e =

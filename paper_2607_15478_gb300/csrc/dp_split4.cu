@@ -13,7 +13,18 @@ namespace pardtw {
 bool split4_supported(int dp, int R) { return (R == 2 || R == 3) && dp <= 16; }
 
 cudaError_t launch_dp_split4(const DpArgs& a, const DpArgs* many, const int* item0, int n,
-                             int items, int* ticket, int dp, int R, int num_sms, cudaStream_t s) {
+                             int items, int* ticket, int dp, int R, int num_sms, cudaStream_t s,
+                             bool transposed) {
+    if (transposed) {  // one pair swept transposed (3 rows per lane)
+        if (many || R != 3) return cudaErrorInvalidValue;
+        switch (dp) {
+            case 4: return launch_t<4, 3, 4, false, false, false, true>(a, many, item0, n, items, ticket, num_sms, s);
+            case 8: return launch_t<8, 3, 4, false, false, false, true>(a, many, item0, n, items, ticket, num_sms, s);
+            case 12: return launch_t<12, 3, 4, false, false, false, true>(a, many, item0, n, items, ticket, num_sms, s);
+            case 16: return launch_t<16, 3, 4, false, false, false, true>(a, many, item0, n, items, ticket, num_sms, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
 #define PARDTW_SPLIT4_CASES(RR, MANY)                                                             \
     switch (dp) {                                                                                 \
         case 4: return launch_t<4, RR, 4, MANY>(a, many, item0, n, items, ticket, num_sms, s);     \

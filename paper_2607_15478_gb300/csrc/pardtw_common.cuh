@@ -120,10 +120,14 @@ cudaError_t launch_dp_multirow(const DpArgs& a, int dp, int R, int num_sms, cuda
 bool multirow_supported(int dp, int R);
 // Warp-specialised DP (dp_split.cu, dp_split4.cu): a cost warp and a DP warp
 // per strip, ns = 2 or 4 strips per CTA; R = 2, 3 or 4 rows per lane.
-cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int ns, int num_sms, cudaStream_t s);
+// transposed: the pair is swept with A and B swapped (rows of the kernel =
+// frames of B), with the tie order mapped back (R = 3, one pair).
+cudaError_t launch_dp_split(const DpArgs& a, int dp, int R, int ns, int num_sms, cudaStream_t s,
+                            bool transposed = false);
 bool split4_supported(int dp, int R);
 cudaError_t launch_dp_split4(const DpArgs& a, const DpArgs* many, const int* item0, int n,
-                             int items, int* ticket, int dp, int R, int num_sms, cudaStream_t s);
+                             int items, int* ticket, int dp, int R, int num_sms, cudaStream_t s,
+                             bool transposed);
 // The subsequence DP of WSDTW over a batch (R = 3, dp <= 32): weights 1, 1, 2,
 // free start in row 0, row La-1 of every pair into its DpArgs::lastrow.
 cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, int total_items,
@@ -132,7 +136,8 @@ cudaError_t launch_dp_subseq_many(const DpArgs* many, const int* item0, int n, i
 bool split_supported(int dp, int R, int ns = 2);
 // The same DP with the cost from BF16 features and FP32 accumulation on the
 // tensor cores (mma.sync m16n8k16): D padded to 64 or 128, R = 3.
-cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s);
+cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s,
+                                 bool transposed = false);
 bool split_bf16_supported(int dp);
 // B normalised and stored as bf16 for the BF16 cost: Lb_pad frames of
 // kBfStride elements (features beyond D and frames beyond Lb are zero).
@@ -154,8 +159,12 @@ struct DpPlan {
     int bf16;  // kind 2 only: the cost on the tensor cores from BF16 features
 };
 DpPlan choose_plan(int La, int dp, const dtw_options& o, int num_sms);
+// Whether a pair is swept transposed (B's frames as rows): B longer than A
+// (or forced by the options) and the transposed pair's plan is the warp-pair
+// DP at 3 rows per lane.
+bool transpose_pair(int La, int Lb, int dp, const dtw_options& o, int num_sms);
 cudaError_t launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, bool transposed = false);
 cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int rps, int wpb,
                              const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
                              int32_t* scratch, int* path_len, float* total, cudaStream_t s);
@@ -175,6 +184,7 @@ struct BtArgs {
     void* scratch;
     const int2* ranges;  // banded DP: the strips' sub-chunk ranges (cells outside have no
                          // path), else null
+    int transposed;      // the matrix is the transposed problem's: emit (column, row)
 };
 size_t bandmap_scratch_bytes(int La, int Lb);
 cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s);
@@ -194,11 +204,13 @@ int padded_dim(int D);
 // wrow (may be null): per coarse row of A a half-width in fine frames that
 // replaces w (the largest over the coarse rows next to a strip is used).
 cudaError_t launch_pool(const float* X, int L, int D, int ds, float* Y, cudaStream_t s);
+// swap: the fine DP sweeps the transposed pair (paths are read as (j, i);
+// La, Lb, Lac are the swept pair's rows, columns, coarse rows).
 cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, int w,
                                const float* wrow, int Lac, int La, int Lb, int nstrips, int rps,
-                               int2* ranges, cudaStream_t s);
+                               int swap, int2* ranges, cudaStream_t s);
 cudaError_t launch_band_touch(const int32_t* path, const int* plen, int cap, int Lb, int rps,
-                              const int2* ranges, int* touch, cudaStream_t s);
+                              const int2* ranges, int swap, int* touch, cudaStream_t s);
 
 // WSDTW (wsdtw.cu): one fragment of A, its backtrace matrix from the batched
 // subsequence DP and the control block of its DP.

@@ -296,3 +296,40 @@ def test_aligner_on_its_own_stream(aligner):
             A, B = dev(wp.A), dev(wp.B)
             path, total = al2.align(A, B)
             assert_parity(wp.A, wp.B, path, total)
+
+
+@pytest.mark.parametrize("La,Lb", [(300, 400), (400, 300), (500, 500), (94, 186), (1000, 1999),
+                                   (2001, 1500), (187, 250)])
+def test_transposed_sweep_is_bit_identical(aligner, La, Lb):
+    # the pair swept with B's frames as rows (the kernel's (1,2) and (2,1)
+    # candidates swapped, the tie order mapped back) gives the same cells,
+    # hence the same path and total, as the direct sweep -- for random
+    # frames and for exact ties (one-hot frames: every cost is 0 or 1)
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(58, La + Lb), La, Lb, 12, knots=4, tmin=0.5, tmax=2.0)
+    rng = np.random.default_rng(La * 7 + Lb)
+    ties = (np.eye(3, dtype=np.float32)[rng.integers(0, 3, La)],
+            np.eye(3, dtype=np.float32)[rng.integers(0, 3, Lb)])
+    for A, B in ((wp.A, wp.B), ties):
+        res = []
+        for t in (pardtw.TRANSPOSE_NEVER, pardtw.TRANSPOSE_ALWAYS, pardtw.TRANSPOSE_AUTO):
+            path, total = aligner.align(dev(A), dev(B), transpose=t)
+            res.append((path.cpu().numpy(), total))
+        for p, tot in res[1:]:
+            np.testing.assert_array_equal(p, res[0][0])
+            assert tot == res[0][1]
+        assert_parity(A, B, res[0][0], res[0][1])
+
+
+@pytest.mark.parametrize("La,Lb", [(700, 900), (900, 700)])
+def test_transposed_sweep_bf16_and_four_strips(aligner, La, Lb):
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(59, La), La, Lb, 64, kind="gaussian", knots=4,
+                           tmin=0.6, tmax=1.6, sigma=0.1)
+    for opts in ({"cost_precision": 1}, {"strips_per_cta": 4}):
+        A = wp.A if "cost_precision" in opts else wp.A[:, :12]
+        B = wp.B if "cost_precision" in opts else wp.B[:, :12]
+        p0, t0 = aligner.align(dev(A), dev(B), transpose=pardtw.TRANSPOSE_NEVER, **opts)
+        p1, t1 = aligner.align(dev(A), dev(B), transpose=pardtw.TRANSPOSE_ALWAYS, **opts)
+        np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+        assert t1 == t0
