@@ -140,8 +140,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-DP_SOURCES = ("paper_2607_15478_gb300/csrc/dp_split.cu", "paper_2607_15478_gb300/csrc/dp_device.cuh",
-              "paper_2607_15478_gb300/csrc/pardtw_common.cuh")
+DP_SOURCES = ("paper_2607_15478_gb300/csrc/dp_split.cuh", "paper_2607_15478_gb300/csrc/dp_split.cu",
+              "paper_2607_15478_gb300/csrc/dp_device.cuh")
 
 
 def dp_sources_sha256():
