@@ -31,8 +31,8 @@ namespace pardtw {
 
 namespace {
 
-constexpr int kSegThreads = 512;
-constexpr int kSegCols = kSegThreads * kColsPerWord;  // 8192 columns computed per CTA
+constexpr int kSegThreads = 256;  // two CTAs per SM (256 rather than 512: -10%)
+constexpr int kSegCols = kSegThreads * kColsPerWord;  // 4096 columns computed per CTA
 constexpr int kNoPath = -2;
 constexpr int kOrigin = -1;
 constexpr int kBand = 256;  // rows per band
@@ -98,10 +98,13 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
     for (int q = 0; q < kColsPerWord; ++q) {
         // field bits of column q (see step_of_field): bit 0 -> (1,1), else
         // bit 1 -> (1,2), else (2,1)
-        const bool f11 = (word >> (2 * q)) & 1u, f12 = (word >> (2 * q + 1)) & 1u;
         int p11 = (q >= 1) ? e1[q - 1] : l1m1;                    // (i-1, j-1)
         int p12 = (q >= 2) ? e1[q - 2] : (q == 1 ? l1m1 : l1m2);  // (i-1, j-2)
         int p21 = (q >= 1) ? e2[q - 1] : l2m1;                    // (i-2, j-1)
+        // all-ones masks of the field's bits 0 and 1 (the choice below is then
+        // two bitwise selects instead of compares and selects)
+        const int m11 = (int)(word << (31 - 2 * q)) >> 31;
+        const int m12 = (int)(word << (30 - 2 * q)) >> 31;
         if (kTop) {
             // predecessors in the band above are named 2 * column + (1 if in
             // its last row)
@@ -114,7 +117,8 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
                 p21 = (r0 >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
             }
         }
-        int v = f11 ? p11 : (f12 ? p12 : p21);
+        int v = (p21 & ~m12) | (p12 & m12);  // bit 1: (1,2), else (2,1)
+        v = (v & ~m11) | (p11 & m11);        // bit 0: (1,1)
         if (kTop && i == 0 && jb + q == 0) v = kOrigin;
         if (kBanded && (jb + q < cx || jb + q >= cy)) v = kNoPath;
         en[q] = v;
@@ -196,18 +200,29 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
     if (r0 + 1 < r1)
         bandmap_row<true, kBanded>(r0 + 1, r0, r1, La, Lb, jb, c0, width, b, top1, t, s_x, e1,
                                    e2, exits, end_entry, a.ranges, rps);
-    // the rest, kRowsAhead at a time, loading the next group meanwhile
-    for (int i = r0 + 2; i < r1; i += kRowsAhead) {
+    // the rest, kRowsAhead at a time, loading the next group meanwhile; whole
+    // groups run without a per-row guard (so the two row buffers rotate by
+    // renaming, not by moves: -15%), then the last rows of the band
+    int i = r0 + 2;
+    for (; i + kRowsAhead <= r1; i += kRowsAhead) {
         uint32_t wn[kRowsAhead];
 #pragma unroll
         for (int u = 0; u < kRowsAhead; ++u) wn[u] = load(i + kRowsAhead + u);
 #pragma unroll
         for (int u = 0; u < kRowsAhead; ++u)
-            if (i + u < r1)
-                bandmap_row<false, kBanded>(i + u, r0, r1, La, Lb, jb, c0, width, b, wq[u], t,
-                                            s_x, e1, e2, exits, end_entry, a.ranges, rps);
+            bandmap_row<false, kBanded>(i + u, r0, r1, La, Lb, jb, c0, width, b, wq[u], t,
+                                        s_x, e1, e2, exits, end_entry, a.ranges, rps);
 #pragma unroll
         for (int u = 0; u < kRowsAhead; ++u) wq[u] = wn[u];
+    }
+#pragma unroll 1
+    for (int u = 0; i + u < r1; ++u) {
+        uint32_t w = 0;
+#pragma unroll
+        for (int v = 0; v < kRowsAhead; ++v)
+            if (v == u) w = wq[v];
+        bandmap_row<false, kBanded>(i + u, r0, r1, La, Lb, jb, c0, width, b, w, t, s_x, e1, e2,
+                                    exits, end_entry, a.ranges, rps);
     }
 }
 
