@@ -167,17 +167,24 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
     __shared__ int s_x[2][kSegThreads][3];
     const int b = blockIdx.y;
     const int width = kSegCols - 2 * band;
-    const int c0 = blockIdx.x * width;
-    if (b >= sc.nbands || c0 >= Lb) return;  // CTA-uniform
+    if (b >= sc.nbands) return;  // CTA-uniform
     const int r0 = b * band;
     const int r1 = min(r0 + band, La);
+    int c0, halo;  // first stored column; columns recomputed to its left (multiple of 16)
     if (kBanded) {
-        // the band's columns over these rows (ranges are monotone in the strip)
+        // segments start at the band's first column over these rows (the
+        // ranges are monotone in the strip): every cell left of it has no
+        // path, so the first segment needs no halo and the rest of the grid
+        // covers only the band's columns
         const int xs = a.ranges[r0 / rps].x * 8, ys = a.ranges[(r1 - 1) / rps].y * 8;
-        const int halo0 = (c0 == 0) ? 0 : 2 * band;
-        if (c0 + width <= xs || c0 - halo0 >= ys) return;  // CTA-uniform
+        c0 = (xs & ~(kColsPerWord - 1)) + blockIdx.x * width;
+        if (c0 >= min(ys, Lb)) return;  // CTA-uniform
+        halo = blockIdx.x == 0 ? 0 : 2 * band;
+    } else {
+        c0 = blockIdx.x * width;
+        if (c0 >= Lb) return;  // CTA-uniform
+        halo = (c0 == 0) ? 0 : 2 * band;
     }
-    const int halo = (c0 == 0) ? 0 : 2 * band;  // multiple of 16
     const int s0 = c0 - halo;
     const int t = threadIdx.x;
     const int jb = s0 + kColsPerWord * t;  // first column of this thread
