@@ -251,6 +251,13 @@ dtw_options defaults() {
     return o;
 }
 
+// Rows per lane of a banded sweep: 3 unless the options ask for 2 or 4 (and
+// the warp-pair kernel has it for this dimension).
+int band_rows_per_lane(int dp, const dtw_options& o) {
+    const int R = o.rows_per_lane;
+    return ((R == 2 || R == 4) && split_supported(dp, R)) ? R : 3;
+}
+
 // One pair, all the way to device-resident outputs.  `out_path`,
 // `out_len`, `out_total` are device pointers (out_total may be null).
 int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D,
@@ -266,7 +273,7 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     }
     // a band (per-strip column ranges) needs the warp-pair kernel at 3 rows
     // per lane, FP32 cost
-    const DpPlan plan = ranges ? DpPlan{2, 3, kSplitStrips}
+    const DpPlan plan = ranges ? DpPlan{2, band_rows_per_lane(padded_dim(D), o), kSplitStrips}
                                : choose_plan(La, padded_dim(D), o, h->num_sms);
     const Layout L = make_layout(La, Lb, D, plan);
     int rc = ensure_workspace(h, L.total, L.border_bytes);
@@ -906,7 +913,7 @@ int band_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, in
                int Dc, int w, const float* wrowA, const float* wrowB, const BandBuf& bb,
                int32_t* path, int* path_len, float* total_cost, int* fell_back) {
     cudaStream_t s = h->stream;
-    const int rps = strip_rows(3);
+    const int rps = strip_rows(band_rows_per_lane(padded_dim(D), o));
     // the fine DP may sweep the transposed pair (B's frames as rows): the
     // strips, their ranges and the band test are then over B.  A band is one
     // chain of strips over all columns whatever its size, so the sweep runs
@@ -1071,7 +1078,8 @@ int dtw_align_banded(dtw_handle* h, const float* A, int La, const float* B, int 
         if (fell_back) *fell_back = 1;
         return align_device(h, A, La, B, Lb, D, o, path, path_len, total_cost);
     }
-    const int nstrips = (std::max(La, Lb) + strip_rows(3) - 1) / strip_rows(3);
+    // strips of the banded sweep at most (its shortest strips: 2 rows per lane)
+    const int nstrips = (std::max(La, Lb) + strip_rows(2) - 1) / strip_rows(2);
     const BandBuf bb = band_buf(Lac, Lbc, D, nstrips, true);
     rc = grow(h, &h->band, &h->band_cap, bb.total);
     if (rc != DTW_OK) return rc;
@@ -1195,7 +1203,8 @@ int dtw_align_learned(dtw_handle* h, const float* A, int La, const float* B, int
     const EncBuf eb = enc_buf(Lac, Lbc, D);
     rc = grow(h, &h->enc, &h->enc_cap, eb.total);
     if (rc != DTW_OK) return rc;
-    const int nstrips = (std::max(La, Lb) + strip_rows(3) - 1) / strip_rows(3);
+    // strips of the banded sweep at most (its shortest strips: 2 rows per lane)
+    const int nstrips = (std::max(La, Lb) + strip_rows(2) - 1) / strip_rows(2);
     const BandBuf bb = band_buf(Lac, Lbc, kEncEmbed, nstrips, false);
     rc = grow(h, &h->band, &h->band_cap, bb.total);
     if (rc != DTW_OK) return rc;
