@@ -339,54 +339,75 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
     }
 }
 
-// One CTA: prefix sum of the counts, then the cells in ascending order.
+// One CTA per band (grid.y: the pair): the band's offset (sum of the counts
+// of the bands before it) and the total, each by a block-wide sum, then the
+// band's cells in ascending order; the CTA of band 0 writes the length and
+// the total (or -status).
 template <bool kMany>
-__global__ void k_bt_emit(const BtArgs one, const BtArgs* __restrict__ many) {
-    const BtArgs& a = kMany ? many[blockIdx.x] : one;
+__global__ void __launch_bounds__(kBand) k_bt_emit(const BtArgs one, const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.y] : one;
     const int La = a.La, Lb = a.Lb, band = kBand;
     const int cap = La < Lb ? La : Lb;
-    const DevCtl* __restrict__ ctl = a.ctl;
-    const float* __restrict__ e_final = a.e_final;
-    const float mu = a.mu;
-    int32_t* __restrict__ path = a.path;
-    int* __restrict__ path_len = a.path_len;
-    float* __restrict__ total = a.total;
     const BtScratch sc = bt_scratch(a.scratch, La, Lb);
     const int nbands = sc.nbands;
+    const int b = blockIdx.x;
+    if (b >= nbands) return;  // CTA-uniform (the grid covers the largest pair)
     const int2* __restrict__ seg = sc.seg;
     const int* __restrict__ count = sc.count;
-    extern __shared__ int s_off[];  // nbands + 1
-    __shared__ int s_err;
-    if (threadIdx.x == 0) {
-        int err = ctl->status;
-        int acc = 0;
-        for (int b = 0; b < nbands; ++b) {
-            s_off[b] = acc;
-            acc += count[b];
+    __shared__ int s_red[2][kBand / 32];
+    // this thread's share of the counts before band b and of all counts
+    int before = 0, all = 0;
+    for (int q = threadIdx.x; q < nbands; q += blockDim.x) {
+        const int c = count[q];
+        all += c;
+        if (q < b) before += c;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, off);
+        all += __shfl_xor_sync(0xffffffffu, all, off);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[0][w] = before;
+        s_red[1][w] = all;
+    }
+    __syncthreads();
+    if (w == 0) {
+        before = lane < (int)(blockDim.x >> 5) ? s_red[0][lane] : 0;
+        all = lane < (int)(blockDim.x >> 5) ? s_red[1][lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, off);
+            all += __shfl_xor_sync(0xffffffffu, all, off);
         }
-        s_off[nbands] = acc;
-        if (err == 0 && (acc < 1 || acc > cap)) err = DTW_ERR_CUDA;
-        s_err = err;
-        if (err != 0) {
-            *path_len = -err;
-            if (total) *total = NAN;
-        } else {
-            *path_len = acc;
-            if (total) *total = fmaf(mu, (float)(La + Lb - 2), *e_final);
+        if (lane == 0) {
+            s_red[0][0] = before;
+            s_red[1][0] = all;
         }
     }
     __syncthreads();
-    if (s_err != 0) return;
-    // band b's cells are stored descending; they go to positions
-    // s_off[b] .. s_off[b+1]-1 reversed
-    for (int b = 0; b < nbands; ++b) {
-        const int n = count[b];
-        const int base = s_off[b];
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int2 c = seg[(size_t)b * band + (n - 1 - k)];
-            path[2 * (base + k)] = a.transposed ? c.y : c.x;
-            path[2 * (base + k) + 1] = a.transposed ? c.x : c.y;
+    before = s_red[0][0];
+    all = s_red[1][0];
+    int err = a.ctl->status;
+    if (err == 0 && (all < 1 || all > cap)) err = DTW_ERR_CUDA;
+    if (b == 0 && threadIdx.x == 0) {
+        if (err != 0) {
+            *a.path_len = -err;
+            if (a.total) *a.total = NAN;
+        } else {
+            *a.path_len = all;
+            if (a.total) *a.total = fmaf(a.mu, (float)(La + Lb - 2), *a.e_final);
         }
+    }
+    if (err != 0) return;
+    // band b's cells are stored descending; they go to before .. before+n-1 reversed
+    const int n = count[b];
+    int32_t* __restrict__ path = a.path;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int2 c = seg[(size_t)b * band + (n - 1 - k)];
+        path[2 * (before + k)] = a.transposed ? c.y : c.x;
+        path[2 * (before + k) + 1] = a.transposed ? c.x : c.y;
     }
 }
 
@@ -410,7 +431,7 @@ cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s) {
         k_bandmap<false, false><<<grid, kSegThreads, 0, s>>>(a, nullptr);
     k_bt_chain<false><<<1, 32, 0, s>>>(a, nullptr);
     k_bt_walk<false><<<(nbands + 3) / 4, 128, 0, s>>>(a, nullptr);
-    k_bt_emit<false><<<1, 256, (nbands + 1) * sizeof(int), s>>>(a, nullptr);
+    k_bt_emit<false><<<dim3((unsigned)nbands, 1), kBand, 0, s>>>(a, nullptr);
     return cudaGetLastError();
 }
 
@@ -424,7 +445,7 @@ cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, in
     k_bt_chain<true><<<n, 32, 0, s>>>(BtArgs{}, many);
     k_bt_walk<true><<<dim3((unsigned)((nbands + 3) / 4), (unsigned)n), 128, 0, s>>>(BtArgs{},
                                                                                      many);
-    k_bt_emit<true><<<n, 256, (nbands + 1) * sizeof(int), s>>>(BtArgs{}, many);
+    k_bt_emit<true><<<dim3((unsigned)nbands, (unsigned)n), kBand, 0, s>>>(BtArgs{}, many);
     return cudaGetLastError();
 }
 
