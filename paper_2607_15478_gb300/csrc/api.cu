@@ -26,6 +26,8 @@ struct dtw_handle {
     size_t ws_cap = 0;
     unsigned long long* border = nullptr;  // tagged border entries (own allocation, zeroed)
     size_t border_cap = 0;                 // bytes
+    unsigned* done = nullptr;              // per-strip flags of the DP (own allocation, zeroed)
+    size_t done_cap = 0;                   // flags
     unsigned epoch = 0;
     bool timing = false;
     bool timed = false;
@@ -236,6 +238,26 @@ int ensure_workspace(dtw_handle* h, size_t bytes, size_t border_bytes) {
     return DTW_OK;
 }
 
+// The per-strip flags of a single-pair DP with its band map inside: a
+// separate zeroed allocation, written only with call epochs (which only grow),
+// so no flag can carry the tag of a live call before its strip is done.
+int ensure_done(dtw_handle* h, int n) {
+    if ((size_t)n <= h->done_cap) return DTW_OK;
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->done) cudaFree(h->done);
+    h->done = nullptr;
+    h->done_cap = 0;
+    const size_t want = (size_t)n + (size_t)n / 8;
+    if (cudaMalloc(&h->done, want * sizeof(unsigned)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->done = nullptr;
+        return DTW_ERR_OOM;
+    }
+    CU(cudaMemsetAsync(h->done, 0, want * sizeof(unsigned), h->stream));
+    h->done_cap = want;
+    return DTW_OK;
+}
+
 dtw_options defaults() {
     dtw_options o;
     o.cost_precision = DTW_COST_FP32;
@@ -276,6 +298,19 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     const Layout L = make_layout(La, Lb, D, plan);
     int rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
+    // The warp-pair DP runs the backtrace's band map on its own CTAs when
+    // its strip groups take more than one round of resident CTAs: the CTAs
+    // that find no group in the last round map the bands above meanwhile
+    // (1e5 x 1.26e5 frames: 28.9 ms against 30.1 ms with the band map
+    // after the DP).  With one round the first band is only ready when the
+    // first strips end, near the end of the sweep, and six warps per SM map
+    // more slowly than the separate kernel's sixteen (20000 x 25000: no
+    // gain); a banded sweep's chain of strips is slowed by items beside it
+    // (+5%).
+    const bool fuse_map =
+        plan.kind == 2 && !ranges && split_map_supported(L.dp, plan.R, plan.spg, plan.bf16 != 0) &&
+        L.ngroups > split_ctas_per_sm(plan.R, plan.spg, L.dp, plan.bf16 != 0) * h->num_sms;
+    if (fuse_map && (rc = ensure_done(h, L.nstrips)) != DTW_OK) return rc;
     cudaStream_t s = h->stream;
     char* ws = h->ws;
     DevCtl* ctl = reinterpret_cast<DevCtl*>(ws + L.off_ctl);
@@ -326,8 +361,6 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     if (a.epoch == 0) a.epoch = ++h->epoch;
     a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
     a.skip_publish = o.debug_skip_publish;
-    CU(launch_plan(L.plan, a, L.dp, h->num_sms, s, tr));
-    if (h->timing) CU(cudaEventRecord(h->ev[2], s));
     BtArgs bt;
     bt.bp = bp;
     bt.La = La;
@@ -344,7 +377,17 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     bt.scratch = ws + L.off_bt;
     bt.ranges = ranges;
     bt.transposed = tr ? 1 : 0;
-    CU(launch_backtrace_bands(bt, s));
+    if (fuse_map) {
+        MapArgs m;
+        m.bt = bt;
+        m.done = h->done;
+        m.nbm = bandmap_items(La, Lb, (2 * plan.spg + 2) * 32);
+        CU(launch_dp_split_map(a, m, L.dp, h->num_sms, s, tr));
+    } else {
+        CU(launch_plan(L.plan, a, L.dp, h->num_sms, s, tr));
+    }
+    if (h->timing) CU(cudaEventRecord(h->ev[2], s));
+    CU(launch_backtrace_bands(bt, s, !fuse_map));
     if (h->timing) {
         CU(cudaEventRecord(h->ev[3], s));
         h->timed = true;
@@ -642,6 +685,7 @@ int dtw_destroy(dtw_handle* h) {
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     if (h->border) cudaFree(h->border);
+    if (h->done) cudaFree(h->done);
     if (h->band) cudaFree(h->band);
     if (h->enc) cudaFree(h->enc);
     if (h->wsd) cudaFree(h->wsd);

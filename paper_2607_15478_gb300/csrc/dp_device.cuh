@@ -53,6 +53,16 @@ __device__ __forceinline__ unsigned long long ldg1(const unsigned long long* p) 
 __device__ __forceinline__ void stg1(unsigned long long* p, unsigned long long a) {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
+// Per-strip completion flags in global memory: released by the DP warp that
+// finished the strip, acquired by the band-map items that read its words.
+__device__ __forceinline__ void st_release_g(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_g(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -28,6 +28,7 @@
 //   - Every wait is bounded (DTW_ERR_TIMEOUT) and gives up when the call has
 //     failed elsewhere.
 #pragma once
+#include "bandmap.cuh"
 #include "dp_device.cuh"
 
 // The kernel templates are included by dp_split.cu (two strips per CTA) and
@@ -421,13 +422,15 @@ __device__ __forceinline__ float pick_row(const float* cur, int k) {
 // bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
 // sub-chunk counts of the input and output rings at the start of this
 // group; csub: that of the cost ring.
-template <int R, int NS, bool kRM, bool kSubseq = false, bool kT = false>
+// kFlag: the strip raises its flag in done[strip] when its words are stored
+// (one pair with the band map inside the kernel).
+template <int R, int NS, bool kRM, bool kSubseq = false, bool kT = false, bool kFlag = false>
 __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
                                        unsigned cring, unsigned cfull, unsigned cempty,
                                        unsigned csub,
-                                       unsigned inf_blk) {
+                                       unsigned inf_blk, unsigned* done = nullptr) {
     constexpr int kRows = 31 * R;
     const bool ghost = lane == kGhostLane;
     const int i0 = strip * kRows + lane * R;
@@ -600,6 +603,12 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
 #pragma unroll
     for (int k = 0; k < R; ++k)
         if (!ghost && i0 + k == p.La - 1) *p.e_final = cur[k];
+    if (kFlag) {
+        // the strip's words are all stored: raise its flag for the band map
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_g(done + strip, p.epoch);
+    }
 }
 
 // Reader warp (groups g > 0): the bottom rows of group g-1 from the global
@@ -687,6 +696,54 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
     }
 }
 
+// Band-map item `item` of the pair (band-major: band item / nseg, column
+// segment item % nseg) by all NT threads of the CTA, once the strips covering
+// the band have raised their flags.  The wait (thread 0) gives up when the
+// call has failed elsewhere, or when no flag it waits for has come up for
+// 8 x the handoff limit (DTW_ERR_TIMEOUT, detail 6): a strip's whole sweep
+// lies between the item's start and its flag, not just one handoff.
+template <int NT>
+__device__ __noinline__ void run_bandmap_item(const DpArgs& p, const MapArgs& m, int item,
+                                              int (*s_x)[NT][3]) {
+    __shared__ int s_ok;
+    const BtArgs& bt = m.bt;
+    constexpr int kWidth = NT * kColsPerWord - 2 * kBand;
+    const int nseg = (bt.Lb + kWidth - 1) / kWidth;
+    const int b = item / nseg, segx = item - b * nseg;
+    const int s0 = (b * kBand) / p.rps;
+    const int s1 = (min((b + 1) * kBand, p.La) - 1) / p.rps;
+    auto ready = [&]() -> int {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            long long t0 = global_ns();
+            for (int s = s0; s <= s1 && ok; ++s)
+                for (int poll = 0;; ++poll) {
+                    if (ld_acquire_g(m.done + s) == p.epoch) {
+                        t0 = global_ns();
+                        break;
+                    }
+                    if (read_status(p.ctl) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > 8 * p.timeout_ns) {
+                        raise_status(p.ctl, DTW_ERR_TIMEOUT, 6);
+                        ok = 0;
+                        break;
+                    }
+                    if (poll >= 4) __nanosleep(256);
+                }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok;
+    };
+    if (bt.ranges)
+        bandmap_segment<NT, true, true>(bt, b, segx, s_x, ready);
+    else
+        bandmap_segment<NT, false, true>(bt, b, segx, s_x, ready);
+}
+
 // NS strips per CTA.  Warps 0..NS-1: the strips' cost warps; NS..2NS-1:
 // their DP warps; 2NS: the reader; 2NS+1: the writer.  Warp w runs on SM
 // sub-partition w % 4, so for NS = 2 each DP warp has a sub-partition of its
@@ -695,10 +752,20 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
 // group only ever waits on groups that started earlier.
 // kMany: the groups come from a work queue over many pairs (`many`, `item0`,
 // `ticket`; see launch_dp_split_many) instead of the pair `one`.
-template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false, bool kT = false>
-__global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
-    k_dp_split(const DpArgs one, const DpArgs* __restrict__ many, const int* __restrict__ item0,
-               int nmany, int* ticket) {
+// kMap (one pair): tickets past the strip groups are the map.nbm band-map
+// items of the pair's backtrace (map.bt, run_bandmap_item); every group has
+// been taken by a running CTA before the first item is, so an item only
+// waits on strips in progress.  For pairs whose groups outnumber the
+// resident CTAs: the CTAs of the last round that find no group then map the
+// bands above while the last strips sweep.  The launch bounds keep as many
+// CTAs per SM as the DP alone fits (split_ctas_per_sm).
+template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false, bool kT = false,
+          bool kMap = false>
+__global__ void __launch_bounds__((2 * NS + 2) * 32,
+                                  (kMap ? split_ctas_per_sm(R, NS, DP, kBF) : 1))
+    k_dp_split(const DpArgs one, const MapArgs map, const DpArgs* __restrict__ many,
+               const int* __restrict__ item0, int nmany, int* ticket) {
+    constexpr int kThreads = (2 * NS + 2) * 32;
     using S = BStage<DP>;
     using M = SplitSmem<DP, R, kBF>;
     __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
@@ -778,8 +845,8 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
                 s_group = gi;
             } else {
                 s_pair = 0;
-                s_group =
-                    read_status(one.ctl) != 0 ? one.ngroups : atomicAdd(&one.ctl->ticket, 1);
+                s_group = read_status(one.ctl) != 0 ? one.ngroups + (kMap ? map.nbm : 0)
+                                                    : atomicAdd(&one.ctl->ticket, 1);
             }
         }
         // +inf border: the top rows of group 0
@@ -790,7 +857,17 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
         if (kMany && s_group < 0) continue;  // nothing of a failed pair runs
         const DpArgs p = kMany ? many[s_pair] : one;
         const int g = s_group;
-        if (g >= p.ngroups) return;
+        if (g >= p.ngroups) {
+            if constexpr (kMap) {
+                if (g - p.ngroups < map.nbm) {
+                    // left-neighbour exchange of the band map
+                    __shared__ int s_bm[2][kThreads][3];
+                    run_bandmap_item<kThreads>(p, map, g - p.ngroups, s_bm);
+                    continue;
+                }
+            }
+            return;
+        }
         const GroupRoles gr = group_roles<NS>(p, g);
         const int strip = g * NS + w;
         // the sub-chunk ranges of the group's strips (all columns without a band)
@@ -809,9 +886,10 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
             }
         } else if (role == 1) {
             if (w < gr.nstrips_here)
-                run_dp<R, NS, kBF, kSubseq, kT>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                run_dp<R, NS, kBF, kSubseq, kT, kMap>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
                                    smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
-                                   cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]));
+                                   cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]),
+                                   kMap ? map.done : nullptr);
         } else if (role == 2) {
             if (gr.reader) {
                 // the first strip's blocks; the strip above (last of the group
@@ -839,12 +917,13 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32, 1)
 }
 
 template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = false,
-          bool kT = false>
+          bool kT = false, bool kMap = false>
 cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
-                     int* ticket, int num_sms, cudaStream_t s) {
+                     int* ticket, int num_sms, cudaStream_t s, const MapArgs* map = nullptr) {
+    static_assert(!kMap || (!kMany && !kSubseq), "the band map runs with one pair");
     constexpr int kThreads = (2 * NS + 2) * 32;
     const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
-    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq, kT>;
+    auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq, kT, kMap>;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         cudaError_t e =
@@ -855,8 +934,12 @@ cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int 
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int grid = blocks_per_sm * num_sms;
+    if (kMap) {
+        if (!map || !map->done || map->nbm <= 0) return cudaErrorInvalidValue;
+        items += map->nbm;
+    }
     if (grid > items) grid = items;
-    kern<<<grid, kThreads, smem, s>>>(a, many, item0, n, ticket);
+    kern<<<grid, kThreads, smem, s>>>(a, map ? *map : MapArgs{}, many, item0, n, ticket);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,13 @@ constexpr int kRowsPerStrip = 30;   // rows of A per warp: lanes 0..29 (lanes 30
 constexpr int kColsPerWord = 16;    // 2-bit codes per uint32 backpointer word
 constexpr int kWarpsPerGroup = 4;   // strips per CTA ("strip group") of the one-warp kernels
 constexpr int kSplitStrips = 2;     // strips per CTA of the cost/DP warp-pair kernel
+// CTAs of the warp-pair DP kernel resident per SM for one pair: two where the
+// DP's registers allow it (two strips per CTA, up to 3 rows per lane and
+// R x dp <= 36: at most 168 registers a thread, which the kernel's launch
+// bounds then enforce), else one.
+__host__ __device__ constexpr int split_ctas_per_sm(int R, int ns, int dp, bool bf16) {
+    return (ns == 2 && !bf16 && R <= 3 && R * dp <= 36) ? 2 : 1;
+}
 // BF16 cost (tensor cores): a frame of B (or row of A) takes kBfStride bf16
 // in memory, 128 features and 8 of padding, so that the 8 rows an ldmatrix
 // reads start 272 bytes apart, in 8 different bank groups.
@@ -186,8 +193,27 @@ struct BtArgs {
                          // path), else null
     int transposed;      // the matrix is the transposed problem's: emit (column, row)
 };
+// The band map inside the DP kernel (one pair): after the strip groups, nbm
+// band-map items (band, column segment) of bt's backtrace run on the same
+// CTAs, each once the strips covering its band have set their flag in
+// done[strip] to the call's epoch.
+struct MapArgs {
+    BtArgs bt;
+    unsigned* done;  // nstrips flags (own zeroed allocation, written only with epochs)
+    int nbm;
+};
 size_t bandmap_scratch_bytes(int La, int Lb);
-cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s);
+// Band-map items (bands x column segments) of a pair when CTAs of `threads`
+// threads run them inside the DP kernel.
+int bandmap_items(int La, int Lb, int threads);
+// with_map = false: the band map already ran inside the DP kernel.
+cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s, bool with_map = true);
+// The warp-pair DP of one pair with its band map inside (dp_split_map.cu):
+// m.nbm = bandmap_items(La, Lb, 192); the backtrace then runs with
+// with_map = false.  R = 3, two strips per CTA, FP32 cost, dp <= 32.
+bool split_map_supported(int dp, int R, int ns, bool bf16);
+cudaError_t launch_dp_split_map(const DpArgs& a, const MapArgs& m, int dp, int num_sms,
+                                cudaStream_t s, bool transposed);
 // n pairs at once; `many` is a device array of n BtArgs, maxLa / maxLb the
 // largest sizes among them.
 cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, int maxLb,

@@ -333,3 +333,49 @@ def test_transposed_sweep_bf16_and_four_strips(aligner, La, Lb):
         p1, t1 = aligner.align(dev(A), dev(B), transpose=pardtw.TRANSPOSE_ALWAYS, **opts)
         np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
         assert t1 == t0
+
+
+# Pairs whose strip groups outnumber the CTAs resident at once (two strips of
+# 93 rows per CTA and one CTA per SM at D = 16; 152 SMs): the DP kernel maps
+# the backtrace's bands itself, on the CTAs that find no strip group left, as
+# the strips of each band complete.  The path must be bit-identical to that
+# of a sweep whose band map runs as a separate kernel, and match the oracle.
+def test_band_map_inside_dp_kernel(aligner):
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(60, 30000), 30000, 16000, 16, knots=64, tmin=1.3,
+                           tmax=2.2)
+    A, B = dev(wp.A), dev(wp.B)
+    p0, t0 = aligner.align(A, B, transpose=pardtw.TRANSPOSE_NEVER)  # 162 groups
+    p1, t1 = aligner.align(A, B, rows_per_lane=1)  # one row per lane, separate band map
+    np.testing.assert_array_equal(p0.cpu().numpy(), p1.cpu().numpy())
+    assert t0 == t1
+    assert_parity(wp.A, wp.B, p0, t0)
+
+
+@pytest.mark.parametrize("case", ["transposed", "two_ctas_per_sm", "d32"])
+def test_band_map_inside_dp_kernel_variants(aligner, case):
+    # the first sweep has more strip groups than resident CTAs (band map in
+    # the DP kernel), the second runs its band map as a separate kernel
+    from paper_2607_15478_gb300 import pardtw
+    if case == "transposed":  # swept with B's 30000 frames as rows: 162 groups
+        wp = synth.warped_pair(synth.rng_for(61, 16000), 16000, 30000, 16, knots=64, tmin=0.45,
+                               tmax=0.77)
+        first = {"transpose": pardtw.TRANSPOSE_ALWAYS}
+        second = {"transpose": pardtw.TRANSPOSE_NEVER}
+    elif case == "two_ctas_per_sm":  # D = 12: two CTAs per SM, 307 groups
+        wp = synth.warped_pair(synth.rng_for(63, 57000), 57000, 30000, 12, knots=64, tmin=1.3,
+                               tmax=2.2)
+        first = {"transpose": pardtw.TRANSPOSE_NEVER}
+        second = {"rows_per_lane": 1}
+    else:  # D = 32: 162 groups
+        wp = synth.warped_pair(synth.rng_for(62, 30000), 30000, 16000, 32, kind="gaussian",
+                               knots=64, tmin=1.3, tmax=2.2, sigma=0.1)
+        first = {"transpose": pardtw.TRANSPOSE_NEVER}
+        second = {"rows_per_lane": 1}
+    A, B = dev(wp.A), dev(wp.B)
+    p0, t0 = aligner.align(A, B, **first)
+    p1, t1 = aligner.align(A, B, **second)
+    p0 = p0.cpu().numpy()
+    check_path_valid(p0, wp.A.shape[0], wp.B.shape[0])
+    np.testing.assert_array_equal(p0, p1.cpu().numpy())
+    assert t0 == t1
