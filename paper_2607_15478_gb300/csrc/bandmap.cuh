@@ -158,9 +158,19 @@ __device__ __forceinline__ void bandmap_segment(const BtArgs& a, int b, int segx
         if (c0 >= min(ys, Lb)) return;  // CTA-uniform
         halo = segx == 0 ? 0 : 2 * band;
     } else {
-        c0 = segx * width;
-        if (c0 >= Lb) return;  // CTA-uniform
-        halo = (c0 == 0) ? 0 : 2 * band;
+        // Only cells that can lie on a path: with steps of slope 1/2 to 2, row
+        // i's cells reachable from (0, 0) that can still reach (La-1, Lb-1)
+        // are the columns lo(i) = max(ceil(i/2), Lb-1 - 2(La-1-i)) through
+        // hi(i) = min(2i, Lb-1 - ceil((La-1-i)/2)).  lo and hi grow with i,
+        // so the band's are within [lo(r0), hi(r1-1)], and a path cell's
+        // predecessors are path cells too: segments start at lo(r0) (the
+        // first without a halo) and end at hi(r1-1); the cells left out
+        // (two thirds of a square matrix) are never asked for.
+        const int xs = max(0, max((r0 + 1) / 2, Lb - 1 - 2 * (La - 1 - r0)));
+        const int ys = min(Lb, min(2 * (r1 - 1), Lb - 1 - (La - r1 + 1) / 2) + 1);
+        c0 = (xs & ~(kColsPerWord - 1)) + segx * width;
+        if (c0 >= ys) return;  // CTA-uniform
+        halo = segx == 0 ? 0 : 2 * band;
     }
     const int s0 = c0 - halo;
     const int t = threadIdx.x;
