@@ -83,9 +83,12 @@ __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
 // One warp per band: walk back from cross[b] while inside band b, writing
 // the cells (descending) into seg + b * band; count[b] = cells written.  The
 // warp holds the backpointer block (one strip of rps rows x 16 columns, wpb
-// words) that contains the current cell, lane l holding words l, l+32, ...;
-// a step reads its word with one shuffle, and a new block is one coalesced
-// load when the path leaves the current one.
+// words) that contains the current cell, lane l holding words l, l+32, ...,
+// and the three blocks the path can enter next (above, left, above-left: a
+// step moves at most two rows and two columns, and a strip has more than
+// two rows), loaded while the path crosses the current one.  A step reads
+// its word with one shuffle; the row within the strip is tracked, not
+// divided out.
 template <bool kMany>
 __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
     const BtArgs& a = kMany ? many[blockIdx.y] : one;
@@ -106,10 +109,22 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
     }
     const int r0 = b * band;
     int i = cross[b].x, j = cross[b].y;
+    int st = i / rps, rr = i - st * rps;  // strip of row i, row within it
+    int ch = j >> 4;                      // chunk of column j
+    auto fetch = [&](int bs, int bc, uint32_t (&w)[4]) {
+        const bool ok = bs >= 0 && bc >= 0;
+        const uint32_t* src = bp + (ok ? ((size_t)bs * nchunk + bc) * wpb : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            w[k] = (ok && lane + 32 * k < wpb) ? __ldg(src + lane + 32 * k) : 0u;
+    };
+    uint32_t cur[4], up[4], lf[4], ul[4];
+    fetch(st, ch, cur);
+    fetch(st - 1, ch, up);
+    fetch(st, ch - 1, lf);
+    fetch(st - 1, ch - 1, ul);
     int n = 0;
     int2* out = seg + (size_t)b * band;
-    int blk = -1;      // (strip, chunk) block index held by the warp
-    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // words lane, lane+32, lane+64, lane+96
     int bad = 0;
     while (i >= r0) {
         if (n >= band || j < 0) {
@@ -119,29 +134,30 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
         if (lane == 0) out[n] = make_int2(i, j);
         ++n;
         if (i == 0 && j == 0) break;
-        const int strip = i / rps, rr = i - strip * rps;
-        const int want = strip * nchunk + (j >> 4);
-        if (want != blk) {  // warp-uniform
-            blk = want;
-            const uint32_t* src = bp + (size_t)want * wpb;
-            w0 = lane < wpb ? __ldg(src + lane) : 0u;
-            w1 = lane + 32 < wpb ? __ldg(src + lane + 32) : 0u;
-            w2 = lane + 64 < wpb ? __ldg(src + lane + 64) : 0u;
-            w3 = lane + 96 < wpb ? __ldg(src + lane + 96) : 0u;
-        }
         const int slot = rr >> 5;
-        const uint32_t mine = slot == 0 ? w0 : (slot == 1 ? w1 : (slot == 2 ? w2 : w3));
-        const uint32_t word = __shfl_sync(0xffffffffu, mine, rr & 31);
-        const int step = step_of_field((word >> (2 * (j & 15))) & 3u);
-        if (step == 0) {
-            i -= 1;
-            j -= 1;
-        } else if (step == 1) {
-            i -= 1;
-            j -= 2;
-        } else {
-            i -= 2;
-            j -= 1;
+        const uint32_t mine = slot == 0 ? cur[0] : (slot == 1 ? cur[1] : (slot == 2 ? cur[2] : cur[3]));
+        const uint32_t f = (__shfl_sync(0xffffffffu, mine, rr & 31) >> (2 * (j & 15))) & 3u;
+        // step_of_field: bit 0 -> (1,1); field 2 -> (1,2); field 0 -> (2,1)
+        const int di = (f == 0u) ? 2 : 1;
+        const int dj = (f == 2u) ? 2 : 1;
+        i -= di;
+        j -= dj;
+        rr -= di;
+        const bool su = rr < 0;           // into the strip above
+        const bool sl = (j >> 4) != ch;   // into the chunk to the left
+        if (su || sl) {                   // warp-uniform
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cur[k] = su ? (sl ? ul[k] : up[k]) : lf[k];
+            if (su) {
+                rr += rps;
+                --st;
+            }
+            if (sl) --ch;
+            if (i >= r0) {
+                fetch(st - 1, ch, up);
+                fetch(st, ch - 1, lf);
+                fetch(st - 1, ch - 1, ul);
+            }
         }
     }
     // the walk must leave the band exactly at the path's cell of the band above

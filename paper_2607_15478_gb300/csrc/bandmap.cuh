@@ -77,10 +77,7 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
         int p11 = (q >= 1) ? e1[q - 1] : l1m1;                    // (i-1, j-1)
         int p12 = (q >= 2) ? e1[q - 2] : (q == 1 ? l1m1 : l1m2);  // (i-1, j-2)
         int p21 = (q >= 1) ? e2[q - 1] : l2m1;                    // (i-2, j-1)
-        // all-ones masks of the field's bits 0 and 1 (the choice below is then
-        // two bitwise selects instead of compares and selects)
-        const int m11 = (int)(word << (31 - 2 * q)) >> 31;
-        const int m12 = (int)(word << (30 - 2 * q)) >> 31;
+        // the field's bits 0 and 1, each tested into a predicate
         if (kTop) {
             // predecessors in the band above are named 2 * column + (1 if in
             // its last row)
@@ -93,8 +90,8 @@ __device__ __forceinline__ void bandmap_row(int i, int r0, int r1, int La, int L
                 p21 = (r0 >= 1 && j >= 1) ? 2 * (j - 1) + 1 : kNoPath;
             }
         }
-        int v = (p21 & ~m12) | (p12 & m12);  // bit 1: (1,2), else (2,1)
-        v = (v & ~m11) | (p11 & m11);        // bit 0: (1,1)
+        int v = (word & (2u << (2 * q))) ? p12 : p21;  // bit 1: (1,2), else (2,1)
+        v = (word & (1u << (2 * q))) ? p11 : v;        // bit 0: (1,1)
         if (kTop && i == 0 && jb + q == 0) v = kOrigin;
         if (kBanded && (jb + q < cx || jb + q >= cy)) v = kNoPath;
         en[q] = v;
@@ -176,10 +173,22 @@ __device__ __forceinline__ void bandmap_segment(const BtArgs& a, int b, int segx
     const int t = threadIdx.x;
     const int jb = s0 + kColsPerWord * t;  // first column of this thread
     const bool have = jb < nchunk * kColsPerWord;
+    // rows are loaded in order r0, r0 + 1, ...: the word address of the next
+    // one (see bp_word_index) advances by one, and by a strip's stride less
+    // its rows where the next row starts a strip
+    int lrow = r0 % rps;
+    const uint32_t* lp =
+        have ? bp + bp_word_index(r0, jb, nchunk, rps, wpb) : bp;
+    const size_t wrap = (size_t)nchunk * wpb - rps;
     auto load = [&](int i) -> uint32_t {
-        if (!(have && i < r1)) return 0u;
-        const uint32_t* q = bp + bp_word_index(i, jb, nchunk, rps, wpb);
-        return kInKernel ? __ldcg(q) : __ldg(q);
+        uint32_t w = 0u;
+        if (have && i < r1) w = kInKernel ? __ldcg(lp) : __ldg(lp);
+        ++lp;
+        if (++lrow == rps) {
+            lrow = 0;
+            lp += wrap;
+        }
+        return w;
     };
     if (!ready()) return;  // CTA-uniform
 
