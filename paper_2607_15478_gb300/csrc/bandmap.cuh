@@ -12,7 +12,7 @@ namespace {
 constexpr int kSegThreads = 256;  // two CTAs per SM (256 rather than 512: -10%)
 constexpr int kNoPath = -2;
 constexpr int kOrigin = -1;
-constexpr int kBand = 256;  // rows per band
+constexpr int kBand = 128;  // rows per band
 
 // The backtrace scratch of one pair (bandmap_scratch_bytes(La, Lb) bytes).
 struct BtScratch {
