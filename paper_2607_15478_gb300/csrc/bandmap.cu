@@ -4,7 +4,7 @@
 // A serial walk costs one dependent memory access per path cell (~2e4 for
 // a 20000 x 25000 pair).  This file splits it:
 //
-//   1. k_bandmap: rows are cut into bands of 256 rows.  For every cell of
+//   1. k_bandmap: rows are cut into bands of 128 rows.  For every cell of
 //      a band, "entry" = the cell of the band above where the optimal path
 //      to this cell last sat before entering the band, encoded as
 //      2 * column + (1 if that cell is in the band above's last row, 0 if in
@@ -14,7 +14,7 @@
 //                    = encode(predecessor)      predecessor in the band above
 //      All columns of a row are independent (the inputs are rows i-1, i-2),
 //      so bands and column segments run in parallel.  A segment recomputes
-//      2 * 256 columns to its left (dependencies move at most 2 columns
+//      2 * 128 columns to its left (dependencies move at most 2 columns
 //      left per row, so those halo values are exact when they are used).
 //      Only the entries of each band's last two rows are stored, and the
 //      end cell's entry.
