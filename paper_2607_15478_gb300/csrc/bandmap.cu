@@ -18,10 +18,13 @@
 //      left per row, so those halo values are exact when they are used).
 //      Only the entries of each band's last two rows are stored, and the
 //      end cell's entry.
-//   2. k_bt_chain (one thread): from the end cell, the entries give the
-//      path's last cell in each band, band by band up to band 0.
+//   2. k_bt_compose composes the maps of bands b and b-1 (every other band),
+//      and k_bt_chain (one thread) follows the entries from the end cell up
+//      to band 0, two bands per dependent load: the path's last cell in
+//      every other band.
 //   3. k_bt_walk (one warp per band): each band's piece of the path is
-//      walked back from that cell to the band's top, in parallel.
+//      walked back from that cell (one lookup away for the bands the chain
+//      stepped over) to the band's top, in parallel.
 //   4. k_bt_emit: the pieces are concatenated in ascending order.
 //
 // Entry codes: -1 = the origin (0, 0); -2 = no path (unreachable cell).
@@ -46,8 +49,50 @@ __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
 
 }  // namespace
 
-// One thread: the path's last cell in every band, from the end cell up.
-// cross[b] = (i, j) of that cell for b < last band; status on failure.
+// The cell named by entry e of a cell of band x: a cell of band x-1's last
+// two rows.
+__device__ __forceinline__ int2 entry_cell(int e, int x) {
+    return make_int2((e & 1) ? x * kBand - 1 : x * kBand - 2, e >> 1);
+}
+// The entry of cell c of a band's last two rows from its exits word x (.x:
+// second-to-last row, .y: last row); last = the band's last row.
+__device__ __forceinline__ int pick_exit(int2 x, int ci, int last) { return ci == last ? x.y : x.x; }
+
+// Two-band exit map: for band b = nbands-2-2m (m = blockIdx.y < n2) and
+// column j, the entries of the cells of band b's last two rows two bands up,
+// composed from band b's exits and band b-1's.  Only the columns a path can
+// cross there are composed (the rest is never read).  Grid: (columns / 256,
+// n2 of the largest pair, pairs).
+template <bool kMany>
+__global__ void __launch_bounds__(256) k_bt_compose(const BtArgs one,
+                                                    const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.z] : one;
+    const int La = a.La, Lb = a.Lb;
+    const BtScratch sc = bt_scratch(a.scratch, La, Lb);
+    const int m = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= sc.n2 || j >= Lb) return;
+    const int b = sc.nbands - 2 - 2 * m;
+    const int r1 = (b + 1) * kBand;  // b <= nbands-2: a whole band
+    // columns of rows r1-2, r1-1 that can lie on a path (see bandmap_segment)
+    const int lo = max((r1 - 1) / 2, Lb - 1 - 2 * (La - 1 - (r1 - 2)));
+    const int hi = min(2 * (r1 - 1), Lb - 1);
+    if (j < lo || j > hi) return;
+    const int2* __restrict__ exits = sc.exits;
+    const int2 x = exits[(size_t)b * Lb + j];
+    auto hop = [&](int e) -> int {
+        if (e < 0) return kNoPath;
+        const int2 c = entry_cell(e, b);
+        if (c.y < 0 || c.y >= Lb) return kNoPath;
+        return pick_exit(exits[(size_t)(b - 1) * Lb + c.y], c.x, b * kBand - 1);
+    };
+    sc.exits2[(size_t)m * Lb + j] = make_int2(hop(x.x), hop(x.y));
+}
+
+// One thread: the path's last cell in bands nbands-1, nbands-2, nbands-4,
+// ... (two bands per dependent load, through the two-band exit map) and in
+// band 0; the walks find the others.  cross[b] = (i, j) of that cell;
+// status on failure.
 template <bool kMany>
 __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
     if (threadIdx.x != 0) return;
@@ -56,28 +101,41 @@ __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
     DevCtl* ctl = a.ctl;
     const BtScratch sc = bt_scratch(a.scratch, La, Lb);
     const int2* __restrict__ exits = sc.exits;
+    const int2* __restrict__ exits2 = sc.exits2;
     const int nbands = sc.nbands;
     int2* __restrict__ cross = sc.cross;
     if (ctl->status != 0) return;
     cross[nbands - 1] = make_int2(La - 1, Lb - 1);
     int e = *sc.end_entry;
-    for (int b = nbands - 1; b >= 1; --b) {
-        if (e < 0) {  // an entry must name a cell of the band above
-            atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
-            return;
-        }
-        const int r0 = b * band;
-        const int j = e >> 1;
-        const int i = (e & 1) ? r0 - 1 : r0 - 2;
-        if (i < (b - 1) * band || j < 0 || j >= Lb) {
-            atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
-            return;
-        }
-        cross[b - 1] = make_int2(i, j);
-        const int2 x = exits[(size_t)(b - 1) * Lb + j];
-        e = (i == r0 - 1) ? x.y : x.x;
+    // c = the cell named by entry e of band x, checked to lie in band x-1
+    int2 c;
+    auto take = [&](int x) -> bool {
+        if (e < 0) return false;  // an entry must name a cell of the band above
+        c = entry_cell(e, x);
+        return c.x >= (x - 1) * band && c.y >= 0 && c.y < Lb;
+    };
+    bool ok = true;
+    int b = nbands - 1;
+    if (b >= 1) {
+        ok = take(b);
+        if (ok) cross[--b] = c;
     }
-    if (e != kOrigin) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
+    while (ok && b >= 2) {  // two bands at a time
+        const int m = (nbands - 2 - b) / 2;
+        e = pick_exit(exits2[(size_t)m * Lb + c.y], c.x, (b + 1) * band - 1);
+        ok = take(b - 1);
+        if (ok) {
+            b -= 2;
+            cross[b] = c;
+        }
+    }
+    if (ok && b == 1) {
+        e = pick_exit(exits[(size_t)Lb + c.y], c.x, 2 * band - 1);
+        ok = take(1);
+        if (ok) cross[b = 0] = c;
+    }
+    if (ok && nbands >= 2) e = pick_exit(exits[c.y], c.x, band - 1);
+    if (!ok || e != kOrigin) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
 }
 
 // One warp per band: walk back from cross[b] while inside band b, writing
@@ -108,7 +166,30 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
         return;
     }
     const int r0 = b * band;
-    int i = cross[b].x, j = cross[b].y;
+    const int2* __restrict__ exits = sc.exits;
+    const int Lb = a.Lb;
+    int bad = 0;
+    // the walk's first cell: from the chain, or (for the bands it steps
+    // over) the cell its band-below's crossing names; and the cell of the
+    // band above where the walk must leave (the entry of the first cell)
+    int2 c = cross[b];
+    if (b < nbands - 1 && b > 0 && ((nbands - 2 - b) & 1)) {
+        const int2 c1 = cross[b + 1];
+        const int e = pick_exit(exits[(size_t)(b + 1) * Lb + c1.y], c1.x, (b + 2) * band - 1);
+        c = entry_cell(e, b + 1);
+        if (e < 0 || c.x < r0 || c.y < 0 || c.y >= Lb) bad = 1;
+    }
+    int2 target = make_int2(-1, -1);
+    if (!bad && b > 0) {
+        const int e = b == nbands - 1
+                          ? *sc.end_entry
+                          : pick_exit(exits[(size_t)b * Lb + c.y], c.x, (b + 1) * band - 1);
+        target = e < 0 ? make_int2(-3, -3) : entry_cell(e, b);
+    }
+    if (bad) {
+        c = make_int2(r0, 0);  // no walk; reported below
+    }
+    int i = c.x, j = c.y;
     int st = i / rps, rr = i - st * rps;  // strip of row i, row within it
     int ch = j >> 4;                      // chunk of column j
     auto fetch = [&](int bs, int bc, uint32_t (&w)[4]) {
@@ -125,8 +206,7 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
     fetch(st - 1, ch - 1, ul);
     int n = 0;
     int2* out = seg + (size_t)b * band;
-    int bad = 0;
-    while (i >= r0) {
+    while (!bad && i >= r0) {
         if (n >= band || j < 0) {
             bad = 1;
             break;
@@ -160,8 +240,8 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
             }
         }
     }
-    // the walk must leave the band exactly at the path's cell of the band above
-    if (b > 0 && !bad && (i != cross[b - 1].x || j != cross[b - 1].y)) bad = 1;
+    // the walk must leave the band exactly at the cell its first cell's entry names
+    if (b > 0 && !bad && (i != target.x || j != target.y)) bad = 1;
     if (lane == 0) {
         if (bad) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
         count[b] = n;
@@ -244,7 +324,9 @@ int bandmap_band_rows() { return kBand; }
 
 size_t bandmap_scratch_bytes(int La, int Lb) {
     const int nbands = (La + kBand - 1) / kBand;
+    const int n2 = nbands >= 4 ? (nbands - 2) / 2 : 0;
     return (size_t)nbands * Lb * sizeof(int2)        // exits
+           + (size_t)n2 * Lb * sizeof(int2)           // exits2
            + (size_t)nbands * sizeof(int2)            // cross
            + (size_t)nbands * kBand * sizeof(int2)    // seg
            + (size_t)nbands * sizeof(int) + 64;       // count, end entry
@@ -266,6 +348,10 @@ cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s, bool with_ma
         else
             k_bandmap<false, false><<<grid, kSegThreads, 0, s>>>(a, nullptr);
     }
+    const int n2 = nbands >= 4 ? (nbands - 2) / 2 : 0;
+    if (n2 > 0)
+        k_bt_compose<false><<<dim3((unsigned)((a.Lb + 255) / 256), (unsigned)n2, 1), 256, 0, s>>>(
+            a, nullptr);
     k_bt_chain<false><<<1, 32, 0, s>>>(a, nullptr);
     k_bt_walk<false><<<(nbands + 3) / 4, 128, 0, s>>>(a, nullptr);
     k_bt_emit<false><<<dim3((unsigned)nbands, 1), kBand, 0, s>>>(a, nullptr);
@@ -279,6 +365,10 @@ cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, in
     const int width = kSegCols - 2 * kBand;
     dim3 grid((unsigned)((maxLb + width - 1) / width), (unsigned)nbands, (unsigned)n);
     k_bandmap<true, false><<<grid, kSegThreads, 0, s>>>(BtArgs{}, many);
+    const int n2 = nbands >= 4 ? (nbands - 2) / 2 : 0;
+    if (n2 > 0)
+        k_bt_compose<true><<<dim3((unsigned)((maxLb + 255) / 256), (unsigned)n2, (unsigned)n),
+                             256, 0, s>>>(BtArgs{}, many);
     k_bt_chain<true><<<n, 32, 0, s>>>(BtArgs{}, many);
     k_bt_walk<true><<<dim3((unsigned)((nbands + 3) / 4), (unsigned)n), 128, 0, s>>>(BtArgs{},
                                                                                      many);

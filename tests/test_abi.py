@@ -55,13 +55,15 @@ def test_workspace_size_follows_memory_model(lib):
     # Sec. VI-D: the 2-bit backtrace matrix (L^2 / 4 bytes) plus O(L) buffers;
     # here also the tagged border rows between strip groups (16 B per column
     # per group of 4 strips) and the band entry maps of the parallel
-    # backtrace (8 B per column per band of 256 rows).  The bound is the
-    # largest layout (one row per lane: strips of 30 rows, 32 words).
+    # backtrace (8 B per column per band of 128 rows, and again for every
+    # other band: the two-band map).  The bound is the largest layout (one
+    # row per lane: strips of 30 rows, 32 words).
     for La, Lb in [(1000, 1200), (20000, 25000), (100000, 130000)]:
         n = pardtw.workspace_size(La, Lb, 12)
         bp = -(-La // 30) * 32 * -(-Lb // 16) * 16 / 4
         border = -(-(-(-La // 30)) // 4) * Lb * 16
-        maps = -(-La // 256) * Lb * 8
+        nbands = -(-La // 128)
+        maps = (nbands + (max(nbands - 2, 0) // 2 if nbands >= 4 else 0)) * Lb * 8
         extra = bp + border + maps
         assert extra <= n <= extra * 1.01 + 64 * (La + Lb) * 12
     with pytest.raises(pardtw.PardtwError):
