@@ -34,13 +34,14 @@ METRIC = "exact DTW GCUPS on 1 GB300; learned-band speedup at <=1-frame path err
 UNIT = "GCUPS"
 WORKLOAD = "pair-20000x12-vs-25000x12 chroma-like, warped (64 knots, tempo 0.7-1.4), cosine cost"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_STEP = 6  # normalise, DP, band map, band chain, band walks, emit
-# learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (6), band
-# ranges (2), banded alignment (6), band-side test (1)
-KERNELS_PER_LEARNED_STEP = 10 + 6 + 2 + 6 + 1
-# WSDTW: batched normalisation, subsequence DP, segment DP, fragment
-# backtraces, compaction
-KERNELS_PER_WSDTW_STEP = 5
+KERNELS_PER_STEP = 7  # normalise, DP, band map, two-band map, band chain, band walks, emit
+# learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (7), band
+# ranges (2), banded alignment (7), band-side test (1)
+KERNELS_PER_LEARNED_STEP = 10 + 7 + 2 + 7 + 1
+# WSDTW: batched normalisation, subsequence DP, segment DP (a tile pass and a
+# fix-up pass per fragment), fragment backtraces, compaction
+def kernels_per_wsdtw_step(nfrag):
+    return 4 + 2 * nfrag
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -544,7 +545,8 @@ def run_batch(args):
             "cpu_baseline": cpu,
             "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 7 * args.steps,
+            # epoch bump, normalisation, DP, band map, two-band map, chain, walks, emit
+            "gpu_launches": 8 * args.steps,
             "clocks": clk.summary(),
         })
     plan.close()
@@ -668,7 +670,8 @@ def run_precision(args):
         "cpu_baseline": None,
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": int(lh[0]) * 8 + 8},
-        "gpu_launches": 7 * args.steps,
+        # normalisation, bf16 packing of B, DP, band map, two-band map, chain, walks, emit
+        "gpu_launches": 8 * args.steps,
         "clocks": clk.summary(),
     })
     al.close()
@@ -917,7 +920,7 @@ def run_wsdtw(args):
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (La + Lb) * D * 4,
                 "d2h_bytes_per_step": int(ph.shape[0]) * 8},
-        "gpu_launches": KERNELS_PER_WSDTW_STEP * args.steps,
+        "gpu_launches": kernels_per_wsdtw_step(args.nfrag) * args.steps,
         "clocks": clk.summary(),
     })
     al.close()
