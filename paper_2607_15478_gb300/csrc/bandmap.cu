@@ -33,7 +33,7 @@
 namespace pardtw {
 namespace {
 
-constexpr int kSegCols = kSegThreads * kColsPerWord;  // 4096 columns computed per CTA
+constexpr int kSegCols = kSegThreads * kColsPerWord;  // 2048 columns computed per CTA
 
 template <bool kMany, bool kBanded>
 __global__ void __launch_bounds__(kSegThreads) k_bandmap(const BtArgs one,
