@@ -311,7 +311,7 @@ def run_ours(args):
         t_e2e = float(t.item())
     e2e_value = ws * cells * args.steps / t_e2e / 1e9
     h2d = (La + Lb) * D * 4
-    d2h = int(lh[0]) * 8 + 8
+    d2h = cap * 8 + 8  # total and length, and the path buffer's min(La, Lb) pairs
 
     if rank == 0:
         peaks, src = measured_peaks()
@@ -669,7 +669,7 @@ def run_precision(args):
                       "mean_path_deviation_vs_fp64_frames": dev_frames},
         "cpu_baseline": None,
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": int(lh[0]) * 8 + 8},
+                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": cap * 8 + 8},
         # normalisation, bf16 packing of B, DP, band map, two-band map, chain, walks, emit
         "gpu_launches": 8 * args.steps,
         "clocks": clk.summary(),

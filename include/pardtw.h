@@ -153,7 +153,9 @@ int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int 
 /* ---- exact alignment of one pair (Sec. II-D ParDTW, Sec. III-B) ----------- */
 /* Align A (La x D) with B (Lb x D).
  *   opt         options, or NULL for the defaults
- *   path        caller-owned int32 buffer of 2*cap entries (device or host)
+ *   path        caller-owned int32 buffer of 2*cap entries (device or host); a
+ *               host buffer receives min(La, Lb) pairs in one copy, those past
+ *               *path_len unspecified
  *   cap         capacity in (i, j) pairs; must be >= min(La, Lb)
  *   path_len    receives the number of pairs written (device or host int)
  *   total_cost  receives D[La-1][Lb-1] in FP32 (device or host float); may be NULL

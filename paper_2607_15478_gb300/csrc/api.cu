@@ -91,7 +91,7 @@ struct Layout {
     DpPlan plan;
     int dp, R, rps, wpb, nstrips, nchunk, ngroups, La_pad, cap;
     size_t off_ctl, off_ahat, off_bhat, off_bbf, off_bp, off_bt, off_stage_a, off_stage_b,
-        off_stage_path, total;
+        total;
     size_t border_bytes;
 };
 
@@ -194,8 +194,6 @@ Layout make_layout(int La, int Lb, int D, const DpPlan& plan) {
     o = align256(o + (size_t)La * D * sizeof(float));
     L.off_stage_b = o;
     o = align256(o + (size_t)Lb * D * sizeof(float));
-    L.off_stage_path = o;
-    o = align256(o + (size_t)2 * L.cap * sizeof(int32_t));
     L.total = o;
     L.border_bytes = (size_t)L.ngroups * Lb * 2 * sizeof(unsigned long long);
     return L;
@@ -712,11 +710,13 @@ int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* by
                             {1, 4, kWarpsPerGroup}, {2, 2, kSplitStrips},
                             {2, 3, kSplitStrips},   {2, 4, kSplitStrips},
                             {2, 3, kSplitStrips, 1}};
-    for (const DpPlan& plan : plans) {
-        const Layout L = make_layout(La, Lb, D, plan);
-        most = std::max(most, L.total + L.border_bytes);
-    }
-    *bytes = most;
+    for (const DpPlan& plan : plans)
+        for (int t = 0; t < 2; ++t) {  // either orientation of the sweep
+            const Layout L = t ? make_layout(Lb, La, D, plan) : make_layout(La, Lb, D, plan);
+            most = std::max(most, L.total + L.border_bytes);
+        }
+    // and a host path staged after the layout
+    *bytes = most + align256((size_t)2 * std::min(La, Lb) * sizeof(int32_t));
     return DTW_OK;
 }
 
@@ -774,16 +774,23 @@ int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     DeviceGuard g(h->device);
     if (!g.ok) return DTW_ERR_CUDA;
 
-    const Layout L = make_layout(La, Lb, D, choose_plan(La, padded_dim(D), o, h->num_sms));
-    rc = ensure_workspace(h, L.total, L.border_bytes);
+    // The workspace holds either orientation's layout (align_device picks
+    // one) with the staged path after both, so nothing moves or overlaps.
+    const int dp = padded_dim(D);
+    const Layout L1 = make_layout(La, Lb, D, choose_plan(La, dp, o, h->num_sms));
+    const Layout L2 = make_layout(Lb, La, D, choose_plan(Lb, dp, o, h->num_sms));
+    const int npairs = std::min(La, Lb);
+    const size_t off_path = std::max(L1.total, L2.total);
+    rc = ensure_workspace(h, off_path + align256((size_t)2 * npairs * sizeof(int32_t)),
+                          std::max(L1.border_bytes, L2.border_bytes));
     if (rc != DTW_OK) return rc;
     const bool path_dev = is_device_ptr(path);
     const bool len_dev = is_device_ptr(path_len);
     const bool tot_dev = total_cost ? is_device_ptr(total_cost) : true;
     char* ws = h->ws;
-    int32_t* dpath = path_dev ? path : reinterpret_cast<int32_t*>(ws + L.off_stage_path);
-    int* dlen = len_dev ? path_len : reinterpret_cast<int*>(ws + L.off_ctl + 24);
-    float* dtot = total_cost ? (tot_dev ? total_cost : reinterpret_cast<float*>(ws + L.off_ctl + 20))
+    int32_t* dpath = path_dev ? path : reinterpret_cast<int32_t*>(ws + off_path);
+    int* dlen = len_dev ? path_len : reinterpret_cast<int*>(ws + L1.off_ctl + 24);
+    float* dtot = total_cost ? (tot_dev ? total_cost : reinterpret_cast<float*>(ws + L1.off_ctl + 20))
                              : nullptr;
     rc = align_device(h, A, La, B, Lb, D, o, dpath, dlen, dtot);
     if (rc != DTW_OK) return rc;
@@ -791,18 +798,18 @@ int dtw_align(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     const bool host_out = !path_dev || !len_dev || !tot_dev;
     if (!host_out) return DTW_OK;
 
-    // host outputs: bring back length and total, then the path
-    CU(cudaMemcpyAsync(h->h_small, ws + L.off_ctl + 20, 8, cudaMemcpyDeviceToHost, s));
+    // host outputs: total, length and all min(La, Lb) path pairs the buffer
+    // has room for, then one synchronisation
+    CU(cudaMemcpyAsync(h->h_small, ws + L1.off_ctl + 20, 8, cudaMemcpyDeviceToHost, s));
     if (len_dev) CU(cudaMemcpyAsync(h->h_small + 1, path_len, 4, cudaMemcpyDeviceToHost, s));
+    if (!path_dev)
+        CU(cudaMemcpyAsync(path, dpath, (size_t)2 * npairs * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const int n = h->h_small[1];
     if (!len_dev) *path_len = n;
     if (total_cost && !tot_dev) memcpy(total_cost, &h->h_small[0], sizeof(float));
     if (n < 0) return -n;
-    if (!path_dev) {
-        CU(cudaMemcpyAsync(path, dpath, (size_t)2 * n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-    }
     return DTW_OK;
 }
 
