@@ -29,6 +29,7 @@
 //
 // Entry codes: -1 = the origin (0, 0); -2 = no path (unreachable cell).
 #include "bandmap.cuh"
+#include "block_walk.cuh"
 
 namespace pardtw {
 namespace {
@@ -138,20 +139,13 @@ __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
     if (!ok || e != kOrigin) atomicCAS(&ctl->status, 0, DTW_ERR_CUDA);
 }
 
-// One warp per band: walk back from cross[b] while inside band b, writing
-// the cells (descending) into seg + b * band; count[b] = cells written.  The
-// warp holds the backpointer block (one strip of rps rows x 16 columns, wpb
-// words) that contains the current cell, lane l holding words l, l+32, ...,
-// and the three blocks the path can enter next (above, left, above-left: a
-// step moves at most two rows and two columns, and a strip has more than
-// two rows), loaded while the path crosses the current one.  A step reads
-// its word with one shuffle; the row within the strip is tracked, not
-// divided out.
+// One warp per band: walk back from the path's last cell in band b while
+// inside the band (BlockWalker), writing the cells (descending) into
+// seg + b * band; count[b] = cells written.
 template <bool kMany>
 __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
     const BtArgs& a = kMany ? many[blockIdx.y] : one;
-    const uint32_t* __restrict__ bp = a.bp;
-    const int nchunk = a.nchunk, rps = a.rps, wpb = a.wpb, band = kBand;
+    const int band = kBand;
     DevCtl* ctl = a.ctl;
     const BtScratch sc = bt_scratch(a.scratch, a.La, a.Lb);
     const int nbands = sc.nbands;
@@ -186,24 +180,10 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
                           : pick_exit(exits[(size_t)b * Lb + c.y], c.x, (b + 1) * band - 1);
         target = e < 0 ? make_int2(-3, -3) : entry_cell(e, b);
     }
-    if (bad) {
-        c = make_int2(r0, 0);  // no walk; reported below
-    }
+    if (bad) c = make_int2(r0, 0);  // no walk; reported below
     int i = c.x, j = c.y;
-    int st = i / rps, rr = i - st * rps;  // strip of row i, row within it
-    int ch = j >> 4;                      // chunk of column j
-    auto fetch = [&](int bs, int bc, uint32_t (&w)[4]) {
-        const bool ok = bs >= 0 && bc >= 0;
-        const uint32_t* src = bp + (ok ? ((size_t)bs * nchunk + bc) * wpb : 0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            w[k] = (ok && lane + 32 * k < wpb) ? __ldg(src + lane + 32 * k) : 0u;
-    };
-    uint32_t cur[4], up[4], lf[4], ul[4];
-    fetch(st, ch, cur);
-    fetch(st - 1, ch, up);
-    fetch(st, ch - 1, lf);
-    fetch(st - 1, ch - 1, ul);
+    BlockWalker w{a.bp, a.nchunk, a.rps, a.wpb, lane};
+    w.start(i, j);
     int n = 0;
     int2* out = seg + (size_t)b * band;
     while (!bad && i >= r0) {
@@ -214,31 +194,11 @@ __global__ void k_bt_walk(const BtArgs one, const BtArgs* __restrict__ many) {
         if (lane == 0) out[n] = make_int2(i, j);
         ++n;
         if (i == 0 && j == 0) break;
-        const int slot = rr >> 5;
-        const uint32_t mine = slot == 0 ? cur[0] : (slot == 1 ? cur[1] : (slot == 2 ? cur[2] : cur[3]));
-        const uint32_t f = (__shfl_sync(0xffffffffu, mine, rr & 31) >> (2 * (j & 15))) & 3u;
-        // step_of_field: bit 0 -> (1,1); field 2 -> (1,2); field 0 -> (2,1)
-        const int di = (f == 0u) ? 2 : 1;
-        const int dj = (f == 2u) ? 2 : 1;
+        const uint32_t f = w.field(j);
+        const int di = field_di(f);
         i -= di;
-        j -= dj;
-        rr -= di;
-        const bool su = rr < 0;           // into the strip above
-        const bool sl = (j >> 4) != ch;   // into the chunk to the left
-        if (su || sl) {                   // warp-uniform
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cur[k] = su ? (sl ? ul[k] : up[k]) : lf[k];
-            if (su) {
-                rr += rps;
-                --st;
-            }
-            if (sl) --ch;
-            if (i >= r0) {
-                fetch(st - 1, ch, up);
-                fetch(st, ch - 1, lf);
-                fetch(st - 1, ch - 1, ul);
-            }
-        }
+        j -= field_dj(f);
+        w.step(di, j, i >= r0);
     }
     // the walk must leave the band exactly at the cell its first cell's entry names
     if (b > 0 && !bad && (i != target.x || j != target.y)) bad = 1;

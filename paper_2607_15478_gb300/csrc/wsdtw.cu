@@ -11,11 +11,12 @@
 //                  arg[k][j]   = the first j' attaining it,
 //                as a tiled prefix scan; then the end frames
 //                e_{N-1} = arg[N-1][Lb-1], e_{k-1} = arg[k-1][e_k - delta_k].
-//   k_bt_subseq  step 5, one thread per fragment: the walk from (last row,
+//   k_bt_subseq  step 5, one warp per fragment: the walk from (last row,
 //                e_k) back to row 0 through the fragment's backtrace matrix,
 //                written backwards into the fragment's slots of a scratch path.
 //   k_compact    the fragment paths one after another into the caller's path.
 #include "dp_device.cuh"
+#include "block_walk.cuh"
 
 namespace pardtw {
 
@@ -157,40 +158,48 @@ __global__ void __launch_bounds__(kTile)
     }
 }
 
-// One thread per fragment: the subsequence path from (len-1, e_k) to row 0,
-// stored backwards (ascending once read from slot row0 + len - n) as global
-// (row of A, frame of B) pairs.  A step that leaves the fragment's cells
-// raises DTW_ERR_CUDA (it cannot happen for a finite end cell).
+// One warp per fragment: the subsequence path from (len-1, e_k) to row 0
+// (BlockWalker), stored backwards (ascending once read from slot
+// row0 + len - n) as global (row of A, frame of B) pairs.  A step that
+// leaves the fragment's cells raises DTW_ERR_CUDA (it cannot happen for a
+// finite end cell).
 __global__ void k_bt_subseq(const WsFrag* __restrict__ fr, int N, const int* __restrict__ ends,
                             int32_t* __restrict__ scratch, int* __restrict__ count,
                             DevCtl* ctl) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (k >= N) return;
     if (ctl->status != 0) {
-        count[k] = 0;
+        if (lane == 0) count[k] = 0;
         return;
     }
     const WsFrag f = fr[k];
     int i = f.len - 1, j = ends[k];
     int n = 0;
     int32_t* out = scratch + 2 * (size_t)(f.row0 + f.len - 1);
+    BlockWalker w{f.bp, f.nchunk, f.rps, f.wpb, lane};
+    w.start(i, max(j, 0));
     for (;;) {
-        out[-2 * n] = f.row0 + i;
-        out[-2 * n + 1] = j;
+        if (lane == 0) {
+            out[-2 * n] = f.row0 + i;
+            out[-2 * n + 1] = j;
+        }
         ++n;
         if (i == 0) break;
-        const uint32_t w = f.bp[bp_word_index(i, j, f.nchunk, f.rps, f.wpb)];
-        const int st = step_of_field((w >> (2 * (j & 15))) & 3u);
-        const int di = st == 2 ? 2 : 1, dj = st == 1 ? 2 : 1;
+        const uint32_t fl = w.field(j);
+        const int di = field_di(fl);
         i -= di;
-        j -= dj;
+        j -= field_dj(fl);
         if (i < 0 || j < 0 || n >= f.len) {
-            raise_status(ctl, DTW_ERR_CUDA, 22);
-            count[k] = 0;
+            if (lane == 0) {
+                raise_status(ctl, DTW_ERR_CUDA, 22);
+                count[k] = 0;
+            }
             return;
         }
+        w.step(di, j, i > 0);
     }
-    count[k] = n;
+    if (lane == 0) count[k] = n;
 }
 
 // The fragment paths one after another: fragment k's n_k pairs sit at the
@@ -237,7 +246,7 @@ size_t seg_dp_scratch_bytes(int Lb) { return sizeof(MinArg) * (size_t)((Lb + kTi
 cudaError_t launch_bt_subseq(const WsFrag* fr, int N, const int* ends, int32_t* scratch,
                              int* count, int32_t* path, int* path_len, DevCtl* ctl,
                              cudaStream_t s) {
-    k_bt_subseq<<<(N + 63) / 64, 64, 0, s>>>(fr, N, ends, scratch, count, ctl);
+    k_bt_subseq<<<(N + 3) / 4, 128, 0, s>>>(fr, N, ends, scratch, count, ctl);
     k_compact<<<1, kSegThreads, 0, s>>>(fr, N, count, scratch, path, path_len, ctl);
     return cudaGetLastError();
 }
