@@ -38,10 +38,12 @@ KERNELS_PER_STEP = 7  # normalise, DP, band map, two-band map, band chain, band 
 # learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (7), band
 # ranges (2), banded alignment (7), band-side test (1)
 KERNELS_PER_LEARNED_STEP = 10 + 7 + 2 + 7 + 1
-# WSDTW: batched normalisation, subsequence DP, segment DP (a tile pass and a
-# fix-up pass per fragment), fragment backtraces, compaction
-def kernels_per_wsdtw_step(nfrag):
-    return 4 + 2 * nfrag
+# WSDTW: batched normalisation, subsequence DP, segment DP (one cooperative
+# launch while every column tile's CTA fits on the GPU at once, as at this
+# size; else a tile pass and a fix-up pass per fragment), fragment
+# backtraces, compaction
+def kernels_per_wsdtw_step(nfrag, Lb):
+    return 5 if (Lb + 1023) // 1024 <= 2 * SM_COUNT else 4 + 2 * nfrag
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -920,7 +922,7 @@ def run_wsdtw(args):
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (La + Lb) * D * 4,
                 "d2h_bytes_per_step": int(ph.shape[0]) * 8},
-        "gpu_launches": kernels_per_wsdtw_step(args.nfrag) * args.steps,
+        "gpu_launches": kernels_per_wsdtw_step(args.nfrag, Lb) * args.steps,
         "clocks": clk.summary(),
     })
     al.close()

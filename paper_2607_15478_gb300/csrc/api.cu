@@ -1309,7 +1309,7 @@ int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     const size_t o_tot = take(sizeof(float));
     const size_t o_ctl = take(sizeof(DevCtl));
     const size_t o_agg = take(seg_dp_scratch_bytes(Lb));
-    const size_t o_done = take(sizeof(unsigned));
+    const size_t o_done = take(2 * sizeof(unsigned));
     int rc = grow(h, &h->wsd, &h->wsd_cap, o);
     if (rc != DTW_OK) return rc;
     char* w = h->wsd;
@@ -1341,7 +1341,8 @@ int dtw_wsdtw(dtw_handle* h, const float* A, int La, const float* B, int Lb, int
     CU(launch_seg_dp(dfr, reinterpret_cast<const float*>(w + o_last), stride, N, Lb,
                      reinterpret_cast<const int*>(w + o_delta), reinterpret_cast<float*>(w + o_dseg),
                      reinterpret_cast<int*>(w + o_arg), w + o_agg,
-                     reinterpret_cast<unsigned*>(w + o_done), dends, dtot, ctl, s));
+                     reinterpret_cast<unsigned*>(w + o_done), dends, dtot, ctl,
+                     kDefaultTimeoutNs, s));
     CU(launch_bt_subseq(dfr, N, dends, reinterpret_cast<int32_t*>(w + o_scr),
                         reinterpret_cast<int*>(w + o_cnt), path, path_len, ctl, s));
     if (ends) CU(cudaMemcpyAsync(ends, dends, sizeof(int) * N, cudaMemcpyDeviceToDevice, s));

@@ -248,10 +248,12 @@ struct WsFrag {
 };
 // Segment-level DP over the fragments' last rows (stride floats apart) with
 // shortest matches delta[k]; end frames, total (D_seg[N-1][Lb-1]) and status.
-// agg: seg_dp_scratch_bytes(Lb) bytes; done: one zeroed counter.
+// agg: seg_dp_scratch_bytes(Lb) bytes; done: two counters (zeroed here);
+// timeout_ns bounds each wait of the one-launch form.
 cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride, int N, int Lb,
                           const int* delta, float* Dseg, int* arg, void* agg, unsigned* done,
-                          int* ends, float* total, DevCtl* ctl, cudaStream_t s);
+                          int* ends, float* total, DevCtl* ctl, long long timeout_ns,
+                          cudaStream_t s);
 size_t seg_dp_scratch_bytes(int Lb);
 // Fragment backtraces from their end frames into `scratch` (2 La ints), then
 // the concatenated path into `path` and its length (or -status) into path_len.

@@ -226,11 +226,159 @@ __global__ void __launch_bounds__(kSegThreads)
 
 }  // namespace
 
+// Lexicographic (value, column) minimum: the same choice as better() when the
+// columns of the two arguments are in order, for any order of arguments.
+__device__ __forceinline__ MinArg lex_min(MinArg a, MinArg b) {
+    return (b.v < a.v || (b.v == a.v && b.j < a.j)) ? b : a;
+}
+
+// Barrier over the CTAs of a cooperative launch (all resident at once):
+// bar[0] counts arrivals, bar[1] is the generation the last arrival bumps.
+// Bounded: a CTA gives up when the call has failed (any status) or after
+// waiting timeout_ns (raising DTW_ERR_TIMEOUT, detail 23), and then returns
+// false, as every CTA does once the call has failed.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevCtl* ctl, long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_g(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            st_release_g(bar + 1, g + 1);
+        } else {
+            const long long t0 = global_ns();
+            while (ld_acquire_g(bar + 1) == g) {
+                if (read_status(ctl) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > timeout_ns) {
+                    raise_status(ctl, DTW_ERR_TIMEOUT, 23);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok && read_status(ctl) == 0;
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+// The whole segment DP in one cooperative launch: one CTA per tile of kTile
+// columns, fragments one after another, two bounded grid barriers per
+// fragment (the tiles' minima complete; D_seg[k] complete before fragment
+// k+1 reads it).  Same values and columns as k_seg_tile + k_seg_fix.
+__global__ void __launch_bounds__(kTile)
+    k_seg_all(const WsFrag* __restrict__ fr, const float* __restrict__ lastrow, size_t stride,
+              int N, int Lb, const int* __restrict__ delta, float* __restrict__ Dseg,
+              int* __restrict__ arg, MinArg* __restrict__ agg, unsigned* __restrict__ bar,
+              int* __restrict__ ends, float* __restrict__ total, DevCtl* ctl,
+              long long timeout_ns) {
+    __shared__ MinArg s_warp[32];
+    __shared__ MinArg s_carry;
+    const int t = blockIdx.x;
+    const int j = t * kTile + threadIdx.x;
+    // a fragment whose DP failed (a bounded wait expired) fails the call
+    if (t == 0 && threadIdx.x == 0)
+        for (int q = 0; q < N; ++q) {
+            const int st = fr[q].pctl->status;
+            if (st != 0) {
+                raise_status(ctl, st, 20);
+                break;
+            }
+        }
+    MinArg v{INFINITY, -1};
+    for (int k = 0; k < N; ++k) {
+        const float* cs = lastrow + (size_t)k * stride;
+        const float* prev = k > 0 ? Dseg + (size_t)(k - 1) * Lb : nullptr;
+        const int dk = k > 0 ? delta[k] : 0;
+        v = MinArg{INFINITY, -1};
+        if (j < Lb) {
+            // D_seg[k-1] was written by other CTAs of this launch: read through L2
+            const float m = k == 0 ? cs[j] : (j - dk >= 0 ? __ldcg(prev + j - dk) + cs[j] : INFINITY);
+            v = MinArg{m, j};
+        }
+        v = block_scan_min(v, s_warp);
+        if (threadIdx.x == blockDim.x - 1) {
+            volatile MinArg* va = agg;
+            va[t].v = v.v;
+            va[t].j = v.j;
+        }
+        if (!grid_barrier(bar, ctl, timeout_ns)) return;
+        // the carry into this tile: the minimum over the tiles before it
+        if (threadIdx.x < 32) {
+            MinArg c{INFINITY, -1};
+            const volatile MinArg* va = agg;
+            for (int q = threadIdx.x; q < t; q += 32) c = lex_min(c, MinArg{va[q].v, va[q].j});
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                MinArg o;
+                o.v = __shfl_xor_sync(0xffffffffu, c.v, off);
+                o.j = __shfl_xor_sync(0xffffffffu, c.j, off);
+                c = lex_min(c, o);
+            }
+            if (threadIdx.x == 0) s_carry = c;
+        }
+        __syncthreads();
+        v = better(s_carry, v);
+        if (j < Lb) {
+            Dseg[(size_t)k * Lb + j] = v.v;
+            arg[(size_t)k * Lb + j] = v.j;
+        }
+        if (!grid_barrier(bar, ctl, timeout_ns)) return;
+    }
+    // the last fragment's last column: the total and the end frames
+    if (j == Lb - 1) {
+        if (ctl->status != 0) return;
+        if (!(v.v < INFINITY)) {
+            raise_status(ctl, DTW_ERR_UNREACHABLE, 21);
+            return;
+        }
+        *total = v.v;
+        int e = v.j;
+        ends[N - 1] = e;
+        for (int q = N - 1; q > 0; --q) {
+            e = __ldcg(arg + (size_t)(q - 1) * Lb + (e - delta[q]));
+            ends[q - 1] = e;
+        }
+    }
+}
+
 cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride, int N, int Lb,
                           const int* delta, float* Dseg, int* arg, void* agg, unsigned* done,
-                          int* ends, float* total, DevCtl* ctl, cudaStream_t s) {
+                          int* ends, float* total, DevCtl* ctl, long long timeout_ns,
+                          cudaStream_t s) {
     const int ntile = (Lb + kTile - 1) / kTile;
-    cudaError_t e = cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(done, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    // one cooperative launch when every tile's CTA can be resident at once
+    static int resident = -1;
+    if (resident < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_all, kTile, 0) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            resident = 0;
+        } else {
+            resident = sms * per_sm;
+        }
+    }
+    if (ntile <= resident) {
+        MinArg* aggp = static_cast<MinArg*>(agg);
+        void* args[] = {(void*)&fr,   (void*)&lastrow, (void*)&stride, (void*)&N,
+                        (void*)&Lb,   (void*)&delta,   (void*)&Dseg,   (void*)&arg,
+                        (void*)&aggp, (void*)&done,    (void*)&ends,   (void*)&total,
+                        (void*)&ctl,  (void*)&timeout_ns};
+        return cudaLaunchCooperativeKernel((const void*)k_seg_all, dim3(ntile), dim3(kTile), args,
+                                           0, s);
+    }
     for (int k = 0; k < N && e == cudaSuccess; ++k) {
         k_seg_tile<<<ntile, kTile, 0, s>>>(fr, lastrow, stride, N, Lb, k, delta, Dseg,
                                            static_cast<MinArg*>(agg), done, ctl);
