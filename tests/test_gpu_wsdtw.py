@@ -115,3 +115,20 @@ def test_wsdtw_argument_errors(aligner):
     path = torch.empty((10, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(pardtw.PardtwError):
         pardtw.dtw_wsdtw(aligner.h, A, B, 11, path, plen)  # more fragments than rows
+
+
+def test_wsdtw_long_reference_two_launch_scan(aligner):
+    # more 1024-column tiles (313) than CTAs of the one-launch segment DP that
+    # are resident at once (two per SM): the scan runs as two launches per
+    # fragment instead; same values, ends and total as the oracle
+    rng = np.random.default_rng(7)
+    B = synth.chroma_frames(rng, 320000).astype(np.float32)
+    A = (B[150000:150060] + 0.01 * rng.standard_normal((60, B.shape[1]))).astype(np.float32)
+    path, ends, total = aligner.wsdtw(dev(A), dev(B), 3)
+    r = ws.wsdtw(A, B, 3)
+    np.testing.assert_array_equal(ends.cpu().numpy(), r.ends)
+    assert abs(total - r.total) <= 1e-5 * abs(r.total) + 1e-6 * 60
+    cseg = aligner.wsdtw_cseg(3, B.shape[0]).cpu().numpy().astype(np.float64)
+    fin = np.isfinite(r.Cseg)
+    np.testing.assert_array_equal(np.isfinite(cseg), fin)
+    assert (np.abs(cseg[fin] - r.Cseg[fin]) <= 1e-5 * np.abs(r.Cseg[fin]) + 2e-5).all()
