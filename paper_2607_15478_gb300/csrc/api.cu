@@ -297,10 +297,10 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     int rc = ensure_workspace(h, L.total, L.border_bytes);
     if (rc != DTW_OK) return rc;
     // The warp-pair DP runs the backtrace's band map on its own CTAs when
-    // its strip groups take more than one round of resident CTAs: the CTAs
-    // that find no group in the last round map the bands above meanwhile
+    // its strip groups take more than one wave of resident CTAs: the CTAs
+    // that find no group in the last wave map the bands above meanwhile
     // (1e5 x 1.26e5 frames: 28.9 ms against 30.1 ms with the band map
-    // after the DP).  With one round the first band is only ready when the
+    // after the DP).  With one wave the first band is only ready when the
     // first strips end, near the end of the sweep, and six warps per SM map
     // more slowly than the separate kernel's sixteen (20000 x 25000: no
     // gain); a banded sweep's chain of strips is slowed by items beside it

@@ -2,7 +2,7 @@
 // (k_dp_split<..., kMap = true>, see dp_split.cuh): two strips of 3 rows per
 // lane per CTA, FP32 cost, either orientation.  For pairs whose strip groups
 // outnumber the CTAs resident at once: the CTAs that find no group left in
-// the last round map the bands whose strips are done, while the last strips
+// the last wave map the bands whose strips are done, while the last strips
 // still sweep, instead of a separate band-map kernel after the DP.
 #include "dp_split.cuh"
 
