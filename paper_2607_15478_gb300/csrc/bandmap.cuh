@@ -45,11 +45,13 @@ __host__ __device__ inline BtScratch bt_scratch(void* scratch, int La, int Lb) {
 }
 
 
-// Grid: (column segments, bands).  Block: kSegThreads threads; thread t owns
-// the 16 columns s0 + 16 t .. + 15 of the segment's computed range, where
+// A segment of a band is mapped by a block of NT threads: thread t owns the
+// 16 columns s0 + 16 t .. + 15 of the segment's computed range, where
 // s0 = c0 - halo; the segment stores columns c0 .. c0 + width - 1 with
-// width = kSegCols - 2 * band (segments are width apart).  Two row buffers of entries per thread live in registers;
-// the two left-neighbour columns a thread needs come through shared memory.
+// width = NT * 16 - 2 * band (segments are width apart).  Two row buffers of
+// entries per thread live in registers; the left-neighbour columns a thread
+// needs come through shared memory.
+//
 // One row of the band map for a thread's 16 columns.  kTop: the row is one
 // of the band's first two rows, whose predecessors may lie in the band above.
 template <int NT, bool kTop, bool kBanded>
