@@ -349,19 +349,27 @@ int dtw_band_cells(dtw_handle* h, long long* cells);
  * real-time loop (live score following) that must not block in the driver's
  * allocator, or a process whose device memory is already reserved by
  * another allocator (a framework's caching allocator, a plugin host with a
- * fixed budget).  dtw_align_static computes exactly what dtw_align computes
- * (same kernels, same result) but allocates nothing: all of its scratch
- * lives in one fixed device array of dtw_static_scratch_bytes() bytes
- * (64 MiB) that every GPU loading the library holds until the process exits.
+ * fixed budget).  dtw_align_static returns what dtw_align returns (the same
+ * path and the same total, bit for bit) but allocates nothing: all of its
+ * scratch lives in one fixed device array of dtw_static_scratch_bytes()
+ * bytes (64 MiB) that every GPU loading the library holds until the process
+ * exits.  It runs dtw_align's DP kernel and parallel backtrace on the pair as
+ * given (A's frames as rows; it never takes the transposed sweep, which
+ * yields the same cells).
  *
  *   A, B, path, path_len, total_cost : device pointers (total_cost may be
  *       NULL); a host pointer is rejected with DTW_ERR_INVALID
  *   cuda_stream : stream the work is ordered on (NULL = legacy default)
+ *   opt : as in dtw_align, except that only the FP32 cost is offered
+ *       (cost_precision = DTW_COST_BF16 returns DTW_ERR_UNSUPPORTED) and
+ *       opt->transpose has no effect
  *   other arguments as in dtw_align; the call is asynchronous and reports
- *       device-side failures through *path_len < 0
+ *       device-side failures (a bounded wait that expired) through
+ *       *path_len = -status
  * Sizes whose scratch (backpointers La*Lb/4 bytes plus padding, border rows,
- * normalised features) exceeds the array return DTW_ERR_SCRATCH_LIMIT before
- * any work is queued; about 1.5e8 cells fit (e.g. 10000 x 15000 at D = 12).
+ * the backtrace's band maps, normalised features) exceeds the array return
+ * DTW_ERR_SCRATCH_LIMIT before any work is queued; about 1.45e8 cells fit
+ * (2.2 cells per byte at D = 12, e.g. 12000 x 12000).
  * The first call on a device looks up the array's device address (a one-time
  * set-up per device, made with that device current); make that first call
  * before any stream capture.  Every call shares the array and leaves its

@@ -56,6 +56,7 @@ def _load():
         lib.oracle_cost_matrix.argtypes = [fp, ci, fp, ci, ci, dp]
         lib.oracle_dtw_matrix.argtypes = [dp, ci, ci, dp, up, ip, ci, ctypes.POINTER(ci), dp]
         lib.oracle_dtw.argtypes = [fp, ci, fp, ci, ci, ip, ci, ctypes.POINTER(ci), dp]
+        lib.oracle_dtw_unit.argtypes = [fp, ci, fp, ci, ci, ip, ci, ctypes.POINTER(ci), dp]
         lib.oracle_path_cost.argtypes = [fp, ci, fp, ci, ci, ip, ci, dp]
         _lib = lib
     return _lib
@@ -164,3 +165,54 @@ def path_cost(A, B, path) -> float:
                                   path.shape[0], ctypes.byref(tot))
     _check(rc, "path_cost")
     return tot.value
+
+
+def path_cost_matrix(C, path) -> float:
+    """FP64 cost of a given path over a given cost matrix: C[0,0] plus, per
+    step, its weight (2 for (1,1), 3 for (1,2) and (2,1), Sec. V) times the
+    cost of the step's destination cell.  Raises on a step outside the set."""
+    C = np.asarray(C, dtype=np.float64)
+    p = np.asarray(path, dtype=np.int64)
+    return path_cost_matrix_values(C[p[:, 0], p[:, 1]], p)
+
+
+def dtw_unit(A, B) -> Tuple[np.ndarray, float]:
+    """Exact DTW with C[i, j] = 1 - a_i . b_j for frames taken as they are
+    (the cosine cost of Sec. IV when the frames are unit vectors; nothing is
+    renormalised).  For features normalised and then rounded to a narrower
+    type, whose norms are no longer exactly 1.  Cost on the fly, as ``dtw``."""
+    A, B = _f32(A), _f32(B)
+    if A.shape[1] != B.shape[1]:
+        raise ValueError("feature dimensions differ")
+    La, Lb = A.shape[0], B.shape[0]
+    cap = min(La, Lb)
+    path = np.empty((cap, 2), dtype=np.int32)
+    n = ctypes.c_int(0)
+    tot = ctypes.c_double(0.0)
+    rc = _load().oracle_dtw_unit(_ptr(A, ctypes.c_float), La, _ptr(B, ctypes.c_float), Lb,
+                                 A.shape[1], _ptr(path, ctypes.c_int32), cap, ctypes.byref(n),
+                                 ctypes.byref(tot))
+    _check(rc, "dtw_unit")
+    return path[: n.value].copy(), tot.value
+
+
+def path_cost_unit(A, B, path) -> float:
+    """FP64 cost of a given path under C[i, j] = 1 - a_i . b_j (frames taken
+    as they are, as ``dtw_unit``), with the Sec. V weights."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    p = np.asarray(path, dtype=np.int64)
+    c = 1.0 - np.einsum("kd,kd->k", A[p[:, 0]], B[p[:, 1]])
+    return path_cost_matrix_values(c, p)
+
+
+def path_cost_matrix_values(c, p) -> float:
+    """C[0,0] + sum of w_step * C[destination] given the path's cell costs
+    ``c`` (one per path cell) and the path ``p``."""
+    d = np.diff(p, axis=0)
+    w = np.full(d.shape[0], np.nan)
+    w[(d[:, 0] == 1) & (d[:, 1] == 1)] = 2.0
+    w[((d[:, 0] == 1) & (d[:, 1] == 2)) | ((d[:, 0] == 2) & (d[:, 1] == 1))] = 3.0
+    if np.isnan(w).any():
+        raise OracleError("path cost: step outside {(1,1),(1,2),(2,1)}")
+    return float(c[0] + np.sum(w * c[1:]))

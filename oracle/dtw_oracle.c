@@ -104,8 +104,9 @@ static void cost_row(const cost_src* s, int i, int Lb, double* out) {
         return;
     }
     const float* a = s->A + (size_t)i * s->D;
-    for (int j = 0; j < Lb; ++j)
-        out[j] = cosine_cost(a, s->B + (size_t)j * s->D, s->D, s->ra[i], s->rb[j]);
+    for (int j = 0; j < Lb; ++j)   /* no norms given: the frames count as unit vectors */
+        out[j] = cosine_cost(a, s->B + (size_t)j * s->D, s->D, s->ra ? s->ra[i] : 1.0,
+                             s->rb ? s->rb[j] : 1.0);
 }
 
 static inline int get_code(const uint8_t* bp, size_t stride, int i, int j) {
@@ -228,6 +229,17 @@ int oracle_dtw(const float* A, int La, const float* B, int Lb, int D,
     free(ra);
     free(rb);
     return rc;
+}
+
+/* Exact DTW of frames taken as given, C[i][j] = 1 - a_i . b_j (the cosine
+ * cost of Sec. IV for frames that are already unit vectors; nothing is
+ * renormalised).  Used for features that were normalised and then rounded
+ * to a narrower type, whose norms are no longer exactly 1. */
+int oracle_dtw_unit(const float* A, int La, const float* B, int Lb, int D,
+                    int32_t* path, int cap, int* len, double* total) {
+    if (!A || !B || La < 1 || Lb < 1 || D < 1) return OR_ERR_INVALID;
+    cost_src s = {NULL, A, B, NULL, NULL, D};
+    return run_dtw(&s, La, Lb, NULL, NULL, path, cap, len, total);
 }
 
 /* C[0,0] + sum over steps of w_step * C[destination], in double. */

@@ -47,8 +47,6 @@ struct dtw_handle {
 
 namespace {
 
-constexpr long long kDefaultTimeoutNs = 2000000000LL;  // 2 s
-
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -895,15 +893,17 @@ int dtw_align_many(dtw_handle* h, int n, const float* const* A, const int* La,
             if (hst[k] != DTW_OK) cost[k] = hcost[k];
     // statuses: host-side ones, or the sign of the device-side lengths
     std::vector<int> lens(n);
-    if (len_dev)
-        CU(cudaMemcpy(lens.data(), path_len, sizeof(int) * n, cudaMemcpyDeviceToHost));
-    else
+    if (len_dev) {
+        CU(cudaMemcpyAsync(lens.data(), path_len, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    } else
         memcpy(lens.data(), path_len, sizeof(int) * n);
     for (int k = 0; k < n; ++k)
         if (hst[k] == DTW_OK && lens[k] < 0) hst[k] = -lens[k];
-    if (st_dev)
-        CU(cudaMemcpy(status, hst.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-    else
+    if (st_dev) {
+        CU(cudaMemcpyAsync(status, hst.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));  // hst is a local buffer
+    } else
         memcpy(status, hst.data(), sizeof(int) * n);
     return DTW_OK;
 }

@@ -10,6 +10,7 @@
 namespace pardtw {
 
 constexpr int kWarp = 32;
+constexpr long long kDefaultTimeoutNs = 2000000000LL;  // bounded device waits: 2 s
 constexpr int kRowsPerStrip = 30;   // rows of A per warp: lanes 0..29 (lanes 30, 31 carry
                                     // the two bottom rows of the strip above)
 constexpr int kColsPerWord = 16;    // 2-bit codes per uint32 backpointer word
@@ -172,9 +173,6 @@ DpPlan choose_plan(int La, int dp, const dtw_options& o, int num_sms);
 bool transpose_pair(int La, int Lb, int dp, const dtw_options& o, int num_sms);
 cudaError_t launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
                         cudaStream_t s, bool transposed = false);
-cudaError_t launch_backtrace(const uint32_t* bp, int La, int Lb, int nchunk, int rps, int wpb,
-                             const DevCtl* ctl, const float* e_final, float mu, int32_t* path,
-                             int32_t* scratch, int* path_len, float* total, cudaStream_t s);
 
 // Parallel backtrace through per-band entry maps (bandmap.cu) of one pair:
 // its backpointers and layout, its control block and end cell, the outputs,

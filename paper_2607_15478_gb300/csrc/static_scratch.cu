@@ -5,10 +5,13 @@
 // the driver's allocator, or a host process whose device memory is already
 // fully reserved by another allocator (a framework's caching allocator, a
 // plugin host with a fixed memory budget).  This entry point serves them: it
-// runs the same kernels as dtw_align, but every byte of scratch it needs
-// (normalised features, the 2-bit backpointer matrix, the border rows
-// between strip groups, control words, the path staging buffer) lives in one
-// file-scope device array of fixed size, so a call allocates nothing.
+// runs the DP kernel and the parallel backtrace that dtw_align runs for the
+// pair swept as given (A's frames as rows: it never takes the transposed
+// sweep, whose cells, path and total are bit-identical), but every byte of
+// scratch it needs (normalised features, the 2-bit backpointer matrix, the
+// border rows between strip groups, control words, the backtrace's band
+// maps) lives in one file-scope device array of fixed size, so a call
+// allocates nothing.  Only the FP32 cost is offered.
 //
 // The array exists on every device that loads the library, for the life of
 // the process.  In host code its name is only a stand-in for the symbol, not
@@ -104,7 +107,6 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     const int nchunk = (Lb + kColsPerWord - 1) / kColsPerWord;
     const int ngroups = (nstrips + plan.spg - 1) / plan.spg;
     const int La_pad = nstrips * rps;
-    const int capn = std::min(La, Lb);
 
     // scratch layout of this call
     size_t off = 0;
@@ -119,8 +121,8 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     const size_t off_border = off;
     const size_t border_bytes = (size_t)ngroups * Lb * 2 * sizeof(unsigned long long);
     off = align256s(off + border_bytes);
-    const size_t off_scratch = off;
-    off = align256s(off + (size_t)2 * capn * sizeof(int32_t));
+    const size_t off_map = off;
+    off = align256s(off + bandmap_scratch_bytes(La, Lb));
     if (off > kStaticScratchBytes) return DTW_ERR_SCRATCH_LIMIT;
 
     unsigned char* base = nullptr;
@@ -133,7 +135,6 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     float* Bt = reinterpret_cast<float*>(base + off_bt);
     uint32_t* bp = reinterpret_cast<uint32_t*>(base + off_bp);
     unsigned long long* border = reinterpret_cast<unsigned long long*>(base + off_border);
-    int32_t* scratch = reinterpret_cast<int32_t*>(base + off_scratch);
 
     // The array keeps the last call's contents.  Border entries must start
     // unmatched: clear them, and tag this call's entries with 1.
@@ -166,12 +167,26 @@ extern "C" int dtw_align_static(const float* A, int La, const float* B, int Lb, 
     a.mu = o.cost_shift;
     a.kcost = 1.0f - o.cost_shift;
     a.epoch = 1u;
-    a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : 2000000000LL;
+    a.timeout_ns = o.wait_limit > 0 ? (long long)o.wait_limit * 1000LL : kDefaultTimeoutNs;
     a.skip_publish = o.debug_skip_publish;
+    BtArgs bt;
+    bt.bp = bp;
+    bt.La = La;
+    bt.Lb = Lb;
+    bt.nchunk = nchunk;
+    bt.rps = rps;
+    bt.wpb = wpb;
+    bt.ctl = ctl;
+    bt.e_final = e_final;
+    bt.mu = o.cost_shift;
+    bt.path = path;
+    bt.path_len = path_len;
+    bt.total = total_cost;
+    bt.scratch = base + off_map;
+    bt.ranges = nullptr;
+    bt.transposed = 0;
     const cudaError_t e = launch_plan(plan, a, dp, num_sms, s);
-    if (e != cudaSuccess ||
-        launch_backtrace(bp, La, Lb, nchunk, rps, wpb, ctl, e_final, o.cost_shift, path, scratch,
-                         path_len, total_cost, s) != cudaSuccess) {
+    if (e != cudaSuccess || launch_backtrace_bands(bt, s, true) != cudaSuccess) {
         (void)cudaGetLastError();
         return DTW_ERR_CUDA;
     }

@@ -15,6 +15,8 @@
 //                e_k) back to row 0 through the fragment's backtrace matrix,
 //                written backwards into the fragment's slots of a scratch path.
 //   k_compact    the fragment paths one after another into the caller's path.
+#include <atomic>
+
 #include "dp_device.cuh"
 #include "block_walk.cuh"
 
@@ -357,17 +359,25 @@ cudaError_t launch_seg_dp(const WsFrag* fr, const float* lastrow, size_t stride,
     cudaError_t e = cudaMemsetAsync(done, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     // one cooperative launch when every tile's CTA can be resident at once
-    static int resident = -1;
-    if (resident < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    // (CTAs resident on the current device, looked up once per device)
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> resident_of[kMaxDev];  // 0 = not looked up yet, else 1 + count
+    int dev = 0, resident = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev = -1;
+    }
+    if (dev >= 0 && dev < kMaxDev && resident_of[dev].load() > 0) {
+        resident = resident_of[dev].load() - 1;
+    } else if (dev >= 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_all, kTile, 0) !=
                 cudaSuccess) {
             (void)cudaGetLastError();
-            resident = 0;
         } else {
             resident = sms * per_sm;
+            if (dev < kMaxDev) resident_of[dev].store(resident + 1);
         }
     }
     if (ntile <= resident) {

@@ -28,3 +28,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    # the largest relative errors of every oracle comparison, per kind of
+    # result, written where PARDTW_PARITY_LOG points (nothing otherwise)
+    path = os.environ.get("PARDTW_PARITY_LOG")
+    if not path:
+        return
+    from tests import _parity
+    if not _parity.RECORD:
+        return
+    import json
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    with open(path, "w") as f:
+        json.dump({"total_rel_bound": _parity.TOTAL_REL, "path_rel_bound": _parity.PATH_REL,
+                   "near_zero": _parity.NEAR_ZERO, "results": _parity.RECORD}, f, indent=1)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2607_15478_gb300 import synth
-from tests._pins import check_path_valid
+from tests._parity import assert_parity
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -40,14 +40,7 @@ def uneven_pairs(seed, n, lo, hi, D=12):
 
 
 def assert_oracle(A, B, path, total):
-    La, Lb = A.shape[0], B.shape[0]
-    p = path.cpu().numpy()
-    check_path_valid(p, La, Lb)
-    po, to = oracle.dtw(A, B)
-    assert abs(total - to) <= max(1e-5 * abs(to), 2e-6 * (La + Lb)), (total, to)
-    if not (p.shape == po.shape and np.array_equal(p, po)):
-        tg = oracle.path_cost(A, B, p)
-        assert abs(tg - to) <= 1e-6 * abs(to) + 1e-7 * (La + Lb), (tg, to)
+    assert_parity(A, B, path, total, name="batch")
 
 
 @pytest.mark.parametrize("R", [3, 2, 4])

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_2607_15478_gb300 import synth
+from tests._parity import check_against
 from tests._pins import check_path_valid
 
 torch = pytest.importorskip("torch")
@@ -51,18 +52,9 @@ def round_bf16(x):
     return u.astype(np.uint32).view(np.float32)
 
 
-def bf16_cost(A, B):
-    a = round_bf16(normalise_fp32(A)).astype(np.float64)
-    b = round_bf16(normalise_fp32(B)).astype(np.float64)
-    return 1.0 - a @ b.T
-
-
-def path_cost_from(C, p):
-    total = C[p[0, 0], p[0, 1]]
-    for (i0, j0), (i1, j1) in zip(p[:-1], p[1:]):
-        w = 2.0 if (i1 - i0, j1 - j0) == (1, 1) else 3.0
-        total += w * C[i1, j1]
-    return total
+def bf16_frames(X):
+    """The frames the tensor cores see: normalised in FP32, rounded to bf16."""
+    return round_bf16(normalise_fp32(X))
 
 
 def mean_deviation(p, q, La):
@@ -82,19 +74,32 @@ def mean_deviation(p, q, La):
 CASES = [(300, 360, 128), (1000, 1200, 128), (2000, 2400, 128), (700, 650, 64), (500, 600, 12)]
 
 
+def assert_bf16_parity(A, B, path, total, name):
+    a, b = bf16_frames(A), bf16_frames(B)
+    po, to = oracle.dtw_unit(a, b)
+    check_against(name, A.shape[0], B.shape[0], path.cpu().numpy(), float(total), po, to,
+                  lambda q: oracle.path_cost_unit(a, b, q))
+
+
 @pytest.mark.parametrize("La,Lb,D", CASES)
 def test_bf16_matches_oracle_on_bf16_features(aligner, La, Lb, D):
     wp = synth.warped_pair(synth.rng_for(3, La + D), La, Lb, D, kind="gaussian", knots=8,
                            tmin=0.7, tmax=1.4, sigma=0.1)
     path, total = aligner.align(dev(wp.A), dev(wp.B), cost_precision=1)
-    p = path.cpu().numpy()
-    check_path_valid(p, La, Lb)
-    C = bf16_cost(wp.A, wp.B)
-    po, to = oracle.dtw_matrix(C)
-    assert abs(total - to) <= max(1e-5 * abs(to), 2e-6 * (La + Lb)), (total, to)
-    if not (p.shape == po.shape and np.array_equal(p, po)):
-        tg = path_cost_from(C, p)
-        assert abs(tg - to) <= 1e-6 * abs(to) + 1e-7 * (La + Lb), (tg, to)
+    assert_bf16_parity(wp.A, wp.B, path, total, "bf16-features")
+
+
+def test_bf16_multi_wave_matches_oracle(aligner):
+    # 30000 rows swept directly: 162 strip groups of 2 x 93 rows, more than the
+    # CTAs resident at once, so the persistent grid runs several waves with
+    # the tensor-core cost warps (and the band map inside the DP kernel)
+    from paper_2607_15478_gb300 import pardtw
+    La, Lb, D = 30000, 16000, 64
+    wp = synth.warped_pair(synth.rng_for(5, La), La, Lb, D, kind="gaussian", knots=64,
+                           tmin=1.3, tmax=2.2, sigma=0.1)
+    path, total = aligner.align(dev(wp.A), dev(wp.B), cost_precision=1,
+                                transpose=pardtw.TRANSPOSE_NEVER)
+    assert_bf16_parity(wp.A, wp.B, path, total, "bf16-features-multi-wave")
 
 
 @pytest.mark.parametrize("La,Lb,D", CASES[:3])

@@ -1,24 +1,20 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
 
-Acceptance, per result:
-  * the GPU path is a valid DTW path (endpoints, step set, length bounds);
-  * it equals the oracle's path index for index, or -- where FP32 rounding
-    resolves a near-tie differently -- its FP64-recomputed cost equals the
-    oracle's optimum within 1e-6 relative, plus 1e-7 * (La + Lb) absolute
-    for totals near zero (the FP32 resolution of one normalised cell cost,
-    about D * 2^-24, times the path weight);
-  * the GPU's FP32 total is within 1e-5 relative of the oracle's FP64 total,
-    with an absolute floor of 2e-6 * (La + Lb) for totals near zero (each
-    FP32 cell cost carries an absolute error of order D * 2^-24 <= 1e-6, and
-    a path weighs (La-1)+(Lb-1)).
-Where every cost is a small integer (one-hot features) the FP32 arithmetic
-is exact, and paths and totals must match exactly.
+Acceptance (tests/_parity.py): the GPU path is a valid DTW path; its FP32
+total lies within 1e-5 relative of the oracle's FP64 total; the path equals
+the oracle's index for index, or -- where FP32 rounding resolves a near-tie
+differently -- its FP64-recomputed cost lies within 1e-6 relative of the
+optimum.  Absolute floors apply only to totals below 1 (identical or
+constant-cost sequences).  Where every cost is a small integer (one-hot
+features) the FP32 arithmetic is exact, and paths and totals must match
+exactly.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2607_15478_gb300 import synth
+from tests._parity import assert_parity
 from tests._pins import check_path_valid, constant_cost_path
 
 torch = pytest.importorskip("torch")
@@ -32,22 +28,6 @@ def aligner():
     a = pardtw.Aligner(0)
     yield a
     a.close()
-
-
-def cost_tol(total, La, Lb):
-    return max(1e-5 * abs(total), 2e-6 * (La + Lb))
-
-
-def assert_parity(A, B, path, total):
-    La, Lb = A.shape[0], B.shape[0]
-    p = path.cpu().numpy() if hasattr(path, "cpu") else np.asarray(path)
-    check_path_valid(p, La, Lb)
-    po, to = oracle.dtw(A, B)
-    assert abs(total - to) <= cost_tol(to, La, Lb), (total, to)
-    if not (p.shape == po.shape and np.array_equal(p, po)):
-        tg = oracle.path_cost(A, B, p)
-        assert abs(tg - to) <= 1e-6 * abs(to) + 1e-7 * (La + Lb), (tg, to)
-    return po, to
 
 
 def dev(x):
@@ -115,7 +95,7 @@ def test_identical_sequences_diagonal(aligner):
     A = synth.chroma_frames(synth.rng_for(52, 0), 777).astype(np.float32)
     path, total = aligner.align(dev(A), dev(A))
     np.testing.assert_array_equal(path.cpu().numpy(), np.stack([np.arange(777)] * 2, 1))
-    assert abs(total) <= 2e-6 * 2 * 777
+    assert_parity(A, A, path, total, name="identical")
 
 
 def test_zero_frames(aligner):
@@ -130,14 +110,14 @@ def test_zero_frames(aligner):
 def test_parity_config0_full(aligner):
     wp = synth.config_pair(0)
     path, total = aligner.align(dev(wp.A), dev(wp.B))
-    assert_parity(wp.A, wp.B, path, total)
+    assert_parity(wp.A, wp.B, path, total, name="pair1000x1200")
 
 
 def test_parity_config1_full(aligner):
     # the benchmark workload, in the launch configuration bench.py times
     wp = synth.config_pair(1)
     path, total = aligner.align(dev(wp.A), dev(wp.B))
-    assert_parity(wp.A, wp.B, path, total)
+    assert_parity(wp.A, wp.B, path, total, name="pair20000x25000")
 
 
 def test_cost_shift_keeps_path(aligner):
@@ -349,7 +329,7 @@ def test_band_map_inside_dp_kernel(aligner):
     p1, t1 = aligner.align(A, B, rows_per_lane=1)  # one row per lane, separate band map
     np.testing.assert_array_equal(p0.cpu().numpy(), p1.cpu().numpy())
     assert t0 == t1
-    assert_parity(wp.A, wp.B, p0, t0)
+    assert_parity(wp.A, wp.B, p0, t0, name="multi-wave")
 
 
 @pytest.mark.parametrize("case", ["transposed", "two_ctas_per_sm", "d32"])
@@ -379,3 +359,4 @@ def test_band_map_inside_dp_kernel_variants(aligner, case):
     check_path_valid(p0, wp.A.shape[0], wp.B.shape[0])
     np.testing.assert_array_equal(p0, p1.cpu().numpy())
     assert t0 == t1
+    assert_parity(wp.A, wp.B, p0, t0, name="multi-wave")

@@ -195,3 +195,44 @@ def test_golden(name):
         path, total = oracle.dtw(g["A"], g["B"])
     assert total == g["total"]
     np.testing.assert_array_equal(path, g["path"])
+
+
+def test_path_cost_matrix_against_enumeration_and_features():
+    # the matrix path cost equals the hand-written weighted sum of _pins for
+    # every path of small shapes, and the on-the-fly path cost of the features
+    rng = np.random.default_rng(17)
+    for La, Lb in [(3, 4), (5, 5), (6, 4)]:
+        C = rng.uniform(0.0, 2.0, size=(La, Lb))
+        for codes in all_paths(La, Lb):
+            p = codes_to_path(codes)
+            assert abs(oracle.path_cost_matrix(C, p) - path_weighted_cost(C, codes)) <= 1e-12
+    wp = synth.warped_pair(synth.rng_for(92, 0), 80, 95, 12, knots=4)
+    path, total = oracle.dtw(wp.A, wp.B)
+    C = oracle.cost_matrix(wp.A, wp.B)
+    assert abs(oracle.path_cost_matrix(C, path) - oracle.path_cost(wp.A, wp.B, path)) <= 1e-12 * total
+    with pytest.raises(oracle.OracleError):
+        oracle.path_cost_matrix(C, np.array([[0, 0], [0, 1]]))
+
+
+def test_dtw_unit_against_matrix_and_normalised_frames():
+    # frames taken as they are: the same as dtw_matrix over 1 - A B^T formed by
+    # a plain float64 matrix product, and the same as dtw for frames whose
+    # norm is exactly 1 (one-hot and 0.5-valued frames in 4 dimensions)
+    rng = np.random.default_rng(23)
+    A = rng.standard_normal((70, 16)).astype(np.float32)
+    B = rng.standard_normal((85, 16)).astype(np.float32)
+    p1, t1 = oracle.dtw_unit(A, B)
+    p2, t2 = oracle.dtw_matrix(1.0 - A.astype(np.float64) @ B.astype(np.float64).T)
+    np.testing.assert_array_equal(p1, p2)
+    assert abs(t1 - t2) <= 1e-12 * abs(t2)
+    assert abs(oracle.path_cost_unit(A, B, p1) - t1) <= 1e-12 * abs(t1)
+    E = np.eye(4, dtype=np.float32)
+    A = np.concatenate([E[rng.integers(0, 4, 40)], np.full((5, 4), 0.5, np.float32)])
+    B = np.concatenate([E[rng.integers(0, 4, 50)], np.full((7, 4), 0.5, np.float32)])
+    pu, tu = oracle.dtw_unit(A, B)
+    pd, td = oracle.dtw(A, B)
+    np.testing.assert_array_equal(pu, pd)
+    assert tu == td
+    # unnormalised frames differ from the cosine cost (a dropped norm shows)
+    A2 = 2.0 * A
+    assert oracle.dtw_unit(A2, B)[1] != td
