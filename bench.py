@@ -3,10 +3,18 @@
 
 One step = one exact alignment of the 20000x12 vs 25000x12 chroma-like pair
 (normalise, column-sweep DP with on-the-fly cosine cost, band entry map,
-band chain, band walks, path emit: 6 kernels), with the inputs already
-resident in HBM.  GCUPS = La*Lb / t / 1e9.
+two-band map, band chain, band walks, path emit: 7 kernels), with the inputs
+already resident in HBM.  GCUPS = La*Lb / t / 1e9.
+
+The same JSON line carries the second half of the metric and the project's
+other forms, each measured in this run on this GPU: a `band` block (the
+100000 x 126231 pair in the learned band against the full exact DP: speedup,
+fallbacks, path deviation), a `batch` block (256 uneven pairs as one CUDA
+graph) and a `bf16` block (the 40000x128 vs 48000x128 pair, BF16 cost on the
+tensor cores against the FP32 cost).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config 1..5] [--no-extras]
 
 N > 1 runs under torchrun, one rank per GPU; a single pair does not shard
 (its DP is one wavefront), so every rank aligns its own replica pair and
@@ -69,6 +77,53 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def step_stats(ms):
+    """Median, 10th and 90th percentile of per-step times (ms)."""
+    import numpy as np
+    a = np.asarray(ms, dtype=np.float64)
+    return {"median": float(np.median(a)), "p10": float(np.percentile(a, 10)),
+            "p90": float(np.percentile(a, 90)), "n": int(a.size)}
+
+
+def cpu_info():
+    """Host cores and CPU model of the machine the oracle is timed on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu model")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown",
+            "machine": os.uname().machine}
+
+
+def jbar(pp, n):
+    """Mean column matched to each row, interpolated over rows a (2,1) step skips."""
+    import numpy as np
+    acc, cnt = np.zeros(n), np.zeros(n)
+    np.add.at(acc, pp[:, 0], pp[:, 1])
+    np.add.at(cnt, pp[:, 0], 1)
+    rows = np.flatnonzero(cnt)
+    return np.interp(np.arange(n), rows, acc[rows] / cnt[rows])
+
+
+def mean_path_deviation(p, q, La):
+    import numpy as np
+    return float(np.mean(np.abs(jbar(p, La) - jbar(q, La))))
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -88,7 +143,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", "5"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -122,9 +177,9 @@ class ClockSampler:
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         t0, t1 = self.window if self.window and self.window[1] else (0.0, float("inf"))
-        # a sample arrives after its 20 ms interval: keep the ones taken inside
+        # a sample arrives after its 5 ms interval: keep the ones taken inside
         for ts, ln in self.lines:
-            if not (t0 < ts <= t1 + 0.02):
+            if not (t0 < ts <= t1 + 0.005):
                 continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:

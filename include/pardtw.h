@@ -390,6 +390,16 @@ size_t dtw_static_scratch_bytes(void);
 int dtw_enable_timing(dtw_handle* h, int on);
 int dtw_stage_times(dtw_handle* h, float* ms, int n);
 
+/* Measured FP32 fused multiply-add throughput of `device`, in FFMA per
+ * second over all SMs (best of three timed launches of a kernel that keeps
+ * every SM sub-partition issuing independent FFMAs; `iters` loop trips of
+ * 128 FFMA per thread, ~20 ms at 4096).  The paper has no counterpart: this
+ * is the measured denominator of the roofline that the DP (bound by FP32
+ * lane arithmetic, Sec. VI-C reports it compute-bound: 99.85% of ParDTW's
+ * GPU time is the DP) is reported against.  Allocates and frees a small
+ * device buffer; synchronises the device's legacy stream. */
+int dtw_fp32_peak(int device, int iters, double* ffma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

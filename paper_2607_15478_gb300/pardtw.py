@@ -37,7 +37,7 @@ EXPORTS = ("dtw_default_options", "dtw_status_string", "dtw_create", "dtw_destro
            "dtw_static_scratch_bytes", "dtw_align_banded", "dtw_encoder_param_count",
            "dtw_encode", "dtw_encoder_grad", "dtw_encoder_adam", "dtw_align_learned",
            "dtw_band_cells", "dtw_wsdtw", "dtw_wsdtw_cseg", "dtw_batch_create",
-           "dtw_batch_run", "dtw_batch_info", "dtw_batch_destroy")
+           "dtw_batch_run", "dtw_batch_info", "dtw_batch_destroy", "dtw_fp32_peak")
 DTW_BATCH_AUTOTUNE = 1
 TRANSPOSE_AUTO, TRANSPOSE_NEVER, TRANSPOSE_ALWAYS = 0, 1, 2
 
@@ -326,6 +326,14 @@ def dtw_align_static(A, B, path, path_len, total=None, options: Options | None =
 
 def dtw_static_scratch_bytes() -> int:
     return int(load_library().dtw_static_scratch_bytes())
+
+
+def fp32_peak(device: int = 0, iters: int = 4096) -> float:
+    """Measured FP32 FMA throughput of the device (FFMA per second)."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().dtw_fp32_peak(int(device), int(iters), ctypes.byref(v)),
+           "dtw_fp32_peak")
+    return float(v.value)
 
 
 class BatchPlan:

@@ -54,11 +54,16 @@ def record(name: str, La: int, Lb: int, total: float, to: float, tg: float | Non
     rel_t = abs(total - to) / abs(to) if to != 0 else abs(total - to)
     rel_p = 0.0 if tg is None else (abs(tg - to) / abs(to) if to != 0 else abs(tg - to))
     r = RECORD.setdefault(name, {"cases": 0, "max_total_rel": 0.0, "max_path_rel": 0.0,
-                                 "paths_identical": 0, "largest": None})
+                                 "paths_identical": 0, "largest": None,
+                                 "near_zero_cases": 0, "max_total_abs_near_zero": 0.0})
     r["cases"] += 1
     r["paths_identical"] += int(identical)
-    if rel_t >= r["max_total_rel"]:
-        r["max_total_rel"] = rel_t
+    if abs(to) < NEAR_ZERO:
+        # judged by the absolute floor: relative errors mean nothing here
+        r["near_zero_cases"] += 1
+        r["max_total_abs_near_zero"] = max(r["max_total_abs_near_zero"], abs(total - to))
+    else:
+        r["max_total_rel"] = max(r["max_total_rel"], rel_t)
     r["max_path_rel"] = max(r["max_path_rel"], rel_p)
     if r["largest"] is None or La * Lb > r["largest"][0] * r["largest"][1]:
         r["largest"] = (La, Lb, float(to), rel_t, rel_p)
@@ -92,12 +97,3 @@ def assert_parity(A, B, path, total, name: str = "exact", ref=None):
                   lambda q: oracle.path_cost(A, B, q))
     return po, to
 
-
-def assert_parity_matrix(C, path, total, name: str, ref=None):
-    """The same rule for a given FP64 cost matrix (oracle.dtw_matrix)."""
-    La, Lb = C.shape
-    p = as_numpy_path(path)
-    po, to = oracle.dtw_matrix(C) if ref is None else ref
-    check_against(name, La, Lb, p, float(total), po, to,
-                  lambda q: oracle.path_cost_matrix(C, q))
-    return po, to
