@@ -267,7 +267,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": WORKLOAD, "La": 20000, "Lb": 25000, "D": 12},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"leading {a}x{b} block of the pair per step, single-threaded "
-                                   f"FP64 row-by-row DTW"},
+                                   f"FP64 row-by-row DTW", **cpu_info()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -370,10 +370,16 @@ def run_ours(args):
     h2d = (La + Lb) * D * 4
     d2h = cap * 8 + 8  # total and length, and the path buffer's min(La, Lb) pairs
 
+    al.close()
     if rank == 0:
         peaks, src = measured_peaks()
-        clock = peaks.get("sm_max_mhz", 2070.0)
-        peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6      # FP32 lane-ops/s
+        nominal_ops, basis = nominal_peak(peaks, src)
+        # the FP32 FMA rate measured on this GPU in this run (an FFMA counts as
+        # one lane-op, as the D dot-product FMAs of a cell do)
+        with ClockSampler(dev.index) as pclk:
+            pclk.mark_start()
+            peak_ops = pardtw.fp32_peak(dev.index)
+            pclk.mark_end()
         ops_per_cell = D + 6
         dp_avg = statistics.mean(dp_ms) / 1e3
         achieved = cells * ops_per_cell / dp_avg
@@ -385,10 +391,11 @@ def run_ours(args):
             a, b, dt = oracle_sample(wp)
             cpu = {"value": a * b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"the full {a}x{b} pair once, single-threaded FP64 row-by-row DTW "
-                             f"({dt:.1f} s)"}
+                             f"({dt:.1f} s)", **cpu_info()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "step_ms": step_stats(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(La, Lb), "La": La, "Lb": Lb, "D": D,
@@ -400,16 +407,30 @@ def run_ours(args):
                          "kernel": "k_dp_split (column-sweep DP: per strip a cost warp and a DP "
                                    "warp, cost on the fly)",
                          "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
-                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                       f"{clock:.0f} MHz (sm_max_mhz, {src})"},
+                         "dp_launch_ms": step_stats(dp_ms),
+                         "peak_basis": "FFMA rate measured in this run (dtw_fp32_peak: every SM "
+                                       "sub-partition issuing independent FFMAs)",
+                         "peak_clocks": pclk.summary(),
+                         "nominal_peak": nominal_ops / 1e12, "nominal_basis": basis,
+                         "frac_of_nominal": achieved / nominal_ops},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk.summary(),
         }
+        if ws == 1 and not args.no_extras:
+            # the metric's second half and the other forms, on this GPU in this
+            # run: each block times its own workload (CUDA events, medians)
+            k = max(5, min(args.steps, 20))
+            line["band"], ex = measure_band(dev, k, args.warmup, flush)
+            ex["al"].close()
+            line["batch"], ex = measure_batch(dev, k, args.warmup, flush)
+            ex["plan"].close()
+            ex["al"].close()
+            line["bf16"], ex = measure_bf16(dev, k, args.warmup, flush)
+            ex["al"].close()
         print(json.dumps(line), flush=True)
-    al.close()
     if ws > 1:
         dist.destroy_process_group()
 
@@ -418,341 +439,17 @@ def _rank0_line(line):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
-    """The batching workload: 256 seeded pairs (La ~ U[500, 8000], Lb = La x
-    U[0.8, 1.25], D = 12) as a planned batch (dtw_batch_create: the DP
-    schedule picked by the autotuner, the whole batch -- normalisation, one
-    persistent DP launch over a (pair, strip group) work queue, the batched
-    backtrace -- captured in one CUDA graph); a step is one graph replay.  The
-    same batch through dtw_align_many (no graph) is timed beside it.  N ranks
-    split the pairs by cell count (LPT) and align their shares independently
-    (strong scaling)."""
+def measure_band(dev, steps, warmup, flush, exact_runs=3):
+    """The learned-band workload (the 100000x12 vs 126231x12 pair, tempo
+    0.6-1.6, 256 knots) aligned exactly inside the band of the trained
+    encoder (dtw_align_learned, bf16 encoder) and, on the same GPU in the same
+    run, by the full exact DP.  Returns the block and what the --config 4 line
+    adds (timings of the banded DP launches, clocks, the pair)."""
     import numpy as np
     import torch
-    import torch.distributed as dist
-    ws, rank, local = dist_env()
-    if ws > 1:
-        dist.init_process_group("nccl")
-        torch.cuda.set_device(local)
-    dev = torch.device("cuda", local if ws > 1 else 0)
-    from paper_2607_15478_gb300 import build as pbuild
-    if rank == 0 or ws == 1:
-        pbuild.build()
-    if ws > 1:
-        dist.barrier()
-    from paper_2607_15478_gb300 import pardtw, shard, synth
-    pairs_all = synth.config_batch(2)
-    cells_all = [p.A.shape[0] * p.B.shape[0] for p in pairs_all]
-    mine = shard.partition_pairs(cells_all, ws)[rank]
-    pairs = [pairs_all[k] for k in mine]
-    cells = sum(cells_all[k] for k in mine)
-    stream = torch.cuda.Stream(device=dev)
-    al = pardtw.Aligner(dev.index, stream)
-    al.enable_timing(True)
-    # all features in one device buffer (A of every pair, then B of every
-    # pair), the pairs' inputs being views of it, so that one host-to-device
-    # copy refills a whole batch
-    sizes = [p.A.size for p in pairs] + [p.B.size for p in pairs]
-    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    feat_h = torch.empty(int(offs[-1]), dtype=torch.float32).pin_memory()
-    for k, x in enumerate([p.A for p in pairs] + [p.B for p in pairs]):
-        feat_h[int(offs[k]):int(offs[k + 1])] = torch.from_numpy(x.reshape(-1))
-    feat = feat_h.to(dev)
-    n_p = len(pairs)
-    As = [feat[int(offs[k]):int(offs[k + 1])].view(pairs[k].A.shape) for k in range(n_p)]
-    Bs = [feat[int(offs[n_p + k]):int(offs[n_p + k + 1])].view(pairs[k].B.shape)
-          for k in range(n_p)]
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    st = None
-
-    def step_many():
-        nonlocal st
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            ev0.record(stream)
-            _, _, st = al.align_many(As, Bs)
-            ev1.record(stream)
-
-    # the same batch without a graph: its time and its DP launch time
-    many_ms, dp_ms = [], []
-    for k in range(args.warmup + 3):
-        step_many()
-        ev1.synchronize()
-        if k >= args.warmup:
-            many_ms.append(ev0.elapsed_time(ev1))
-            dp_ms.append(al.stage_times()[1])
-    if st is not None and (st != 0).any():
-        raise RuntimeError(f"batch alignment failed on rank {rank}")
-    plan = al.plan_batch(As, Bs, autotune=True)
-    R_tuned, NS_tuned, tuned_ms = plan.info()
-
-    def step():
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            ev0.record(stream)
-            plan.run()
-            ev1.record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    if (plan.path_len.cpu().numpy() <= 0).any():
-        raise RuntimeError(f"planned batch failed on rank {rank}")
-    step_ms = []
-    with ClockSampler(dev.index) as clk:
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        clk.mark_start()
-        for _ in range(args.steps):
-            step()
-            ev1.synchronize()
-            step_ms.append(ev0.elapsed_time(ev1))
-        torch.cuda.synchronize(dev)
-        clk.mark_end()
-        if ws > 1:
-            dist.barrier()
-    t_local = sum(step_ms) / 1e3
-    t_max = t_local
-    if ws > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = sum(cells_all) * args.steps / t_max / 1e9
-    # end to end: the batch's features copied in from pinned host memory (one
-    # copy into the plan's input buffer), the plan's graph, paths, lengths and
-    # costs copied out (one copy each), the paths split per pair on the host
-    paths_h = torch.empty(plan.paths.shape, dtype=torch.int32).pin_memory()
-    lens_h = torch.empty(plan.path_len.shape, dtype=torch.int32).pin_memory()
-    cost_h = torch.empty(plan.cost.shape, dtype=torch.float32).pin_memory()
-    al.enable_timing(False)
-    e2e_t = []
-    for k in range(args.warmup + args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-        stream.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            feat.copy_(feat_h, non_blocking=True)
-            plan.run()
-            paths_h.copy_(plan.paths, non_blocking=True)
-            lens_h.copy_(plan.path_len, non_blocking=True)
-            cost_h.copy_(plan.cost, non_blocking=True)
-        stream.synchronize()
-        ln = lens_h.numpy()
-        out = [paths_h[int(plan.off[q]):int(plan.off[q]) + int(ln[q])] for q in range(n_p)]
-        e2e_t.append(time.perf_counter() - t0)
-    h2d = int(feat_h.numel()) * 4
-    d2h = int(paths_h.numel()) * 4 + 8 * n_p
-    t_e2e = sum(e2e_t[args.warmup:])
-    if ws > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    if rank == 0:
-        peaks, src = measured_peaks()
-        clock = peaks.get("sm_max_mhz", 2070.0)
-        peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6
-        dp_avg = statistics.mean(dp_ms) / 1e3
-        achieved = cells * 18 / dp_avg
-        cpu = None
-        if not args.no_cpu_baseline:
-            import oracle
-            oracle.build()
-            t0 = time.perf_counter()
-            done = 0
-            for p in pairs_all:
-                if time.perf_counter() - t0 > 15.0:
-                    break
-                oracle.dtw(p.A, p.B)
-                done += p.A.shape[0] * p.B.shape[0]
-            dt = time.perf_counter() - t0
-            cpu = {"value": done / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"the first pairs of the batch, one after another, until 15 s "
-                             f"({done / 1e9:.2f} Gcells in {dt:.1f} s), single-threaded FP64"}
-        _rank0_line({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "batch-256-pairs La~U[500,8000] Lb=La*U[0.8,1.25] D=12 "
-                                   "chroma-like, warped (8 knots)",
-                       "pairs": len(pairs_all), "cells": sum(cells_all), "D": 12,
-                       "l2": "flushed between steps (512 MiB write)",
-                       "parallelism": f"pairs split by cell count over {ws} rank(s)",
-                       "graph": "one CUDA graph replay per step (dtw_batch_run)",
-                       "schedule": f"autotuned: {R_tuned} rows per lane, {NS_tuned} strips "
-                                   f"per CTA"},
-            "batch": {"graph_ms": 1e3 * t_max / args.steps,
-                      "align_many_ms": statistics.median(many_ms),
-                      "autotune_rows_per_lane": R_tuned, "autotune_strips_per_cta": NS_tuned,
-                      "autotune_ms": {f"R{r}_NS{ns}": tuned_ms[(3 if ns == 4 else 0) + r - 2]
-                                      for ns in (2, 4) for r in (2, 3, 4)}},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
-                         "traffic": None,
-                         "kernel": "k_dp_split, batch mode (work queue over pairs), "
-                                   "3 rows per lane, 4 strips per CTA (timed through "
-                                   "dtw_align_many)",
-                         "ops_per_cell": 18, "dp_ms": 1e3 * dp_avg,
-                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                       f"{clock:.0f} MHz (sm_max_mhz, {src})"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # epoch bump, normalisation, DP, band map, two-band map, chain, walks, emit
-            "gpu_launches": 8 * args.steps,
-            "clocks": clk.summary(),
-        })
-    plan.close()
-    al.close()
-    if ws > 1:
-        dist.destroy_process_group()
-
-
-def run_precision(args):
-    """The precision workload: the 40000x128 vs 48000x128 pair with the cost
-    from bf16 features on the tensor cores (FP32 accumulate, FP32 DP); the
-    FP32 cost path is timed once beside it, and the errors against it and
-    against the FP64 oracle (on a 2000x2400 pair of the same recipe) are
-    reported."""
-    import numpy as np
-    import torch
-    ws, rank, local = dist_env()
-    dev = torch.device("cuda", local if ws > 1 else 0)
-    from paper_2607_15478_gb300 import build as pbuild
-    pbuild.build()
-    from paper_2607_15478_gb300 import pardtw, synth
-    wp = synth.config_pair(3, pair=rank)
-    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
-    cells = La * Lb
-    stream = torch.cuda.Stream(device=dev)
-    al = pardtw.Aligner(dev.index, stream)
-    al.enable_timing(True)
-    A = torch.from_numpy(wp.A).to(dev)
-    B = torch.from_numpy(wp.B).to(dev)
-    cap = min(La, Lb)
-    path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
-    plen = torch.zeros(1, dtype=torch.int32, device=dev)
-    tot = torch.zeros(1, dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-
-    def step(prec):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            ev0.record(stream)
-            al.align_into(A, B, path, plen, tot, cost_precision=prec)
-            ev1.record(stream)
-
-    for _ in range(args.warmup):
-        step(1)
-    step_ms, dp_ms = [], []
-    with ClockSampler(dev.index) as clk:
-        torch.cuda.synchronize(dev)
-        clk.mark_start()
-        for _ in range(args.steps):
-            step(1)
-            ev1.synchronize()
-            step_ms.append(ev0.elapsed_time(ev1))
-            dp_ms.append(al.stage_times()[1])
-        clk.mark_end()
-    t = sum(step_ms) / 1e3
-    value = cells * args.steps / t / 1e9
-    tot_bf, path_bf = float(tot.item()), path[:int(plen.item())].cpu().numpy()
-    step(0)  # the FP32 cost path once, for comparison
-    ev1.synchronize()
-    fp32_ms = ev0.elapsed_time(ev1)
-    tot_f32, path_f32 = float(tot.item()), path[:int(plen.item())].cpu().numpy()
-    # e2e: host features in, path out
-    Ah = torch.from_numpy(wp.A).pin_memory()
-    Bh = torch.from_numpy(wp.B).pin_memory()
-    ph = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
-    lh = torch.zeros(1, dtype=torch.int32).pin_memory()
-    th = torch.zeros(1, dtype=torch.float32).pin_memory()
-    al.enable_timing(False)
-    opts = pardtw.make_options(cost_precision=1)
-    e2e_t = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        pardtw.dtw_align(al.h, Ah, Bh, ph, lh, th, opts)
-        e2e_t.append(time.perf_counter() - t0)
-    t_e2e = sum(e2e_t[args.warmup:])
-    # error against the FP64 oracle on a smaller pair of the same recipe
-    import oracle
-    oracle.build()
-    sp = synth.config_pair(3, La=2000, Lb=2400)
-    pb, tb = al.align(torch.from_numpy(sp.A).to(dev), torch.from_numpy(sp.B).to(dev),
-                      cost_precision=1)
-    po, to = oracle.dtw(sp.A, sp.B)
-    pbn = pb.cpu().numpy()
-    tg = oracle.path_cost(sp.A, sp.B, pbn)
-
-    def jbar(pp, n):
-        acc, cnt = np.zeros(n), np.zeros(n)
-        np.add.at(acc, pp[:, 0], pp[:, 1])
-        np.add.at(cnt, pp[:, 0], 1)
-        rows = np.flatnonzero(cnt)
-        return np.interp(np.arange(n), rows, acc[rows] / cnt[rows])
-    dev_frames = float(np.mean(np.abs(jbar(pbn, 2000) - jbar(po, 2000))))
-    dev_full = float(np.mean(np.abs(jbar(path_bf, La) - jbar(path_f32, La))))
-    peaks, src = measured_peaks()
-    dp_avg = statistics.mean(dp_ms) / 1e3
-    tflops = cells * 2 * 128 / dp_avg / 1e12
-    peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
-    _rank0_line({
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 cost (f32 accumulate), f32 DP",
-        "data": "synthetic",
-        "config": {"workload": "pair-40000x128-vs-48000x128 gaussian frames, L2-normalised, "
-                               "warped (64 knots) + N(0,0.1)", "La": La, "Lb": Lb, "D": D,
-                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU"},
-        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
-                     "unit": "TFLOP/s", "frac": tflops / peak_tf, "traffic": None,
-                     "kernel": "k_dp_split BF16 (cost warps: mma.sync m16n8k16; DP warps FP32)",
-                     "dp_ms": 1e3 * dp_avg,
-                     "note": "cost contraction flops (2 x 128 per cell) over the DP launch; the "
-                             "launch is bound by the DP recurrence, not the tensor pipe"},
-        "precision": {"fp32_cost_step_ms": fp32_ms, "speedup_vs_fp32_cost": fp32_ms / (1e3 * t / args.steps),
-                      "total_rel_diff_vs_fp32": abs(tot_bf - tot_f32) / abs(tot_f32),
-                      "mean_path_deviation_vs_fp32_frames": dev_full,
-                      "oracle_pair": "2000x2400, same recipe",
-                      "total_rel_error_vs_fp64": abs(tb - to) / abs(to),
-                      "path_cost_rel_excess_vs_fp64": (tg - to) / abs(to),
-                      "mean_path_deviation_vs_fp64_frames": dev_frames},
-        "cpu_baseline": None,
-        "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": cap * 8 + 8},
-        # normalisation, bf16 packing of B, DP, band map, two-band map, chain, walks, emit
-        "gpu_launches": 8 * args.steps,
-        "clocks": clk.summary(),
-    })
-    al.close()
-
-
-def run_band(args):
-    """The learned-band workload: the 100000x12 vs 100000-130000x12 pair
-    (tempo 0.6-1.6, 256 knots) aligned exactly inside the band of the learned
-    encoder (dtw_align_learned, bf16 encoder, trained weights of the
-    package), against the full exact DP of the same pair on the same GPU.
-    value = full-matrix cells (La x Lb) per second of the banded alignment;
-    the speedup over the exact DP and the path deviation from the exact path
-    are reported beside it."""
-    import numpy as np
-    import torch
-    ws, rank, local = dist_env()
-    dev = torch.device("cuda", local if ws > 1 else 0)
-    from paper_2607_15478_gb300 import band_train
-    from paper_2607_15478_gb300 import build as pbuild
-    pbuild.build()
-    from paper_2607_15478_gb300 import pardtw, synth
-    wp = synth.config_pair(4, pair=rank)
-    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
-    cells = La * Lb
+    from paper_2607_15478_gb300 import band_train, pardtw, synth
+    wp = synth.config_pair(4)
+    La, Lb = wp.A.shape[0], wp.B.shape[0]
     stream = torch.cuda.Stream(device=dev)
     al = pardtw.Aligner(dev.index, stream)
     al.enable_timing(True)
@@ -763,7 +460,6 @@ def run_band(args):
     path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
     plen = torch.zeros(1, dtype=torch.int32, device=dev)
     tot = torch.zeros(1, dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     fell = []
@@ -780,36 +476,404 @@ def run_band(args):
         ev1.synchronize()
         return ev0.elapsed_time(ev1)
 
-    # the exact DP of the same pair: its path, total and time
     for _ in range(2):
         step(exact=True)
-    exact_ms = statistics.median([step(exact=True) for _ in range(max(3, args.steps // 4))])
+    exact_all = [step(exact=True) for _ in range(exact_runs)]
+    if int(plen.item()) <= 0:
+        raise RuntimeError(f"exact alignment failed: {pardtw.status_string(-int(plen.item()))}")
     p_exact = path[:int(plen.item())].cpu().numpy()
     t_exact = float(tot.item())
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     fell.clear()
     step_ms, dp_ms = [], []
     with ClockSampler(dev.index) as clk:
         torch.cuda.synchronize(dev)
         clk.mark_start()
-        for _ in range(args.steps):
+        for _ in range(steps):
             step_ms.append(step())
             dp_ms.append(al.stage_times()[1])
         clk.mark_end()
-    t = sum(step_ms) / 1e3
-    value = cells * args.steps / t / 1e9
+    if int(plen.item()) <= 0:
+        raise RuntimeError(f"banded alignment failed: {pardtw.status_string(-int(plen.item()))}")
     band_cells = al.band_cells()
     p_band = path[:int(plen.item())].cpu().numpy()
     t_band = float(tot.item())
+    exact_ms = statistics.median(exact_all)
+    band_ms = statistics.median(step_ms)
+    block = {
+        "workload": f"pair-{La}x12-vs-{Lb}x12 chroma-like, warped (256 knots, tempo 0.6-1.6)",
+        "exact_ms": exact_ms, "band_ms": band_ms, "speedup_vs_exact": exact_ms / band_ms,
+        "band_step_ms": step_stats(step_ms), "exact_step_ms": step_stats(exact_all),
+        "fell_back_steps": int(sum(fell)), "steps": steps,
+        "same_path_as_exact": bool(p_band.shape == p_exact.shape and
+                                   np.array_equal(p_band, p_exact)),
+        "mean_path_deviation_frames": mean_path_deviation(p_band, p_exact, La),
+        "total_rel_diff_vs_exact": abs(t_band - t_exact) / abs(t_exact),
+        "band_cells": band_cells, "band_fraction": band_cells / (La * Lb),
+        "exact_gcups": La * Lb / exact_ms / 1e6,
+        "weights": "paper_2607_15478_gb300/weights/band_encoder_d12.npy",
+        "timing": "CUDA events on the aligner's stream, L2 flushed before every step; "
+                  "medians over the steps",
+    }
+    extra = {"wp": wp, "al": al, "P": P, "stream": stream, "step_ms": step_ms,
+             "dp_ms": dp_ms, "clocks": clk.summary()}
+    return block, extra
 
-    def jbar(pp, n):
-        acc, cnt = np.zeros(n), np.zeros(n)
-        np.add.at(acc, pp[:, 0], pp[:, 1])
-        np.add.at(cnt, pp[:, 0], 1)
-        rows = np.flatnonzero(cnt)
-        return np.interp(np.arange(n), rows, acc[rows] / cnt[rows])
-    deviation = float(np.mean(np.abs(jbar(p_band, La) - jbar(p_exact, La))))
+
+def measure_batch(dev, steps, warmup, flush, pairs=None, want_e2e=False):
+    """The batching workload: 256 seeded pairs (La ~ U[500, 8000], Lb = La x
+    U[0.8, 1.25], D = 12) as a planned batch (dtw_batch_create: DP schedule
+    picked by the autotuner, the whole batch captured in one CUDA graph); a
+    step is one graph replay.  The same batch through dtw_align_many (no
+    graph) is timed beside it."""
+    import numpy as np
+    import torch
+    from paper_2607_15478_gb300 import pardtw, synth
+    if pairs is None:
+        pairs = synth.config_batch(2)
+    cells = sum(p.A.shape[0] * p.B.shape[0] for p in pairs)
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    # all features in one device buffer (A of every pair, then B of every
+    # pair), the pairs' inputs being views of it, so that one host-to-device
+    # copy refills a whole batch
+    sizes = [p.A.size for p in pairs] + [p.B.size for p in pairs]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    feat_h = torch.empty(int(offs[-1]), dtype=torch.float32).pin_memory()
+    for k, x in enumerate([p.A for p in pairs] + [p.B for p in pairs]):
+        feat_h[int(offs[k]):int(offs[k + 1])] = torch.from_numpy(x.reshape(-1))
+    feat = feat_h.to(dev)
+    n_p = len(pairs)
+    As = [feat[int(offs[k]):int(offs[k + 1])].view(pairs[k].A.shape) for k in range(n_p)]
+    Bs = [feat[int(offs[n_p + k]):int(offs[n_p + k + 1])].view(pairs[k].B.shape)
+          for k in range(n_p)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    st = None
+
+    def step_many():
+        nonlocal st
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            _, _, st = al.align_many(As, Bs)
+            ev1.record(stream)
+
+    many_ms, dp_ms = [], []
+    for k in range(warmup + 3):
+        step_many()
+        ev1.synchronize()
+        if k >= warmup:
+            many_ms.append(ev0.elapsed_time(ev1))
+            dp_ms.append(al.stage_times()[1])
+    if st is not None and (st != 0).any():
+        raise RuntimeError("batch alignment failed")
+    plan = al.plan_batch(As, Bs, autotune=True)
+    R_tuned, NS_tuned, tuned_ms = plan.info()
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            plan.run()
+            ev1.record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if (plan.path_len.cpu().numpy() <= 0).any():
+        raise RuntimeError("planned batch failed")
+    step_ms = []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(steps):
+            step()
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize(dev)
+        clk.mark_end()
+    graph_ms = statistics.median(step_ms)
+    block = {
+        "workload": "batch-256-pairs La~U[500,8000] Lb=La*U[0.8,1.25] D=12 chroma-like, "
+                    "warped (8 knots)" if n_p == 256 else f"batch of {n_p} pairs",
+        "pairs": n_p, "cells": cells, "graph_ms": graph_ms, "gcups": cells / graph_ms / 1e6,
+        "graph_step_ms": step_stats(step_ms), "align_many_ms": statistics.median(many_ms),
+        "align_many_dp_ms": statistics.median(dp_ms),
+        "autotune_rows_per_lane": R_tuned, "autotune_strips_per_cta": NS_tuned,
+        "autotune_ms": {f"R{r}_NS{ns}": tuned_ms[(3 if ns == 4 else 0) + r - 2]
+                        for ns in (2, 4) for r in (2, 3, 4)},
+        "timing": "CUDA events around one graph replay, L2 flushed before every step",
+    }
+    extra = {"step_ms": step_ms, "dp_ms": dp_ms, "clocks": clk.summary(), "plan": plan,
+             "al": al, "stream": stream, "feat": feat, "feat_h": feat_h}
+    if want_e2e:
+        # end to end: the batch's features copied in from pinned host memory
+        # (one copy into the plan's input buffer), the plan's graph, paths,
+        # lengths and costs copied out (one copy each), split per pair
+        paths_h = torch.empty(plan.paths.shape, dtype=torch.int32).pin_memory()
+        lens_h = torch.empty(plan.path_len.shape, dtype=torch.int32).pin_memory()
+        cost_h = torch.empty(plan.cost.shape, dtype=torch.float32).pin_memory()
+        al.enable_timing(False)
+        e2e_t = []
+        for k in range(warmup + steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                feat.copy_(feat_h, non_blocking=True)
+                plan.run()
+                paths_h.copy_(plan.paths, non_blocking=True)
+                lens_h.copy_(plan.path_len, non_blocking=True)
+                cost_h.copy_(plan.cost, non_blocking=True)
+            stream.synchronize()
+            ln = lens_h.numpy()
+            _ = [paths_h[int(plan.off[q]):int(plan.off[q]) + int(ln[q])] for q in range(n_p)]
+            e2e_t.append(time.perf_counter() - t0)
+        extra["e2e_s"] = sum(e2e_t[warmup:])
+        extra["h2d"] = int(feat_h.numel()) * 4
+        extra["d2h"] = int(paths_h.numel()) * 4 + 8 * n_p
+    return block, extra
+
+
+def measure_bf16(dev, steps, warmup, flush, fp32_runs=2):
+    """The precision workload: the 40000x128 vs 48000x128 pair with the cost
+    from bf16 features on the tensor cores (FP32 accumulate, FP32 DP), against
+    the FP32 cost path on the same GPU in the same run."""
+    import torch
+    from paper_2607_15478_gb300 import pardtw, synth
+    wp = synth.config_pair(3)
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    cells = La * Lb
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    al.enable_timing(True)
+    A = torch.from_numpy(wp.A).to(dev)
+    B = torch.from_numpy(wp.B).to(dev)
+    cap = min(La, Lb)
+    path = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    plen = torch.zeros(1, dtype=torch.int32, device=dev)
+    tot = torch.zeros(1, dtype=torch.float32, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def step(prec):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0.record(stream)
+            al.align_into(A, B, path, plen, tot, cost_precision=prec)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(warmup):
+        step(1)
+    step_ms, dp_ms = [], []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
+        for _ in range(steps):
+            step_ms.append(step(1))
+            dp_ms.append(al.stage_times()[1])
+        clk.mark_end()
+    if int(plen.item()) <= 0:
+        raise RuntimeError(f"bf16 alignment failed: {pardtw.status_string(-int(plen.item()))}")
+    tot_bf, path_bf = float(tot.item()), path[:int(plen.item())].cpu().numpy()
+    step(0)  # warm-up of the FP32 cost path
+    fp32_all, fp32_dp = [], []
+    for _ in range(fp32_runs):
+        fp32_all.append(step(0))
+        fp32_dp.append(al.stage_times()[1])
+    tot_f32, path_f32 = float(tot.item()), path[:int(plen.item())].cpu().numpy()
+    bf16_ms = statistics.median(step_ms)
+    fp32_ms = statistics.median(fp32_all)
+    block = {
+        "workload": "pair-40000x128-vs-48000x128 gaussian frames, L2-normalised, warped "
+                    "(64 knots) + N(0,0.1)",
+        "bf16_ms": bf16_ms, "bf16_gcups": cells / bf16_ms / 1e6,
+        "bf16_step_ms": step_stats(step_ms), "bf16_dp_ms": statistics.median(dp_ms),
+        "fp32_ms": fp32_ms, "fp32_gcups": cells / fp32_ms / 1e6,
+        "fp32_dp_ms": statistics.median(fp32_dp),
+        "speedup_vs_fp32_cost": fp32_ms / bf16_ms,
+        "total_rel_diff_vs_fp32": abs(tot_bf - tot_f32) / abs(tot_f32),
+        "mean_path_deviation_vs_fp32_frames": mean_path_deviation(path_bf, path_f32, La),
+        "error_vs_fp64_oracle": "tests/test_gpu_bf16.py (recorded in profiles/)",
+        "timing": "CUDA events on the aligner's stream, L2 flushed before every step",
+    }
+    extra = {"wp": wp, "al": al, "stream": stream, "step_ms": step_ms, "dp_ms": dp_ms,
+             "clocks": clk.summary(), "cells": cells}
+    return block, extra
+
+
+def nominal_peak(peaks, src):
+    clock = peaks.get("sm_max_mhz", 2070.0)
+    return (SM_COUNT * FP32_LANES_PER_SM * clock * 1e6,
+            f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {clock:.0f} MHz "
+            f"(sm_max_mhz, {src})")
+
+
+def run_batch(args):
+    """--config 2: the batching workload's own line (strong scaling: N ranks
+    split the 256 pairs by cell count, LPT, and align their shares)."""
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    if rank == 0 or ws == 1:
+        pbuild.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2607_15478_gb300 import shard, synth
+    pairs_all = synth.config_batch(2)
+    cells_all = [p.A.shape[0] * p.B.shape[0] for p in pairs_all]
+    mine = shard.partition_pairs(cells_all, ws)[rank]
+    pairs = [pairs_all[k] for k in mine]
+    cells = sum(cells_all[k] for k in mine)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if ws > 1:
+        dist.barrier()
+    block, ex = measure_batch(dev, args.steps, args.warmup, flush, pairs=pairs, want_e2e=True)
+    t_local = sum(ex["step_ms"]) / 1e3
+    t_max, t_e2e = t_local, ex["e2e_s"]
+    if ws > 1:
+        t = torch.tensor([t_local, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, t_e2e = float(t[0].item()), float(t[1].item())
+    value = sum(cells_all) * args.steps / t_max / 1e9
+    if rank == 0:
+        peaks, src = measured_peaks()
+        peak_ops, basis = nominal_peak(peaks, src)
+        dp_avg = statistics.mean(ex["dp_ms"]) / 1e3
+        achieved = cells * 18 / dp_avg
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            done = 0
+            for p in pairs_all:
+                if time.perf_counter() - t0 > 15.0:
+                    break
+                oracle.dtw(p.A, p.B)
+                done += p.A.shape[0] * p.B.shape[0]
+            dt = time.perf_counter() - t0
+            cpu = {"value": done / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the first pairs of the batch, one after another, until 15 s "
+                             f"({done / 1e9:.2f} Gcells in {dt:.1f} s), single-threaded FP64",
+                   **cpu_info()}
+        _rank0_line({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "step_ms": step_stats(ex["step_ms"]),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch-256-pairs La~U[500,8000] Lb=La*U[0.8,1.25] D=12 "
+                                   "chroma-like, warped (8 knots)",
+                       "pairs": len(pairs_all), "cells": sum(cells_all), "D": 12,
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"pairs split by cell count over {ws} rank(s)",
+                       "graph": "one CUDA graph replay per step (dtw_batch_run)",
+                       "schedule": f"autotuned: {block['autotune_rows_per_lane']} rows per "
+                                   f"lane, {block['autotune_strips_per_cta']} strips per CTA"},
+            "batch": block,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
+                         "traffic": None,
+                         "kernel": "k_dp_split, batch mode (work queue over pairs), timed "
+                                   "through dtw_align_many",
+                         "ops_per_cell": 18, "dp_ms": 1e3 * dp_avg, "peak_basis": basis},
+            "cpu_baseline": cpu,
+            "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": ex["h2d"], "d2h_bytes_per_step": ex["d2h"]},
+            # epoch bump, normalisation, DP, band map, two-band map, chain, walks, emit
+            "gpu_launches": 8 * args.steps,
+            "clocks": ex["clocks"],
+        })
+    ex["plan"].close()
+    ex["al"].close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_precision(args):
+    """--config 3: the precision workload's own line."""
+    import torch
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2607_15478_gb300 import pardtw
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    block, ex = measure_bf16(dev, args.steps, args.warmup, flush)
+    wp, al, cells = ex["wp"], ex["al"], ex["cells"]
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    cap = min(La, Lb)
+    t = sum(ex["step_ms"]) / 1e3
+    # e2e: host features in, path out
+    Ah = torch.from_numpy(wp.A).pin_memory()
+    Bh = torch.from_numpy(wp.B).pin_memory()
+    ph = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
+    lh = torch.zeros(1, dtype=torch.int32).pin_memory()
+    th = torch.zeros(1, dtype=torch.float32).pin_memory()
+    al.enable_timing(False)
+    opts = pardtw.make_options(cost_precision=1)
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pardtw.dtw_align(al.h, Ah, Bh, ph, lh, th, opts)
+        e2e_t.append(time.perf_counter() - t0)
+    t_e2e = sum(e2e_t[args.warmup:])
+    peaks, src = measured_peaks()
+    dp_avg = statistics.mean(ex["dp_ms"]) / 1e3
+    tflops = cells * 2 * 128 / dp_avg / 1e12
+    peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    _rank0_line({
+        "metric": METRIC, "value": cells * args.steps / t / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "step_ms": step_stats(ex["step_ms"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 cost (f32 accumulate), f32 DP",
+        "data": "synthetic",
+        "config": {"workload": block["workload"], "La": La, "Lb": Lb, "D": D,
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU"},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": tflops / peak_tf, "traffic": None,
+                     "kernel": "k_dp_split BF16 (cost warps: mma.sync m16n8k16; DP warps FP32)",
+                     "dp_ms": 1e3 * dp_avg,
+                     "note": "cost contraction flops (2 x 128 per cell) over the DP launch; the "
+                             "launch is bound by the DP recurrence, not the tensor pipe"},
+        "bf16": block,
+        "cpu_baseline": None,
+        "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": cap * 8 + 8},
+        # normalisation, bf16 packing of B, DP, band map, two-band map, chain, walks, emit
+        "gpu_launches": 8 * args.steps,
+        "clocks": ex["clocks"],
+    })
+    al.close()
+
+
+def run_band(args):
+    """--config 4: the learned-band workload's own line; value = full-matrix
+    cells (La x Lb) per second of the banded alignment."""
+    import torch
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    from paper_2607_15478_gb300 import build as pbuild
+    pbuild.build()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    block, ex = measure_band(dev, args.steps, args.warmup, flush,
+                             exact_runs=max(3, args.steps // 4))
+    wp, al, P, stream = ex["wp"], ex["al"], ex["P"], ex["stream"]
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    cells = La * Lb
+    t = sum(ex["step_ms"]) / 1e3
     # e2e: host features in, path out, through the public API
     Ah = torch.from_numpy(wp.A).pin_memory()
     Bh = torch.from_numpy(wp.B).pin_memory()
@@ -828,10 +892,10 @@ def run_band(args):
         e2e_t.append(time.perf_counter() - t0)
     t_e2e = sum(e2e_t[args.warmup:])
     peaks, src = measured_peaks()
-    clock = peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6
+    peak_ops, basis = nominal_peak(peaks, src)
     ops_per_cell = D + 6
-    dp_avg = statistics.mean(dp_ms) / 1e3
+    dp_avg = statistics.mean(ex["dp_ms"]) / 1e3
+    band_cells = block["band_cells"]
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -839,38 +903,32 @@ def run_band(args):
         a, b, dt = oracle_sample(wp, cells_target=3.0e8)
         cpu = {"value": a * b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"leading {a}x{b} block of the pair, single-threaded FP64 row-by-row "
-                         f"exact DTW ({dt:.1f} s)"}
+                         f"exact DTW ({dt:.1f} s)", **cpu_info()}
     _rank0_line({
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": cells * args.steps / t / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "step_ms": step_stats(ex["step_ms"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (encoder bf16)",
         "data": "synthetic",
-        "config": {"workload": f"pair-{La}x12-vs-{Lb}x12 chroma-like, warped (256 knots, tempo "
-                               f"0.6-1.6), exact DTW in the learned band",
+        "config": {"workload": block["workload"] + ", exact DTW in the learned band",
                    "La": La, "Lb": Lb, "D": D, "downsample": 8,
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU",
                    "value_definition": "La x Lb cells over the banded alignment's time"},
-        "band": {"exact_ms": exact_ms, "band_ms": 1e3 * t / args.steps,
-                 "speedup_vs_exact": exact_ms / (1e3 * t / args.steps),
-                 "fell_back_steps": int(sum(fell)), "same_path_as_exact":
-                     bool(p_band.shape == p_exact.shape and np.array_equal(p_band, p_exact)),
-                 "mean_path_deviation_frames": deviation,
-                 "total_rel_diff": abs(t_band - t_exact) / abs(t_exact),
-                 "band_cells": band_cells, "band_fraction": band_cells / cells,
-                 "weights": "paper_2607_15478_gb300/weights/band_encoder_d12.npy"},
+        "band": block,
         "roofline": {"bound": "alu", "achieved": band_cells * ops_per_cell / dp_avg / 1e12,
                      "peak": peak_ops / 1e12, "unit": "T FP32 lane-ops/s",
                      "frac": band_cells * ops_per_cell / dp_avg / peak_ops, "traffic": None,
                      "kernel": "k_dp_split over the band's strip ranges",
-                     "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
+                     "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg, "peak_basis": basis,
                      "note": "the banded DP is one chain of strips (each waits for the "
                              "bottom rows of the one above): bound by the per-column step "
                              "latency of a strip, not by a pipe"},
         "cpu_baseline": cpu,
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": int(ph.shape[0]) * 8 + 8},
+                "h2d_bytes_per_step": (La + Lb) * D * 4,
+                "d2h_bytes_per_step": int(ph.shape[0]) * 8 + 8},
         "gpu_launches": KERNELS_PER_LEARNED_STEP * args.steps,
-        "clocks": clk.summary(),
+        "clocks": ex["clocks"],
     })
     al.close()
 
@@ -990,6 +1048,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line only: skip the band, batch and bf16 blocks")
     ap.add_argument("--La", type=int, default=None,
                     help="override the pair's lengths (same recipe; for profiling smaller cases)")
     ap.add_argument("--Lb", type=int, default=None)
