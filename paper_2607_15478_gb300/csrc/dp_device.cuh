@@ -367,9 +367,10 @@ __device__ __forceinline__ float eq_as_float(float a, float b) {
 // (1,1), (1,2), (2,1) instead of 2, 3, 3 (w12 carries the (1,2) weight).
 // kT: the pair is swept transposed (rows of the kernel = frames of B), so
 // the kernel's (1,2) candidate is the problem's (2,1) and vice versa; the
-// problem's tie order (1,1), (1,2), (2,1) is then the kernel's c0, c2, c1,
-// and the field keeps the kernel's decoding: bit 1 only when c1 attains the
-// minimum and c2 does not.  Same cells, same values, same path.
+// problem's tie order (1,1), (1,2), (2,1) is then the kernel's c0, c2, c1.
+// Bit 1 then records that c2 attains the minimum (one compare, as in the
+// direct sweep), and transpose_fields turns the finished word into the
+// kernel's decoding before it is stored.  Same cells, same values, same path.
 template <int R, bool kSubseq = false, bool kT = false>
 __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, const float* w12,
                                         bool ghost, float g0, float g1, bool origin_here,
@@ -392,12 +393,7 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
         const float c2 = fmaf(w21, cost[k], x2);     // from (i-2, j-1)
         float mk = min3f(c0, c1, c2);
         fw[k] = fmaf(eq_as_float(c0, mk), bit0, fw[k]);
-        if constexpr (kT) {
-            const float e1 = eq_as_float(c1, mk);
-            fw[k] = fmaf(fmaf(-e1, eq_as_float(c2, mk), e1), bit1, fw[k]);
-        } else {
-            fw[k] = fmaf(eq_as_float(c1, mk), bit1, fw[k]);
-        }
+        fw[k] = fmaf(eq_as_float(kT ? c2 : c1, mk), bit1, fw[k]);
         if (k == 0) mk = origin_here ? cost[0] + mu : mk;  // E[0][0] = C[0][0]
         m[k] = mk;
     }
@@ -409,6 +405,15 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
         prv[k] = cur[k];
         cur[k] = m[k];
     }
+}
+
+// A word of the transposed sweep, whose bit 1 of each field says that the
+// kernel's c2 attains the minimum, in the decoding of step_of_field: where
+// bit 0 is clear (the diagonal does not attain it), the step is c2's when c2
+// attains the minimum, else c1's, so bit 1 is inverted there; where bit 0 is
+// set the step is the diagonal whatever bit 1 holds.
+__device__ __forceinline__ uint32_t transpose_fields(uint32_t w) {
+    return w ^ (~(w << 1) & 0xAAAAAAAAu);
 }
 
 // The 16 field bits a sub-chunk accumulated, as the low or high half of a

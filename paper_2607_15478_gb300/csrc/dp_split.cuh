@@ -596,6 +596,10 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             }
 
         }
+        if constexpr (kT) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] = transpose_fields(word[k]);
+        }
         store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
                            (size_t)lane * R,
                        word);
