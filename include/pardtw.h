@@ -103,7 +103,17 @@ typedef struct dtw_options {
      * Applies to the default warp-pair DP at 3 rows per lane (FP32 or BF16
      * cost); the tie order is mapped so that results do not depend on it. */
     int transpose;
+    /* DTW_CLUSTERS_AUTO (0, default): the default DP of one pair (warp pairs
+     * at 3 rows per lane, two strips per CTA) runs in thread-block clusters
+     * of up to 8 CTAs, which hand the strip border from CTA to CTA through
+     * distributed shared memory instead of global memory, when the device
+     * has room for them; DTW_CLUSTERS_NEVER (1): never.  Results do not
+     * depend on it. */
+    int clusters;
 } dtw_options;
+
+#define DTW_CLUSTERS_AUTO 0
+#define DTW_CLUSTERS_NEVER 1
 
 #define DTW_TRANSPOSE_AUTO 0
 #define DTW_TRANSPOSE_NEVER 1

@@ -100,7 +100,8 @@ struct Layout {
 // warp pair with 3 rows per lane for D <= 32, one row per lane above.
 DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
     const DpPlan one = {0, 1, kWarpsPerGroup};
-    if (o.cost_precision == DTW_COST_BF16) return {2, 3, kSplitStrips, 1};
+    const int nocl = o.clusters == DTW_CLUSTERS_NEVER ? 1 : 0;
+    if (o.cost_precision == DTW_COST_BF16) return {2, 3, kSplitStrips, 1, nocl};
     const int req = o.rows_per_lane;
     if (req == 1) return one;
     if (o.dp_schedule == DTW_SCHEDULE_FUSED) {
@@ -115,7 +116,7 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
     // of every size measured (1e5 x 1.26e5: 30.3 vs 31.5 ms; 5e4 x 6.25e4:
     // 8.32 vs 8.45 ms); batches pick theirs with the autotuner
     if (o.strips_per_cta == 4 && split_supported(dp, R, 4)) return {2, R, 4};
-    return {2, R, kSplitStrips};
+    return {2, R, kSplitStrips, 0, nocl};
 }
 
 cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int num_sms,
@@ -125,6 +126,11 @@ cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int
         case 0: return launch_dp(a, dp, num_sms, s);
         case 1: return launch_dp_multirow(a, dp, plan.R, num_sms, s);
         case 2:
+            if (!plan.no_clusters && plan.R == 3 && plan.spg == kSplitStrips) {
+                bool used = false;
+                const cudaError_t e = launch_dp_split_cl(a, dp, plan.bf16 != 0, transposed, s, &used);
+                if (e != cudaSuccess || used) return e;
+            }
             return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s, transposed)
                              : launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s, transposed);
         default: return cudaErrorInvalidValue;
@@ -264,6 +270,7 @@ dtw_options defaults() {
     o.dp_schedule = DTW_SCHEDULE_AUTO;
     o.strips_per_cta = 0;
     o.transpose = DTW_TRANSPOSE_AUTO;
+    o.clusters = DTW_CLUSTERS_AUTO;
     return o;
 }
 
@@ -289,7 +296,8 @@ int align_device(dtw_handle* h, const float* A, int La, const float* B, int Lb, 
     }
     // a band (per-strip column ranges) needs the warp-pair kernel at 3 rows
     // per lane, FP32 cost
-    const DpPlan plan = ranges ? DpPlan{2, band_rows_per_lane(padded_dim(D), o), kSplitStrips}
+    const DpPlan plan = ranges ? DpPlan{2, band_rows_per_lane(padded_dim(D), o), kSplitStrips, 0,
+                                        o.clusters == DTW_CLUSTERS_NEVER ? 1 : 0}
                                : choose_plan(La, padded_dim(D), o, h->num_sms);
     const Layout L = make_layout(La, Lb, D, plan);
     int rc = ensure_workspace(h, L.total, L.border_bytes);

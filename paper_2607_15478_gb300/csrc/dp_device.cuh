@@ -257,6 +257,69 @@ __device__ __forceinline__ int mbar_wait(unsigned bar, unsigned par, DevCtl* ctl
     return mbar_wait_slow(bar, par, ctl, timeout_ns, where);
 }
 
+// ---- thread-block clusters: between the strip groups of two CTAs of one
+// cluster the border travels through distributed shared memory.  The
+// writer warp of the CTA above copies each block of its last strip's bottom
+// rows into the staging ring of the CTA below with asynchronous stores that
+// complete a transaction count on that CTA's full barrier (armed for 64
+// bytes per use by the receiving reader warp), so no fence orders them; the
+// reader warp below, once it holds a block's values in registers, re-arms
+// the full barrier and arrives on the sender's empty barrier with a count
+// that depends on a loaded value, so the arrival cannot be performed before
+// the loads.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+// Barrier of every thread of the cluster (shared-memory accesses before it
+// are visible to the cluster after it).
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+// The shared::cluster address of local shared address `addr` in CTA `rank`.
+__device__ __forceinline__ unsigned map_rank(unsigned addr, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_u32(unsigned addr, unsigned v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Asynchronous 4-byte store into the shared memory of another CTA of the
+// cluster; completes 4 bytes of the transaction count of `remote_bar`, an
+// mbarrier of that CTA (both shared::cluster addresses).
+__device__ __forceinline__ void st_async_f32(unsigned addr, float v, unsigned remote_bar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+        "r"(__float_as_uint(v)), "r"(remote_bar)
+        : "memory");
+}
+// Arrive on a local mbarrier and expect `bytes` more transaction bytes for
+// the phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+// 0, computed from x (a register dependency on x that the compiler keeps).
+__device__ __forceinline__ unsigned zero_after(unsigned x) {
+    unsigned z;
+    asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(x));
+    return z;
+}
+// Relaxed arrival with `count` on an mbarrier of another CTA of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(unsigned remote_bar, unsigned count) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(remote_bar),
+                 "r"(count)
+                 : "memory");
+}
+
 template <int DP>
 struct BRing {
     using S = BStage<DP>;

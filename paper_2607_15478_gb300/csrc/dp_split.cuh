@@ -700,6 +700,97 @@ __device__ __forceinline__ void run_writer(const DpArgs& p, int g, int lane,
     }
 }
 
+// Cluster links.  Between two CTAs of one cluster the border goes through
+// a staging ring of kRingBlk blocks in the shared memory of the CTA below
+// (`link`, full barriers `lfull` there, empty barriers `lempty` in the CTA
+// above); the DP warps' own rings are untouched, so their sweep is the same
+// code with or without clusters.  Producer and consumer count the link's
+// uses as the blocks of the strip above's range, in order.
+
+// Writer warp of a CTA with another CTA of its cluster below: every block of
+// the last strip's range [nfirst, nsub) from ring NS into the staging ring of
+// CTA crank + 1 (lanes 0..15: value v = column v % 8 of row v / 8), each
+// value an asynchronous store completing 4 of the 64 bytes its full barrier
+// expects.
+__device__ __forceinline__ void run_link_writer(const DpArgs& p, int lane, float (*ringo)[2][kSub],
+                                                unsigned bfullo, unsigned bemptyo, unsigned rbase,
+                                                int nfirst, int nsub, unsigned link_s,
+                                                unsigned lfull_s, unsigned lempty_s,
+                                                unsigned lbase, unsigned crank) {
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    for (int n = nfirst; n < nsub; ++n) {
+        const unsigned t = rbase + (unsigned)(n - nfirst);  // use of ring NS
+        const unsigned u = lbase + (unsigned)(n - nfirst);  // use of the link
+        if (!mbar_wait(bar_at(bfullo, t % kRingBlk), use_parity(t, kRingBlk), p.ctl, p.timeout_ns,
+                       9))
+            return;
+        // the link block's previous use has been read below
+        if (!mbar_wait(bar_at(lempty_s, u % kRingBlk), use_parity(u, kRingBlk) ^ 1u, p.ctl,
+                       p.timeout_ns, 10))
+            return;
+        const float v = ringo[t % kRingBlk][row][cofs];
+        mbar_arrive(bar_at(bemptyo, t % kRingBlk));
+        if (lane < 2 * kSub)
+            st_async_f32(map_rank(link_s + (u % kRingBlk) * (2 * kSub * 4) +
+                                      (unsigned)(row * kSub + cofs) * 4u,
+                                  crank + 1),
+                         v, map_rank(bar_at(lfull_s, u % kRingBlk), crank + 1));
+    }
+}
+
+// Reader warp of a CTA with another CTA of its cluster above: ring 0 for the
+// first strip's range [nfirst, nsub) from the staging ring, which carries
+// the strip above's range [pa, pb): blocks of it before nfirst (or after
+// nsub) are consumed unread, blocks of the strip's range past pb read +inf.
+// Lane 0 re-arms a consumed block's full barrier for its next use and then
+// arrives on the sender's empty barrier, with a count that depends on the
+// value it loaded (the warp's loads of the block are one instruction).
+__device__ __forceinline__ void run_link_reader(const DpArgs& p, int lane, float (*ring0)[2][kSub],
+                                                unsigned bfull0, unsigned bempty0, unsigned rbase,
+                                                int nfirst, int nsub, int pa, int pb,
+                                                float (*link)[2][kSub], unsigned lfull_s,
+                                                unsigned lempty_s, unsigned lbase,
+                                                unsigned crank) {
+    const int cofs = lane & (kSub - 1), row = (lane >> 3) & 1;
+    auto release = [&](unsigned u, unsigned dep) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar_at(lfull_s, u % kRingBlk), 2 * kSub * 4);
+            mbar_arrive_remote_relaxed(map_rank(bar_at(lempty_s, u % kRingBlk), crank - 1),
+                                       1u + zero_after(dep));
+        }
+        __syncwarp();
+    };
+    auto skip = [&](int n) -> int {
+        const unsigned u = lbase + (unsigned)(n - pa);
+        if (!mbar_wait(bar_at(lfull_s, u % kRingBlk), use_parity(u, kRingBlk), p.ctl,
+                       p.timeout_ns, 11))
+            return 0;
+        release(u, 0u);
+        return 1;
+    };
+    for (int n = pa; n < min(nfirst, pb); ++n)
+        if (!skip(n)) return;
+    for (int n = nfirst; n < nsub; ++n) {
+        const unsigned t = rbase + (unsigned)(n - nfirst);  // use of ring 0
+        float v = INFINITY;
+        if (n >= pa && n < pb) {
+            const unsigned u = lbase + (unsigned)(n - pa);
+            if (!mbar_wait(bar_at(lfull_s, u % kRingBlk), use_parity(u, kRingBlk), p.ctl,
+                           p.timeout_ns, 11))
+                return;
+            v = link[u % kRingBlk][row][cofs];
+            release(u, __float_as_uint(v));
+        }
+        if (!mbar_wait(bar_at(bempty0, t % kRingBlk), use_parity(t, kRingBlk) ^ 1u, p.ctl,
+                       p.timeout_ns, 8))
+            return;
+        if (lane < 2 * kSub) ring0[t % kRingBlk][row][cofs] = v;
+        mbar_arrive(bar_at(bfull0, t % kRingBlk));
+    }
+    for (int n = max(pa, max(nsub, nfirst)); n < pb; ++n)
+        if (!skip(n)) return;
+}
+
 // Band-map item `item` of the pair (band-major: band item / nseg, column
 // segment item % nseg) by all NT threads of the CTA, once the strips covering
 // the band have raised their flags.  The wait (thread 0) gives up when the
@@ -763,12 +854,20 @@ __device__ __noinline__ void run_bandmap_item(const DpArgs& p, const MapArgs& m,
 // resident CTAs: the CTAs of the last round that find no group then map the
 // bands above while the last strips sweep.  The launch bounds keep as many
 // CTAs per SM as the DP alone fits (split_ctas_per_sm).
+// kCl (one pair, no band map): the kernel runs in clusters of cn CTAs that
+// take tickets together: ticket T gives CTA rank r the strip group
+// T cn + r, so the border between two of a ticket's groups goes through
+// distributed shared memory (run_link_writer, run_link_reader); only rank 0
+// reads a global border and only rank cn - 1 writes one.  A CTA leaves only
+// when its whole cluster does (no CTA's shared memory may disappear while a
+// peer can still reach it).
 template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false, bool kT = false,
-          bool kMap = false>
+          bool kMap = false, bool kCl = false>
 __global__ void __launch_bounds__((2 * NS + 2) * 32,
                                   (kMap ? split_ctas_per_sm(R, NS, DP, kBF) : 1))
     k_dp_split(const DpArgs one, const MapArgs map, const DpArgs* __restrict__ many,
                const int* __restrict__ item0, int nmany, int* ticket) {
+    static_assert(!kCl || (!kMany && !kMap && !kSubseq), "clusters sweep one plain pair");
     constexpr int kThreads = (2 * NS + 2) * 32;
     using S = BStage<DP>;
     using M = SplitSmem<DP, R, kBF>;
@@ -780,8 +879,15 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
     __shared__ __align__(8) unsigned long long bempty[NS + 1][kRingBlk];
     __shared__ __align__(16) float s_inf[2][kSub];  // +inf border block, never written after
     __shared__ int s_group, s_pair;
+    // cluster link into this CTA (staging ring, its full barriers) and out of
+    // it (the empty barriers of the staging ring of the CTA below)
+    __shared__ __align__(16) float link[kCl ? kRingBlk : 1][2][kSub];
+    __shared__ __align__(8) unsigned long long lfull[kCl ? kRingBlk : 1];
+    __shared__ __align__(8) unsigned long long lempty[kCl ? kRingBlk : 1];
     extern __shared__ __align__(128) unsigned char dyn[];  // NS * M::kStripBytes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned crank = kCl ? cluster_rank() : 0u;
+    const unsigned cn = kCl ? cluster_size() : 1u;
     const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
     const int w = role == 0 ? wid : (role == 1 ? wid - NS : 0);  // strip slot
     unsigned char* mine = dyn + (size_t)w * M::kStripBytes;
@@ -816,18 +922,49 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
                 mbar_init(smem_u32(&bfull[s][k]), s == 0 ? kWarp : 1);
                 mbar_init(smem_u32(&bempty[s][k]), kWarp);
             }
+        if (kCl) {
+            // the staging ring: a full barrier completes on the reader's
+            // arrival and 64 bytes of asynchronous stores from the CTA above
+            // (armed here for the first uses); an empty barrier (of the link
+            // to the CTA below) on one arrival of that CTA's reader
+            for (int k = 0; k < kRingBlk; ++k) {
+                mbar_init(smem_u32(&lfull[k]), 1);
+                mbar_init(smem_u32(&lempty[k]), 1);
+            }
+            if (crank > 0)
+                for (int k = 0; k < kRingBlk; ++k)
+                    mbar_arrive_expect_tx(smem_u32(&lfull[k]), 2 * kSub * 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if constexpr (kCl) cluster_sync_all();  // every CTA's barriers before any remote access
     // Lifetime sub-chunk counts of the cost rings and the border rings.
     unsigned csub[NS], rsub[NS + 1];
 #pragma unroll
     for (int s = 0; s < NS; ++s) csub[s] = 0;
 #pragma unroll
     for (int s = 0; s <= NS; ++s) rsub[s] = 0;
+    unsigned lin = 0, lout = 0;  // uses of the cluster links into and out of this CTA
 
     for (;;) {
+        if constexpr (kCl) {
+            // every warp of the cluster finished the previous ticket; rank 0
+            // takes the next one and hands it to every CTA of the cluster
+            cluster_sync_all();
+            if (crank == 0 && threadIdx.x == 0) {
+                const int T = read_status(one.ctl) != 0 ? one.ngroups
+                                                        : atomicAdd(&one.ctl->ticket, 1);
+                for (unsigned r = 0; r < cn; ++r)
+                    st_cluster_u32(map_rank(smem_u32(&s_pair), r), (unsigned)T);
+            }
+            cluster_sync_all();
+            const int T = s_pair;
+            if ((long long)T * cn >= one.ngroups) break;  // the whole cluster leaves
+            if (threadIdx.x == 0) s_group = T * (int)cn + (int)crank;
+        } else {
         __syncthreads();  // every warp finished the previous group
-        if (threadIdx.x == 0) {
+        }
+        if (!kCl && threadIdx.x == 0) {
             if (kMany) {
                 // item t -> (pair, group): the last pair whose first item is <= t
                 const int t = atomicAdd(ticket, 1);
@@ -861,6 +998,7 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
         if (kMany && s_group < 0) continue;  // nothing of a failed pair runs
         const DpArgs p = kMany ? many[s_pair] : one;
         const int g = s_group;
+        if (kCl && g >= p.ngroups) continue;  // this CTA's group of the ticket does not exist
         if (g >= p.ngroups) {
             if constexpr (kMap) {
                 if (g - p.ngroups < map.nbm) {
@@ -899,13 +1037,27 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
                 // the first strip's blocks; the strip above (last of the group
                 // above) published its own range's columns
                 const int2 above = strip_range(p, g * NS - 1);
-                run_reader(p, g, lane, ring[0], smem_u32(&bfull[0][0]), smem_u32(&bempty[0][0]),
-                           rsub[0], rgs[0].x, rgs[0].y, above.x * kSub, above.y * kSub);
+                if (kCl && crank > 0)
+                    run_link_reader(p, lane, ring[0], smem_u32(&bfull[0][0]),
+                                    smem_u32(&bempty[0][0]), rsub[0], rgs[0].x, rgs[0].y, above.x,
+                                    above.y, link, smem_u32(&lfull[0]), smem_u32(&lempty[0]), lin,
+                                    crank);
+                else
+                    run_reader(p, g, lane, ring[0], smem_u32(&bfull[0][0]),
+                               smem_u32(&bempty[0][0]), rsub[0], rgs[0].x, rgs[0].y,
+                               above.x * kSub, above.y * kSub);
             }
         } else {
-            if (gr.writer)
-                run_writer(p, g, lane, ring[NS], smem_u32(&bfull[NS][0]),
-                           smem_u32(&bempty[NS][0]), rsub[NS], rgs[NS - 1].x, rgs[NS - 1].y);
+            if (gr.writer) {
+                if (kCl && crank + 1 < cn)
+                    run_link_writer(p, lane, ring[NS], smem_u32(&bfull[NS][0]),
+                                    smem_u32(&bempty[NS][0]), rsub[NS], rgs[NS - 1].x,
+                                    rgs[NS - 1].y, smem_u32(&link[0][0][0]), smem_u32(&lfull[0]),
+                                    smem_u32(&lempty[0]), lout, crank);
+                else
+                    run_writer(p, g, lane, ring[NS], smem_u32(&bfull[NS][0]),
+                               smem_u32(&bempty[NS][0]), rsub[NS], rgs[NS - 1].x, rgs[NS - 1].y);
+            }
         }
         // ring uses of this group, in blocks of 8 columns: a cost ring the
         // strip's range; ring 0 the first strip's range; ring w (1 <= w < NS)
@@ -914,10 +1066,16 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
         for (int q = 0; q < NS; ++q)
             if (q < gr.nstrips_here) csub[q] += (unsigned)(rgs[q].y - rgs[q].x);
         if (ring_used<NS>(gr, 0)) rsub[0] += (unsigned)(rgs[0].y - rgs[0].x);
+        if (kCl && crank > 0 && gr.reader) {  // the link carries the strip above's range
+            const int2 above = strip_range(p, g * NS - 1);
+            lin += (unsigned)(above.y - above.x);
+        }
+        if (kCl && crank + 1 < cn && gr.writer) lout += (unsigned)(rgs[NS - 1].y - rgs[NS - 1].x);
 #pragma unroll
         for (int q = 1; q <= NS; ++q)
             if (ring_used<NS>(gr, q)) rsub[q] += (unsigned)(rgs[q - 1].y - rgs[q - 1].x);
     }
+    if constexpr (kCl) cluster_sync_all();  // no peer reaches this CTA's shared memory any more
 }
 
 template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = false,

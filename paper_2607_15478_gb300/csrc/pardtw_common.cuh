@@ -146,6 +146,13 @@ bool split_supported(int dp, int R, int ns = 2);
 // tensor cores (mma.sync m16n8k16): D padded to 64 or 128, R = 3.
 cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStream_t s,
                                  bool transposed = false);
+// The warp-pair DP of one pair at 3 rows per lane and two strips per CTA,
+// run in thread-block clusters whose CTAs pass the strip border through
+// distributed shared memory (dp_split_cl.cu; dp <= 32, or 64 / 128 with
+// bf16).  *used = false (and nothing launched) when no cluster
+// configuration fits this device.
+cudaError_t launch_dp_split_cl(const DpArgs& a, int dp, bool bf16, bool transposed,
+                               cudaStream_t s, bool* used);
 bool split_bf16_supported(int dp);
 // B normalised and stored as bf16 for the BF16 cost: Lb_pad frames of
 // kBfStride elements (features beyond D and frames beyond Lb are zero).
@@ -165,6 +172,7 @@ cudaError_t launch_dp_split_many(const DpArgs* many, const int* item0, int n, in
 struct DpPlan {
     int kind, R, spg;
     int bf16;  // kind 2 only: the cost on the tensor cores from BF16 features
+    int no_clusters;  // kind 2, R = 3, two strips: 1 = never run in thread-block clusters
 };
 DpPlan choose_plan(int La, int dp, const dtw_options& o, int num_sms);
 // Whether a pair is swept transposed (B's frames as rows): B longer than A

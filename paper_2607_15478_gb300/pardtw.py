@@ -60,9 +60,11 @@ class Options(ctypes.Structure):
     _fields_ = [("cost_precision", ctypes.c_int), ("cost_shift", ctypes.c_float),
                 ("wait_limit", ctypes.c_int), ("debug_skip_publish", ctypes.c_int),
                 ("rows_per_lane", ctypes.c_int), ("dp_schedule", ctypes.c_int),
-                ("strips_per_cta", ctypes.c_int), ("transpose", ctypes.c_int)]
+                ("strips_per_cta", ctypes.c_int), ("transpose", ctypes.c_int),
+                ("clusters", ctypes.c_int)]
 
 SCHEDULE_AUTO, SCHEDULE_FUSED, SCHEDULE_SPLIT = 0, 1, 2
+CLUSTERS_AUTO, CLUSTERS_NEVER = 0, 1
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -130,7 +132,7 @@ def status_string(status: int) -> str:
 def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
                  debug_skip_publish: int = -1, rows_per_lane: int = 0,
                  dp_schedule: int = SCHEDULE_AUTO, cost_precision: int = DTW_COST_FP32,
-                 strips_per_cta: int = 0, transpose: int = 0) -> Options:
+                 strips_per_cta: int = 0, transpose: int = 0, clusters: int = 0) -> Options:
     o = Options()
     load_library().dtw_default_options(ctypes.byref(o))
     o.cost_precision = int(cost_precision)
@@ -141,6 +143,7 @@ def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
     o.dp_schedule = int(dp_schedule)
     o.strips_per_cta = int(strips_per_cta)
     o.transpose = int(transpose)
+    o.clusters = int(clusters)
     return o
 
 
