@@ -499,12 +499,40 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
             const unsigned t = csub + (unsigned)(n - rg.x);
 
-            // border rows top-2, top-1 of columns js .. js+7 (the group's top
+            // The three waits of a sub-chunk -- the border rows top-2, top-1
+            // of columns js .. js+7 from the ring above (the group's top
             // border is +inf in group 0, and so are the columns the strip
-            // above did not sweep: block 0 of ring 0 holds +inf)
+            // above did not sweep: the +inf block inf_blk), every 4 blocks the
+            // output ring (the consumer empties it in order, so once the
+            // previous use of block to+3 is consumed so are those of to ..
+            // to+2), and the costs (the cost warp runs up to kCostSlots
+            // sub-chunks ahead, so they are normally there) -- are first
+            // tested together without blocking, so that their latencies
+            // overlap; only a barrier not yet complete is waited for.
             const bool have_in = from_ring && n < rp.y;
-            if (have_in && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk),
-                                      p.ctl, p.timeout_ns, 1))
+            const bool need_out = to_ring && ((n - rg.x) & 3) == 0;
+            const bool need_cost = n > rg.x;
+            const unsigned tl = to + 3u;
+            const int rb = have_in ? mbar_test_wait(bar_at(bfull_in, ti % kRingBlk),
+                                                    use_parity(ti, kRingBlk))
+                                   : 1;
+            const int ro = need_out ? mbar_test_wait(bar_at(bempty_out, tl % kRingBlk),
+                                                     use_parity(tl, kRingBlk) ^ 1u)
+                                    : 1;
+            const int rc = need_cost ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
+                                                      use_parity(t, kCostSlots))
+                                     : 1;
+            if (!__all_sync(kFull, rb) &&
+                !mbar_wait_slow(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                                p.timeout_ns, 1))
+                return;
+            if (!__all_sync(kFull, ro) &&
+                !mbar_wait_slow(bar_at(bempty_out, tl % kRingBlk), use_parity(tl, kRingBlk) ^ 1u,
+                                p.ctl, p.timeout_ns, 2))
+                return;
+            if (!__all_sync(kFull, rc) &&
+                !mbar_wait_slow(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
+                                p.timeout_ns, 7))
                 return;
             float gv0[kSub], gv1[kSub];
             {
@@ -516,28 +544,12 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                 gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
                 gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
             }
+            // this sub-chunk's costs (loaded here rather than half-way through
+            // the previous sub-chunk keeps the 8 steps below one straight-line
+            // block: measured 8% faster)
+            if (need_cost) load_costs<R, kRM>(cring, t, lane, c);
             if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
-            // the output blocks must have been read below: the consumer
-            // empties them in order, so once the previous use of block to+3
-            // is consumed so are those of to .. to+2 (one wait per 4 blocks)
-            if (to_ring && ((n - rg.x) & 3) == 0) {
-                const unsigned tl = to + 3u;
-                if (!mbar_wait(bar_at(bempty_out, tl % kRingBlk), use_parity(tl, kRingBlk) ^ 1u,
-                               p.ctl, p.timeout_ns, 2))
-                    return;
-            }
-
-            // this sub-chunk's costs (the cost warp runs up to kCostSlots
-            // sub-chunks ahead, so they are normally there; loading them here
-            // rather than half-way through the previous sub-chunk keeps the 8
-            // steps below one straight-line block: measured 8% faster)
-            if (n > rg.x) {
-                if (!mbar_wait(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
-                               p.timeout_ns, 7))
-                    return;
-                load_costs<R, kRM>(cring, t, lane, c);
-                mbar_arrive(bar_at(cempty, t % kCostSlots));
-            }
+            if (need_cost) mbar_arrive(bar_at(cempty, t % kCostSlots));
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
             float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
             (void)ol;
