@@ -199,7 +199,7 @@ class ClockSampler:
 
 
 DP_SOURCES = ("paper_2607_15478_gb300/csrc/dp_split.cuh", "paper_2607_15478_gb300/csrc/dp_split.cu",
-              "paper_2607_15478_gb300/csrc/dp_device.cuh")
+              "paper_2607_15478_gb300/csrc/dp_split_cl.cu", "paper_2607_15478_gb300/csrc/dp_device.cuh")
 
 
 def dp_sources_sha256():
@@ -405,7 +405,9 @@ def run_ours(args):
                          "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
                          "traffic": traffic,
                          "kernel": "k_dp_split (column-sweep DP: per strip a cost warp and a DP "
-                                   "warp, cost on the fly)",
+                                   "warp, cost on the fly; thread-block clusters, the strip "
+                                   "border between CTAs of a cluster in distributed shared "
+                                   "memory)",
                          "ops_per_cell": ops_per_cell, "dp_ms": 1e3 * dp_avg,
                          "dp_launch_ms": step_stats(dp_ms),
                          "peak_basis": "FFMA rate measured in this run (dtw_fp32_peak: every SM "
