@@ -81,8 +81,9 @@ typedef struct dtw_options {
     int debug_skip_publish;
     /* Rows of A each GPU lane sweeps (1, 2, 3 or 4); 0 = chosen from La, D
      * and the SM count.  Results do not depend on it (it only changes the
-     * work decomposition); D > 32 runs with 1, and a value the chosen
-     * schedule does not support falls back to 1. */
+     * work decomposition); 32 < D <= 128 runs with 3 (two cost warps per
+     * strip) or 1, and a value the chosen schedule does not support falls
+     * back to 1. */
     int rows_per_lane;
     /* Division of labour of the DP for rows_per_lane >= 2: DTW_SCHEDULE_AUTO
      * (0, the default: cost/DP warp pairs), DTW_SCHEDULE_FUSED (1: one warp

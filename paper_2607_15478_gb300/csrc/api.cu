@@ -110,6 +110,8 @@ DpPlan pardtw::choose_plan(int La, int dp, const dtw_options& o, int num_sms) {
         return one;
     }
     const int R = req == 0 ? 3 : req;
+    // D = 64, 128: the warp pairs with two cost warps per strip, 3 rows per lane
+    if (split_wide_supported(dp)) return R == 3 ? DpPlan{2, 3, kSplitStrips, 0, nocl} : one;
     if (!split_supported(dp, R)) return one;
     // two strips per CTA unless asked for four: with the DP warp's costs
     // loaded at the start of each sub-chunk, two beat four on single pairs
@@ -131,8 +133,9 @@ cudaError_t pardtw::launch_plan(const DpPlan& plan, const DpArgs& a, int dp, int
                 const cudaError_t e = launch_dp_split_cl(a, dp, plan.bf16 != 0, transposed, s, &used);
                 if (e != cudaSuccess || used) return e;
             }
-            return plan.bf16 ? launch_dp_split_bf16(a, dp, num_sms, s, transposed)
-                             : launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s, transposed);
+            if (plan.bf16) return launch_dp_split_bf16(a, dp, num_sms, s, transposed);
+            if (split_wide_supported(dp)) return launch_dp_split_wide(a, dp, num_sms, s, transposed);
+            return launch_dp_split(a, dp, plan.R, plan.spg, num_sms, s, transposed);
         default: return cudaErrorInvalidValue;
     }
 }

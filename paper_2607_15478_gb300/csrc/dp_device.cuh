@@ -158,11 +158,13 @@ __device__ __forceinline__ int refill_top(float (*blk)[kSub], int js, int lane, 
 // bulk copies (cp.async.bulk) with one mbarrier per slot.  Block t of a warp's lifetime sits in slot
 // t % kSlots; its mbarrier phase parity is (t / kSlots) & 1.  A copy is
 // issued three blocks ahead of use, so the L2 latency never meets the
-// sweep.  Only lane 0 issues; all lanes wait on the barrier.
-template <int DP>
+// sweep.  Only lane 0 issues; all lanes wait on the barrier.  (The wide
+// FP32 cost warps of dp_split.cuh use rings of two slots: a copy one block
+// ahead, each block a whole 16-frame chunk.)
+template <int DP, int kSlotsT = 4>
 struct BStage {
     static constexpr int kBlk = DP <= 16 ? 64 : (DP <= 32 ? 32 : 16);  // frames per copy
-    static constexpr int kSlots = 4;
+    static constexpr int kSlots = kSlotsT;
     static constexpr int kAhead = kSlots - 1;
     static constexpr int kWarpBytes = kSlots * kBlk * DP * 4;
 };
@@ -320,9 +322,9 @@ __device__ __forceinline__ void mbar_arrive_remote_relaxed(unsigned remote_bar, 
                  : "memory");
 }
 
-template <int DP>
+template <int DP, int kSlotsT = 4>
 struct BRing {
-    using S = BStage<DP>;
+    using S = BStage<DP, kSlotsT>;
     const float* stage;   // this warp's kSlots * kBlk frames
     unsigned stage_s;     // its shared address
     unsigned bar_s;       // shared address of this warp's kSlots mbarriers

@@ -64,15 +64,37 @@ struct CostRingRM {
 constexpr int kBfSlots = 4;
 constexpr int kBfBlkBytes = kColsPerWord * kBfStride * 2;
 
+// FP32 cost for D > 32 ("wide"): -a^ of the lane's R rows no longer fits in
+// registers, so the strip's rows of A^ sit in shared memory (rows padded by 4
+// floats: the 16-byte loads of rows 3l + k of a warp fall in distinct bank
+// groups), and two cost warps share a strip, each computing 4 of the 8
+// columns of a sub-chunk.
+template <int DP, bool kBF>
+struct CostWide {
+    static constexpr bool kOn = DP > 32 && !kBF;
+    static constexpr int kNC = kOn ? 2 : 1;  // cost warps per strip
+    static constexpr int kStride = DP + 4;   // floats per row of the A tile
+    static constexpr int kBSlots = 2;        // chunks of B in each cost warp's ring
+};
 template <int DP, int R, bool kBF>
 struct SplitSmem {
-    // per strip slot: the cost warp's operands (B stage, or A tile and B
-    // stage), then the cost ring
+    // per strip slot: the cost warp's operands (B stage; A tile and B stage
+    // for the BF16 cost; A tile for the wide FP32 cost), then the cost ring
     static constexpr int kOperandBytes =
-        kBF ? 32 * R * kBfStride * 2 + kBfSlots * kBfBlkBytes : BStage<DP>::kWarpBytes;
+        kBF ? 32 * R * kBfStride * 2 + kBfSlots * kBfBlkBytes
+            : (CostWide<DP, kBF>::kOn
+                   ? 32 * R * CostWide<DP, kBF>::kStride * 4 +
+                         2 * BStage<DP, CostWide<DP, kBF>::kBSlots>::kWarpBytes
+                   : BStage<DP>::kWarpBytes);
     static constexpr int kStripBytes =
         kOperandBytes + (kBF ? CostRingRM<R>::kBytes : CostRing<R>::kBytes);
 };
+// Threads of a CTA of NS strips: per strip the cost warp(s) and a DP warp,
+// plus the reader and the writer.
+template <int DP, int NS, bool kBF>
+__host__ __device__ constexpr int split_threads() {
+    return ((CostWide<DP, kBF>::kNC + 1) * NS + 2) * 32;
+}
 
 // Barrier `slot` of an array of 8-byte mbarriers, and the phase parity a
 // waiter for the t-th (lifetime) use of a ring of n slots expects.
@@ -172,6 +194,119 @@ __device__ __forceinline__ void run_cost(const DpArgs& p, int strip, int lane, u
                     c[k][7] = fmaf(na[k][d], b1.w, c[k][7]);
                 }
             }
+        }
+        const unsigned dst = cring + slot * CR::kSlotBytes + (unsigned)lane * 16u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            sts128(dst + (unsigned)(2 * k) * (kWarp * 16),
+                   make_float4(c[k][0], c[k][1], c[k][2], c[k][3]));
+            sts128(dst + (unsigned)(2 * k + 1) * (kWarp * 16),
+                   make_float4(c[k][4], c[k][5], c[k][6], c[k][7]));
+        }
+        mbar_arrive(bar_at(cfull, slot));
+    }
+    br.drain();
+}
+
+// Cost warp `half` (0 or 1) of `strip` for D > 32, FP32: every other
+// sub-chunk of the strip (the (n - first)-th for n - first = half mod 2), all
+// 8 columns, C' = (1 - mu) - a^_i . b^_j with one FMA per feature in feature
+// order (the values of every other decomposition).  A^ of the strip comes
+// from the A tile in shared memory (`tile`, 32 R rows of kStride floats),
+// which the two cost warps of the strip load together at the strip's start
+// (named barrier 1 + w), and is reused for 8 columns per load; B^ from the
+// warp's own ring of two 16-frame chunks in shared memory, filled by bulk
+// copies one chunk ahead (B^ through L1 instead ran at L2 latency, ~1100
+// cycles per column; 4 columns per warp and sub-chunk, at 426).  A slot of
+// the cost ring is written by one warp, as in the narrow kernel.
+template <int DP, int R>
+__device__ __forceinline__ void run_cost_wide(const DpArgs& p, int strip, int w, int half,
+                                              int lane, float* tile, unsigned cring,
+                                              unsigned cfull, unsigned cempty, unsigned csub,
+                                              BRing<DP, CostWide<DP, false>::kBSlots>& br) {
+    using W = CostWide<DP, false>;
+    using S = BStage<DP, W::kBSlots>;
+    using CR = CostRing<R>;
+    constexpr int kRows = 31 * R;
+    constexpr int kS = W::kStride;
+    static_assert(S::kBlk == 2 * kSub, "one chunk of B per sub-chunk pair");
+    const bool ghost = lane == kGhostLane;
+    // the strip's rows of A^ (ghost rows zero) into the tile, 16 bytes a lane
+    {
+        const int tid = half * kWarp + lane;
+        for (int e = tid; e < 32 * R * (DP / 4); e += 2 * kWarp) {
+            const int r = e / (DP / 4), q = e - r * (DP / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < kRows)
+                v = __ldg(reinterpret_cast<const float4*>(p.Ahat + (size_t)(strip * kRows + r) * DP) + q);
+            *reinterpret_cast<float4*>(tile + r * kS + 4 * q) = v;
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + w), "r"(2 * kWarp) : "memory");
+    }
+    const float kc = ghost ? kGhostCost : p.kcost;
+    const int Lb_pad = p.nchunk * kColsPerWord;
+    const int2 rg = strip_range(p, strip);  // rg.x even: sub-chunk pairs are chunks
+    const float* arow = tile + (lane * R) * kS;
+    const int n0 = rg.x + half;
+    const int q0 = n0 * kSub / S::kBlk;
+    br.begin(q0, min((rg.y * kSub + S::kBlk - 1) / S::kBlk, (Lb_pad + S::kBlk - 1) / S::kBlk));
+    br.top_up(q0, p.Bhat, Lb_pad, lane);
+    for (int n = n0; n < rg.y; n += 2) {
+        const int js = n * kSub;
+        const int q = js / S::kBlk;
+        if (!br.wait(q, p.ctl, p.timeout_ns)) break;
+        br.top_up(q, p.Bhat, Lb_pad, lane);
+        // feature d of the sub-chunk's 8 frames: 32 bytes at bsrc + 64 d
+        const unsigned bsrc = br.chunk_s(js >> 4) + (unsigned)(js & 15) * 4u;
+        const unsigned t = csub + (unsigned)(n - rg.x);
+        const unsigned slot = t % kCostSlots;
+        // the DP warp has read this slot's previous contents
+        if (!mbar_wait(bar_at(cempty, slot), use_parity(t, kCostSlots) ^ 1u, p.ctl, p.timeout_ns,
+                       6))
+            break;
+        float c[R][kSub];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int f = 0; f < kSub; ++f) c[k][f] = kc;
+        // per group of 4 features: R rows of A^ (one 16-byte load each) and
+        // the 8 frames of 4 features of B^ (two 16-byte loads each); two
+        // buffers, the next group's loads issued before this group's FMAs
+        float4 a0[R], b0[8], a1[R], b1[8];
+        auto load = [&](int g, float4* a, float4* b) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) a[k] = *reinterpret_cast<const float4*>(arow + k * kS + 4 * g);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                b[2 * e] = lds128(bsrc + (unsigned)(4 * g + e) * 64u);
+                b[2 * e + 1] = lds128(bsrc + (unsigned)(4 * g + e) * 64u + 16u);
+            }
+        };
+        auto fmas = [&](const float4* a, const float4* b) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 u = b[2 * e], v = b[2 * e + 1];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const float x = e == 0 ? a[k].x : (e == 1 ? a[k].y : (e == 2 ? a[k].z : a[k].w));
+                    c[k][0] = fmaf(-x, u.x, c[k][0]);
+                    c[k][1] = fmaf(-x, u.y, c[k][1]);
+                    c[k][2] = fmaf(-x, u.z, c[k][2]);
+                    c[k][3] = fmaf(-x, u.w, c[k][3]);
+                    c[k][4] = fmaf(-x, v.x, c[k][4]);
+                    c[k][5] = fmaf(-x, v.y, c[k][5]);
+                    c[k][6] = fmaf(-x, v.z, c[k][6]);
+                    c[k][7] = fmaf(-x, v.w, c[k][7]);
+                }
+            }
+        };
+        load(0, a0, b0);
+#pragma unroll 1
+        for (int g = 0; g < DP / 4; g += 2) {
+            load(g + 1, a1, b1);
+            fmas(a0, b0);
+            if (g + 2 < DP / 4) load(g + 2, a0, b0);
+            fmas(a1, b1);
         }
         const unsigned dst = cring + slot * CR::kSlotBytes + (unsigned)lane * 16u;
 #pragma unroll
@@ -875,16 +1010,18 @@ __device__ __noinline__ void run_bandmap_item(const DpArgs& p, const MapArgs& m,
 // peer can still reach it).
 template <int DP, int R, int NS, bool kMany, bool kBF, bool kSubseq = false, bool kT = false,
           bool kMap = false, bool kCl = false>
-__global__ void __launch_bounds__((2 * NS + 2) * 32,
+__global__ void __launch_bounds__(split_threads<DP, NS, kBF>(),
                                   (kMap ? split_ctas_per_sm(R, NS, DP, kBF) : 1))
     k_dp_split(const DpArgs one, const MapArgs map, const DpArgs* __restrict__ many,
                const int* __restrict__ item0, int nmany, int* ticket) {
     static_assert(!kCl || (!kMany && !kMap && !kSubseq), "clusters sweep one plain pair");
-    constexpr int kThreads = (2 * NS + 2) * 32;
+    constexpr int kThreads = split_threads<DP, NS, kBF>();
+    constexpr int kNC = CostWide<DP, kBF>::kNC;  // cost warps per strip
+    constexpr bool kWide = CostWide<DP, kBF>::kOn;
     using S = BStage<DP>;
     using M = SplitSmem<DP, R, kBF>;
     __shared__ __align__(16) float ring[NS + 1][kRingBlk][2][kSub];
-    __shared__ __align__(8) unsigned long long bbar[NS][S::kSlots];
+    __shared__ __align__(8) unsigned long long bbar[NS * kNC][S::kSlots];
     __shared__ __align__(8) unsigned long long cfull[NS][kCostSlots];
     __shared__ __align__(8) unsigned long long cempty[NS][kCostSlots];
     __shared__ __align__(8) unsigned long long bfull[NS + 1][kRingBlk];
@@ -900,8 +1037,12 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned crank = kCl ? cluster_rank() : 0u;
     const unsigned cn = kCl ? cluster_size() : 1u;
-    const int role = wid < NS ? 0 : (wid < 2 * NS ? 1 : (wid == 2 * NS ? 2 : 3));
-    const int w = role == 0 ? wid : (role == 1 ? wid - NS : 0);  // strip slot
+    // warps 0 .. kNC NS - 1: cost warps (strip slot wid % NS, half wid / NS);
+    // then one DP warp per strip, the reader and the writer
+    const int role = wid < kNC * NS ? 0
+                                    : (wid < (kNC + 1) * NS ? 1 : (wid == (kNC + 1) * NS ? 2 : 3));
+    const int w = role == 0 ? wid % NS : (role == 1 ? wid - kNC * NS : 0);  // strip slot
+    const int half = role == 0 ? wid / NS : 0;
     unsigned char* mine = dyn + (size_t)w * M::kStripBytes;
     const unsigned cring_s = smem_u32(mine + M::kOperandBytes);
     const unsigned a_s = smem_u32(mine);                                  // kBF: A tile
@@ -918,12 +1059,23 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
     br.first = 0;
     br.nblk = 0;
     br.issued = br.waited = 0;
+    // the wide FP32 cost warps: A tile, then a B ring per half (two chunks)
+    using WS = BStage<DP, CostWide<DP, kBF>::kBSlots>;
+    BRing<DP, CostWide<DP, kBF>::kBSlots> bw;
+    bw.stage_s = smem_u32(mine + 32 * R * CostWide<DP, kBF>::kStride * 4 + half * WS::kWarpBytes);
+    bw.stage = reinterpret_cast<const float*>(mine);  // (unused by the wide cost warp)
+    bw.bar_s = smem_u32(&bbar[half * NS + w][0]);
+    bw.base = 0;
+    bw.first = 0;
+    bw.nblk = 0;
+    bw.issued = bw.waited = 0;
     if (threadIdx.x < 2 * kSub) (&s_inf[0][0])[threadIdx.x] = INFINITY;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
+        for (int s = 0; s < NS * kNC; ++s)
             for (int k = 0; k < S::kSlots; ++k) mbar_init(smem_u32(&bbar[s][k]), 1);
+        for (int s = 0; s < NS; ++s) {
             for (int k = 0; k < kCostSlots; ++k) {
-                mbar_init(smem_u32(&cfull[s][k]), kWarp);   // the cost warp's lanes
+                mbar_init(smem_u32(&cfull[s][k]), kWarp);  // the lanes of the slot's cost warp
                 mbar_init(smem_u32(&cempty[s][k]), kWarp);  // the DP warp's lanes
             }
         }
@@ -1035,6 +1187,9 @@ __global__ void __launch_bounds__((2 * NS + 2) * 32,
                 if constexpr (kBF)
                     run_cost_bf16<DP, R>(p, strip, lane, a_s, b_s, smem_u32(&bbar[w][0]), bbase,
                                          cring_s, cfull_s, cempty_s, csub[w]);
+                else if constexpr (kWide)
+                    run_cost_wide<DP, R>(p, strip, w, half, lane, reinterpret_cast<float*>(mine),
+                                         cring_s, cfull_s, cempty_s, csub[w], bw);
                 else
                     run_cost<DP, R>(p, strip, lane, cring_s, cfull_s, cempty_s, csub[w], br);
             }
@@ -1095,7 +1250,7 @@ template <int DP, int R, int NS, bool kMany, bool kBF = false, bool kSubseq = fa
 cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int n, int items,
                      int* ticket, int num_sms, cudaStream_t s, const MapArgs* map = nullptr) {
     static_assert(!kMap || (!kMany && !kSubseq), "the band map runs with one pair");
-    constexpr int kThreads = (2 * NS + 2) * 32;
+    constexpr int kThreads = split_threads<DP, NS, kBF>();
     const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
     auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq, kT, kMap>;
     static int blocks_per_sm = 0;

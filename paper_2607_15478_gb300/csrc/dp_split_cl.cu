@@ -1,128 +1,9 @@
-// Warp-pair DP of one pair in thread-block clusters (k_dp_split<..., kCl>,
-// see dp_split.cuh).  Between two CTAs the strip border otherwise goes
-// through global memory: the writer warp of the CTA above stores it, the
-// reader warp of the CTA below polls it, and each hop costs about 3 us
-// (measured on the 20000 x 25000 pair: 0.48 us from strip to strip inside a
-// CTA, 3.0 us from CTA to CTA, 22% of the DP time).  In a cluster the last
-// DP warp of a CTA writes straight into ring 0 of the next CTA's shared
-// memory, so only one hop in cn stays global.
-//
-// Every CTA of a cluster sits on an SM of its own (the dynamic shared
-// memory is raised so that two CTAs cannot share an SM, which would put two
-// DP warps on one SM sub-partition).  The cluster size is the largest of 8,
-// 4, 2 whose resident clusters hold every strip group of the pair at once;
-// a pair with more groups (a long band) runs persistent clusters of 8.
-#include <mutex>
-
-#include "dp_split.cuh"
+// Instantiations of the cluster DP (dp_split_cl.cuh) for the FP32 cost at
+// D <= 32 and the BF16 cost at D = 64, 128; the FP32 cost at D = 64, 128 is
+// in dp_split_wide.cu.
+#include "dp_split_cl.cuh"
 
 namespace pardtw {
-namespace {
-
-constexpr int kClSmemFloor = 120 * 1024;  // > half an SM's shared memory: one CTA per SM
-constexpr int kClMaxDev = 64;
-constexpr int kClSizes[3] = {8, 4, 2};
-
-template <int DP, bool kBF, bool kT>
-struct ClKernel {
-    static constexpr int R = 3, NS = 2;
-    static constexpr int kThreads = (2 * NS + 2) * 32;
-    static constexpr auto kern() { return k_dp_split<DP, R, NS, false, kBF, false, kT, false, true>; }
-    static int smem() {
-        return std::max(NS * SplitSmem<DP, R, kBF>::kStripBytes, kClSmemFloor);
-    }
-};
-
-struct ClInfo {
-    bool ready = false, ok = false;
-    int max_clusters[3] = {0, 0, 0};  // resident clusters of size kClSizes[k]
-};
-
-cudaLaunchConfig_t cl_config(dim3 grid, int threads, int smem, cudaStream_t s,
-                             cudaLaunchAttribute* at, int cn) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = (size_t)smem;
-    cfg.stream = s;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cn;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
-// Attributes and cluster occupancy of one instantiation, once per device.
-template <int DP, bool kBF, bool kT>
-const ClInfo& cl_info(int dev) {
-    static ClInfo info[kClMaxDev];
-    static std::mutex mu;
-    using K = ClKernel<DP, kBF, kT>;
-    std::lock_guard<std::mutex> lock(mu);
-    ClInfo& ci = info[dev];
-    if (ci.ready) return ci;
-    ci.ready = true;
-    auto* kern = K::kern();
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::smem()) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return ci;
-    }
-    for (int k = 0; k < 3; ++k) {
-        cudaLaunchAttribute at[1];
-        cudaLaunchConfig_t cfg =
-            cl_config(dim3((unsigned)kClSizes[k]), K::kThreads, K::smem(), nullptr, at, kClSizes[k]);
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
-            (void)cudaGetLastError();
-            n = 0;
-        }
-        ci.max_clusters[k] = n;
-    }
-    ci.ok = true;
-    return ci;
-}
-
-template <int DP, bool kBF, bool kT>
-cudaError_t launch_cl(const DpArgs& a, cudaStream_t s, bool* used) {
-    *used = false;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kClMaxDev) {
-        (void)cudaGetLastError();
-        return cudaSuccess;
-    }
-    const ClInfo& ci = cl_info<DP, kBF, kT>(dev);
-    if (!ci.ok) return cudaSuccess;
-    int cn = 0, nclusters = 0;
-    // one wave: the largest cluster size whose resident clusters hold every group
-    for (int k = 0; k < 3 && cn == 0; ++k) {
-        const int need = (a.ngroups + kClSizes[k] - 1) / kClSizes[k];
-        if (ci.max_clusters[k] >= need) {
-            cn = kClSizes[k];
-            nclusters = need;
-        }
-    }
-    // several waves: persistent clusters of 8
-    if (cn == 0 && ci.max_clusters[0] > 0) {
-        cn = kClSizes[0];
-        nclusters = ci.max_clusters[0];
-    }
-    if (cn == 0) return cudaSuccess;
-    using K = ClKernel<DP, kBF, kT>;
-    cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg =
-        cl_config(dim3((unsigned)(nclusters * cn)), K::kThreads, K::smem(), s, at, cn);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, K::kern(), a, MapArgs{},
-                                             static_cast<const DpArgs*>(nullptr),
-                                             static_cast<const int*>(nullptr), 1,
-                                             static_cast<int*>(nullptr));
-    if (e == cudaSuccess) *used = true;
-    return e;
-}
-
-}  // namespace
 
 cudaError_t launch_dp_split_cl(const DpArgs& a, int dp, bool bf16, bool transposed,
                                cudaStream_t s, bool* used) {
@@ -142,6 +23,8 @@ cudaError_t launch_dp_split_cl(const DpArgs& a, int dp, bool bf16, bool transpos
         case 12: return transposed ? launch_cl<12, false, true>(a, s, used) : launch_cl<12, false, false>(a, s, used);
         case 16: return transposed ? launch_cl<16, false, true>(a, s, used) : launch_cl<16, false, false>(a, s, used);
         case 32: return transposed ? launch_cl<32, false, true>(a, s, used) : launch_cl<32, false, false>(a, s, used);
+        case 64:
+        case 128: return launch_dp_split_wide_cl(a, dp, transposed, s, used);
         default: return cudaSuccess;
     }
 }

@@ -153,6 +153,14 @@ cudaError_t launch_dp_split_bf16(const DpArgs& a, int dp, int num_sms, cudaStrea
 // configuration fits this device.
 cudaError_t launch_dp_split_cl(const DpArgs& a, int dp, bool bf16, bool transposed,
                                cudaStream_t s, bool* used);
+// The warp-pair DP with the FP32 cost at D = 64, 128 (dp_split_wide.cu): two
+// cost warps per strip, 3 rows per lane, two strips per CTA; the same in
+// thread-block clusters.
+bool split_wide_supported(int dp);
+cudaError_t launch_dp_split_wide(const DpArgs& a, int dp, int num_sms, cudaStream_t s,
+                                 bool transposed = false);
+cudaError_t launch_dp_split_wide_cl(const DpArgs& a, int dp, bool transposed, cudaStream_t s,
+                                    bool* used);
 bool split_bf16_supported(int dp);
 // B normalised and stored as bf16 for the BF16 cost: Lb_pad frames of
 // kBfStride elements (features beyond D and frames beyond Lb are zero).

@@ -360,3 +360,41 @@ def test_band_map_inside_dp_kernel_variants(aligner, case):
     np.testing.assert_array_equal(p0, p1.cpu().numpy())
     assert t0 == t1
     assert_parity(wp.A, wp.B, p0, t0, name="multi-wave")
+
+
+# D = 64, 128 with the FP32 cost: the warp pairs with two cost warps per
+# strip (the strip's rows of A^ in shared memory, 4 of the 8 columns of a
+# sub-chunk each) keep one FMA per feature in feature order, so every cell
+# equals that of the one-row-per-lane kernel bit for bit, in either sweep
+# direction and with or without thread-block clusters.
+@pytest.mark.parametrize("La,Lb,D", [(300, 360, 64), (700, 900, 128), (2000, 1700, 100),
+                                     (3100, 3600, 128)])
+def test_wide_features_equal_one_row_per_lane(aligner, La, Lb, D):
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(57, La + D), La, Lb, D, kind="gaussian", knots=8,
+                           tmin=0.6, tmax=1.6, sigma=0.1)
+    A, B = dev(wp.A), dev(wp.B)
+    p_ref, t_ref = aligner.align(A, B, rows_per_lane=1)
+    p_ref = p_ref.cpu().numpy()
+    for tr in (pardtw.TRANSPOSE_NEVER, pardtw.TRANSPOSE_ALWAYS):
+        for cl in (pardtw.CLUSTERS_AUTO, pardtw.CLUSTERS_NEVER):
+            p, t = aligner.align(A, B, transpose=tr, clusters=cl)
+            np.testing.assert_array_equal(p.cpu().numpy(), p_ref, err_msg=f"tr={tr} cl={cl}")
+            assert t == t_ref, (tr, cl)
+    assert_parity(wp.A, wp.B, p_ref, t_ref, name="wide-fp32")
+
+
+def test_wide_features_multi_wave(aligner):
+    # 30000 rows swept directly at D = 64: 162 strip groups, more than one
+    # wave of CTAs (persistent clusters take several tickets each)
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(58, 30000), 30000, 16000, 64, kind="gaussian",
+                           knots=64, tmin=1.3, tmax=2.2, sigma=0.1)
+    A, B = dev(wp.A), dev(wp.B)
+    p0, t0 = aligner.align(A, B, transpose=pardtw.TRANSPOSE_NEVER)
+    p1, t1 = aligner.align(A, B, transpose=pardtw.TRANSPOSE_NEVER, clusters=pardtw.CLUSTERS_NEVER)
+    p2, t2 = aligner.align(A, B, rows_per_lane=1)
+    np.testing.assert_array_equal(p0.cpu().numpy(), p1.cpu().numpy())
+    np.testing.assert_array_equal(p0.cpu().numpy(), p2.cpu().numpy())
+    assert t0 == t1 == t2
+    assert_parity(wp.A, wp.B, p0, t0, name="wide-fp32-multi-wave")
