@@ -641,13 +641,13 @@ def measure_batch(dev, steps, warmup, flush, pairs=None, want_e2e=False):
     return block, extra
 
 
-def measure_bf16(dev, steps, warmup, flush, fp32_runs=2):
+def measure_bf16(dev, steps, warmup, flush, fp32_runs=2, La=None, Lb=None):
     """The precision workload: the 40000x128 vs 48000x128 pair with the cost
     from bf16 features on the tensor cores (FP32 accumulate, FP32 DP), against
     the FP32 cost path on the same GPU in the same run."""
     import torch
     from paper_2607_15478_gb300 import pardtw, synth
-    wp = synth.config_pair(3)
+    wp = synth.config_pair(3, La=La, Lb=Lb)
     La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
     cells = La * Lb
     stream = torch.cuda.Stream(device=dev)
@@ -693,7 +693,7 @@ def measure_bf16(dev, steps, warmup, flush, fp32_runs=2):
     bf16_ms = statistics.median(step_ms)
     fp32_ms = statistics.median(fp32_all)
     block = {
-        "workload": "pair-40000x128-vs-48000x128 gaussian frames, L2-normalised, warped "
+        "workload": f"pair-{La}x128-vs-{Lb}x128 gaussian frames, L2-normalised, warped "
                     "(64 knots) + N(0,0.1)",
         "bf16_ms": bf16_ms, "bf16_gcups": cells / bf16_ms / 1e6,
         "bf16_step_ms": step_stats(step_ms), "bf16_dp_ms": statistics.median(dp_ms),
@@ -813,7 +813,7 @@ def run_precision(args):
     pbuild.build()
     from paper_2607_15478_gb300 import pardtw
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    block, ex = measure_bf16(dev, args.steps, args.warmup, flush)
+    block, ex = measure_bf16(dev, args.steps, args.warmup, flush, La=args.La, Lb=args.Lb)
     wp, al, cells = ex["wp"], ex["al"], ex["cells"]
     La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
     cap = min(La, Lb)
