@@ -146,11 +146,15 @@ int dtw_destroy(dtw_handle* h);
 /* Rebind the handle to another stream (later calls are ordered on it). */
 int dtw_set_stream(dtw_handle* h, void* cuda_stream);
 
-/* Upper bound on the bytes of device workspace dtw_align needs for
- * (La, Lb, D) (Sec. VI-D's memory model: the 2-bit backtrace matrix
- * dominates, La*Lb/4 bytes plus at most 7% padding, plus border rows
- * between strip groups, La*Lb/8 bytes at most, plus O((La+Lb)*D)).
- * Errors: DTW_ERR_INVALID. */
+/* Bytes of device workspace dtw_align needs for (La, Lb, D) with the
+ * options `opt` (NULL = defaults), for either orientation of the sweep
+ * (Sec. VI-D's memory model: the 2-bit backtrace matrix dominates, La*Lb/4
+ * bytes plus 3% padding at 3 rows per lane (7% at 1); plus the tagged
+ * border rows between strip groups, 16 bytes per column and group of two
+ * 93-row strips (La*Lb/11.6 bytes; La*Lb/7.5 at 1 row per lane); plus the
+ * parallel backtrace's band maps, 12 bytes per column and 128 rows
+ * (La*Lb/10.7 bytes); plus O((La+Lb)*D)).  About 0.44 bytes per cell with
+ * the default options.  Errors: DTW_ERR_INVALID, DTW_ERR_UNSUPPORTED. */
 int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes);
 
 /* ---- cost matrix (Sec. IV cosine distance; Sec. VI-B explicit matrix) ---- */

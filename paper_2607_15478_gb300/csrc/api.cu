@@ -711,19 +711,20 @@ int dtw_set_stream(dtw_handle* h, void* cuda_stream) {
 }
 
 int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes) {
-    (void)opt;
     if (!bytes || La < 1 || Lb < 1 || D < 1) return DTW_ERR_INVALID;
-    if (padded_dim(D) == 0) return DTW_ERR_UNSUPPORTED;
+    const int dp = padded_dim(D);
+    if (dp == 0) return DTW_ERR_UNSUPPORTED;
+    const dtw_options o = opt ? *opt : defaults();
     size_t most = 0;
-    const DpPlan plans[] = {{0, 1, kWarpsPerGroup}, {1, 2, kWarpsPerGroup},
-                            {1, 4, kWarpsPerGroup}, {2, 2, kSplitStrips},
-                            {2, 3, kSplitStrips},   {2, 4, kSplitStrips},
-                            {2, 3, kSplitStrips, 1}};
-    for (const DpPlan& plan : plans)
-        for (int t = 0; t < 2; ++t) {  // either orientation of the sweep
-            const Layout L = t ? make_layout(Lb, La, D, plan) : make_layout(La, Lb, D, plan);
-            most = std::max(most, L.total + L.border_bytes);
-        }
+    for (int t = 0; t < 2; ++t) {  // either orientation of the sweep
+        const int rows = t ? Lb : La, cols = t ? La : Lb;
+        // the plan dtw_align takes (the SM count only decides between plans
+        // of the same layout)
+        const DpPlan plan = choose_plan(rows, dp, o, 152);
+        const Layout L = make_layout(rows, cols, D, plan);
+        // a pair swept in several waves of CTAs also keeps one flag per strip
+        most = std::max(most, L.total + L.border_bytes + align256((size_t)L.nstrips * 4));
+    }
     // and a host path staged after the layout
     *bytes = most + align256((size_t)2 * std::min(La, Lb) * sizeof(int32_t));
     return DTW_OK;

@@ -147,9 +147,10 @@ def make_options(cost_shift: float = 0.0, wait_limit_us: int = 0,
     return o
 
 
-def workspace_size(La: int, Lb: int, D: int) -> int:
+def workspace_size(La: int, Lb: int, D: int, options: Options | None = None) -> int:
     n = ctypes.c_size_t(0)
-    rc = load_library().dtw_workspace_size(La, Lb, D, None, ctypes.byref(n))
+    rc = load_library().dtw_workspace_size(La, Lb, D, ctypes.byref(options) if options else None,
+                                           ctypes.byref(n))
     if rc != DTW_OK:
         raise PardtwError(rc, "dtw_workspace_size")
     return n.value

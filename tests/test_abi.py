@@ -51,23 +51,59 @@ def test_default_options(lib):
     assert o.cost_shift == 0.0 and o.debug_skip_publish == -1
 
 
+def _layout_bytes(rows, cols, rps, words, spg):
+    """The dominant buffers of one sweep orientation: 2-bit fields (words per
+    strip and 16-column chunk), tagged border rows (16 B per column and
+    group of spg strips), band maps of the parallel backtrace (8 B per column
+    per 128-row band, again for every other band)."""
+    nstrips = -(-rows // rps)
+    bp = nstrips * words * -(-cols // 16) * 4
+    border = -(-nstrips // spg) * cols * 16
+    nbands = -(-rows // 128)
+    maps = (nbands + ((nbands - 2) // 2 if nbands >= 4 else 0)) * cols * 8
+    return bp + border + maps
+
+
 def test_workspace_size_follows_memory_model(lib):
-    # Sec. VI-D: the 2-bit backtrace matrix (L^2 / 4 bytes) plus O(L) buffers;
-    # here also the tagged border rows between strip groups (16 B per column
-    # per group of 4 strips) and the band entry maps of the parallel
-    # backtrace (8 B per column per band of 128 rows, and again for every
-    # other band: the two-band map).  The bound is the largest layout (one
-    # row per lane: strips of 30 rows, 32 words).
+    # Sec. VI-D: the 2-bit backtrace matrix (L^2 / 4 bytes) plus O(L)
+    # buffers; here also the tagged border rows between strip groups and the
+    # band entry maps of the parallel backtrace.  Default options: 3 rows per
+    # lane (93-row strips, 96 words), two strips per CTA; either orientation
+    # of the sweep.
     for La, Lb in [(1000, 1200), (20000, 25000), (100000, 130000)]:
         n = pardtw.workspace_size(La, Lb, 12)
-        bp = -(-La // 30) * 32 * -(-Lb // 16) * 16 / 4
-        border = -(-(-(-La // 30)) // 4) * Lb * 16
-        nbands = -(-La // 128)
-        maps = (nbands + (max(nbands - 2, 0) // 2 if nbands >= 4 else 0)) * Lb * 8
-        extra = bp + border + maps
+        extra = max(_layout_bytes(La, Lb, 93, 96, 2), _layout_bytes(Lb, La, 93, 96, 2))
         assert extra <= n <= extra * 1.01 + 64 * (La + Lb) * 12
+        # about 0.44 bytes per cell
+        if La >= 20000:
+            assert 0.43 <= n / (La * Lb) <= 0.45
+    # one row per lane (30-row strips of 32 words, four strips per CTA)
+    n1 = pardtw.workspace_size(20000, 25000, 12, pardtw.make_options(rows_per_lane=1))
+    extra = max(_layout_bytes(20000, 25000, 30, 32, 4), _layout_bytes(25000, 20000, 30, 32, 4))
+    assert extra <= n1 <= extra * 1.01 + 64 * 45000 * 12
     with pytest.raises(pardtw.PardtwError):
         pardtw.workspace_size(0, 10, 12)
+
+
+def test_largest_square_pair_on_gb300(lib):
+    # Sec. VI-D sizes the longest pair by the memory the 2-bit matrix takes:
+    # L_max = 2^16 sqrt(T) for T GB (1.10e6 frames for the 280 GB of a GB300
+    # that a process can use).  With the border rows and band maps this
+    # library needs 0.44 bytes per cell: the largest square pair is ~0.8e6
+    # frames (0.73 of the paper's bound), found here by bisection on
+    # dtw_workspace_size.
+    budget = 280e9
+    lo, hi = 1000, 2_000_000
+    while hi - lo > 1000:
+        mid = (lo + hi) // 2
+        if pardtw.workspace_size(mid, mid, 12) <= budget:
+            lo = mid
+        else:
+            hi = mid
+    paper = 2 ** 16 * (280.0 ** 0.5)
+    assert 790_000 <= lo <= 810_000, lo
+    assert 0.71 <= lo / paper <= 0.75
+    assert pardtw.workspace_size(lo, lo, 12) <= budget < pardtw.workspace_size(lo + 1000, lo + 1000, 12)
 
 
 def test_workspace_size_rejects_unsupported_dim(lib):
