@@ -553,13 +553,101 @@ __device__ __forceinline__ float pick_row(const float* cur, int k) {
     return v;
 }
 
+// The two border rows of a ring block (8 columns each) into registers.
+__device__ __forceinline__ void load_border(unsigned s, float* g0, float* g1) {
+    const float4 a0 = lds128(s), a1 = lds128(s + 16);
+    const float4 b0 = lds128(s + 32), b1 = lds128(s + 48);
+    g0[0] = a0.x; g0[1] = a0.y; g0[2] = a0.z; g0[3] = a0.w;
+    g0[4] = a1.x; g0[5] = a1.y; g0[6] = a1.z; g0[7] = a1.w;
+    g1[0] = b0.x; g1[1] = b0.y; g1[2] = b0.z; g1[3] = b0.w;
+    g1[4] = b1.x; g1[5] = b1.y; g1[6] = b1.z; g1[7] = b1.w;
+}
+// The strip's two bottom rows of a sub-chunk into a ring block.
+__device__ __forceinline__ void store_border(unsigned d, const float* o0, const float* o1) {
+    sts128(d, make_float4(o0[0], o0[1], o0[2], o0[3]));
+    sts128(d + 16, make_float4(o0[4], o0[5], o0[6], o0[7]));
+    sts128(d + 32, make_float4(o1[0], o1[1], o1[2], o1[3]));
+    sts128(d + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
+}
+// Subsequence DP: row La-1 of the nsteps columns at dst.
+__device__ __forceinline__ void store_lastrow(float* dst, int nsteps, const float* ol) {
+    if (nsteps == kSub) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(ol[0], ol[1], ol[2], ol[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(ol[4], ol[5], ol[6], ol[7]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kSub; ++u)
+            if (u < nsteps) dst[u] = ol[u];
+    }
+}
+// The 8 DP steps of a full sub-chunk.
+template <int R, bool kSubseq, bool kT>
+__device__ __forceinline__ void sweep_full(const float (*c)[kSub], const float* g0, const float* g1,
+                                           bool first_col, bool is_origin, int srcA,
+                                           const float* w12, bool ghost, float mu, float* cur,
+                                           float* prv, float& ylp, float* fw, float* o0, float* o1,
+                                           float* ol, int kl) {
+#pragma unroll
+    for (int u = 0; u < kSub; ++u) {
+        float cu[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+        dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, g0[u], g1[u],
+                                (kSubseq || (first_col && u == 0)) && is_origin, mu, cur, prv, ylp,
+                                fw, o0[u], o1[u]);
+        if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+    }
+}
+
+// The DP steps of one sub-chunk (nsteps <= 8 columns; the cell of the first
+// column of the sweep is the origin when first_col and is_origin hold).
+template <int R, bool kSubseq, bool kT>
+__device__ __forceinline__ void sweep_sub(const float (*c)[kSub], const float* g0, const float* g1,
+                                          int nsteps, bool first_col, bool is_origin, int srcA,
+                                          const float* w12, bool ghost, float mu, float* cur,
+                                          float* prv, float& ylp, float* fw, float* o0, float* o1,
+                                          float* ol, int kl) {
+    if (nsteps == kSub) {
+#pragma unroll
+        for (int u = 0; u < kSub; ++u) {
+            float cu[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+            dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, g0[u], g1[u],
+                                    (kSubseq || (first_col && u == 0)) && is_origin, mu, cur, prv,
+                                    ylp, fw, o0[u], o1[u]);
+            if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kSub; ++u) {
+            if (u >= nsteps) break;
+            float cu[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+            dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, g0[u], g1[u],
+                                    (kSubseq || (first_col && u == 0)) && is_origin, mu, cur, prv,
+                                    ylp, fw, o0[u], o1[u]);
+            if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+        }
+    }
+}
+
 // DP warp of `strip` (slot w of group g).  ring: the NS + 1 border rings;
 // bfull / bempty: their mbarriers (kRingBlk per ring); rin / rout: lifetime
 // sub-chunk counts of the input and output rings at the start of this
 // group; csub: that of the cost ring.
 // kFlag: the strip raises its flag in done[strip] when its words are stored
 // (one pair with the band map inside the kernel).
-template <int R, int NS, bool kRM, bool kSubseq = false, bool kT = false, bool kFlag = false>
+// kWords: a trip of the sweep takes a whole backpointer word (two sub-chunks,
+// one set of barrier tests, loads and arrivals for 16 columns) instead of
+// one sub-chunk; kTwoCost: two cost warps fill alternate cost slots.  Taken
+// where the DP warp alone sets the pace (BF16 cost: 12% faster at D = 128)
+// and not for the FP32 cost at D <= 32, where the trip of a sub-chunk was
+// faster on GB300 (the strip below waits for a whole word of the border, and
+// the per-column work did not shrink).
+template <int R, int NS, bool kRM, bool kSubseq = false, bool kT = false, bool kFlag = false,
+          bool kWords = false, bool kTwoCost = false>
 __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, int w, int strip,
                                        int lane, float (*ring)[kRingBlk][2][kSub], unsigned bfull,
                                        unsigned bempty, unsigned rin, unsigned rout,
@@ -604,61 +692,49 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
         }
 
-    // costs of the first sub-chunk
-    float c[R][kSub];
-    if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
-                   p.timeout_ns, 7))
-        return;
-    load_costs<R, kRM>(cring, csub, lane, c);
-    mbar_arrive(bar_at(cempty, csub % kCostSlots));
-
     float cur[R], prv[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) cur[k] = prv[k] = INFINITY;
     float ylp = INFINITY;
     // (no poll of the failure flag in the sweep: every wait checks it on its
     // slow path, and a warp that never waits ends with its strip)
-    const int jend = min(rg.y * kSub, Lb);
-    for (int j0 = rg.x * kSub; j0 < jend; j0 += kColsPerWord) {
-        uint32_t word[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) word[k] = 0;
-        // the two sub-chunks of a backpointer word: not unrolled (half the
-        // code of the sweep loop; measured 4-5% faster on a long pair)
-#pragma unroll 1
-        for (int h = 0; h < kColsPerWord / kSub; ++h) {
-            const int js = j0 + h * kSub;
-            if (js >= jend) break;
-            const int n = js / kSub;
-            const int nsteps = min(kSub, Lb - js);
+    if constexpr (kWords) {
+        const int jend = min(rg.y * kSub, Lb);
+        // whole words first (16 full columns), then the last, ragged word
+        uint32_t tailw[R];
+        const int jfull = rg.x * kSub + ((jend - rg.x * kSub) / kColsPerWord) * kColsPerWord;
+        for (int j0 = rg.x * kSub; j0 < jfull; j0 += kColsPerWord) {
+            // One backpointer word per trip: sub-chunks n (even; ranges start on
+            // whole words) and n + 1.
+            const int n = j0 / kSub;
+            constexpr bool two = true;
             const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
             const unsigned t = csub + (unsigned)(n - rg.x);
+            const bool in0 = from_ring && n < rp.y;
+            const bool in1 = two && from_ring && n + 1 < rp.y;
 
-            // The three waits of a sub-chunk -- the border rows top-2, top-1
-            // of columns js .. js+7 from the ring above (the group's top
-            // border is +inf in group 0, and so are the columns the strip
-            // above did not sweep: the +inf block inf_blk), every 4 blocks the
-            // output ring (the consumer empties it in order, so once the
-            // previous use of block to+3 is consumed so are those of to ..
-            // to+2), and the costs (the cost warp runs up to kCostSlots
-            // sub-chunks ahead, so they are normally there) -- are first
-            // tested together without blocking, so that their latencies
-            // overlap; only a barrier not yet complete is waited for.
-            const bool have_in = from_ring && n < rp.y;
+            // The waits of the word, first tested together without blocking: the
+            // border blocks from the ring above (the producer publishes them in
+            // order, so the second one's barrier implies the first's; columns the
+            // strip above did not sweep are +inf), every other word the output
+            // ring (its consumer empties it in order, so once the previous use of
+            // block to+3 is consumed so are those of to .. to+2), and the cost
+            // slots (filled in order by one cost warp; with two cost warps, which
+            // take alternate slots, both are tested).
             const bool need_out = to_ring && ((n - rg.x) & 3) == 0;
-            const bool need_cost = n > rg.x;
-            const unsigned tl = to + 3u;
-            const int rb = have_in ? mbar_test_wait(bar_at(bfull_in, ti % kRingBlk),
-                                                    use_parity(ti, kRingBlk))
-                                   : 1;
+            const unsigned tl = to + 3u, tb = in1 ? ti + 1u : ti, tc = two ? t + 1u : t;
+            const int rb = in0 ? mbar_test_wait(bar_at(bfull_in, tb % kRingBlk),
+                                                 use_parity(tb, kRingBlk))
+                               : 1;
             const int ro = need_out ? mbar_test_wait(bar_at(bempty_out, tl % kRingBlk),
                                                      use_parity(tl, kRingBlk) ^ 1u)
                                     : 1;
-            const int rc = need_cost ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
-                                                      use_parity(t, kCostSlots))
-                                     : 1;
+            const int rc = mbar_test_wait(bar_at(cfull, tc % kCostSlots), use_parity(tc, kCostSlots));
+            const int rc0 = (kTwoCost && two) ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
+                                                               use_parity(t, kCostSlots))
+                                              : 1;
             if (!__all_sync(kFull, rb) &&
-                !mbar_wait_slow(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                !mbar_wait_slow(bar_at(bfull_in, tb % kRingBlk), use_parity(tb, kRingBlk), p.ctl,
                                 p.timeout_ns, 1))
                 return;
             if (!__all_sync(kFull, ro) &&
@@ -666,90 +742,264 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                                 p.ctl, p.timeout_ns, 2))
                 return;
             if (!__all_sync(kFull, rc) &&
+                !mbar_wait_slow(bar_at(cfull, tc % kCostSlots), use_parity(tc, kCostSlots), p.ctl,
+                                p.timeout_ns, 7))
+                return;
+            if (kTwoCost && !__all_sync(kFull, rc0) &&
                 !mbar_wait_slow(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
                                 p.timeout_ns, 7))
                 return;
-            float gv0[kSub], gv1[kSub];
-            {
-                const unsigned s0 = have_in ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk;
-                const float4 a0 = lds128(s0), a1 = lds128(s0 + 16);
-                const float4 b0 = lds128(s0 + 32), b1 = lds128(s0 + 48);
-                gv0[0] = a0.x; gv0[1] = a0.y; gv0[2] = a0.z; gv0[3] = a0.w;
-                gv0[4] = a1.x; gv0[5] = a1.y; gv0[6] = a1.z; gv0[7] = a1.w;
-                gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
-                gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
-            }
-            // this sub-chunk's costs (loaded here rather than half-way through
-            // the previous sub-chunk keeps the 8 steps below one straight-line
-            // block: measured 8% faster)
-            if (need_cost) load_costs<R, kRM>(cring, t, lane, c);
-            if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
-            if (need_cost) mbar_arrive(bar_at(cempty, t % kCostSlots));
+            float gA0[kSub], gA1[kSub], gB0[kSub], gB1[kSub];
+            load_border(in0 ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk, gA0, gA1);
+            load_border(in1 ? smem_u32(&myring[(ti + 1u) % kRingBlk][0][0]) : inf_blk, gB0, gB1);
+            float cA[R][kSub], cB[R][kSub];
+            load_costs<R, kRM>(cring, t, lane, cA);
+            if (two) load_costs<R, kRM>(cring, t + 1u, lane, cB);
+            if (in0) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+            if (in1) mbar_arrive(bar_at(bempty_in, (ti + 1u) % kRingBlk));
+            mbar_arrive(bar_at(cempty, t % kCostSlots));
+            if (two) mbar_arrive(bar_at(cempty, (t + 1u) % kCostSlots));
+
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
             float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
             (void)ol;
-            float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
+            float fw[R];  // backpointer fields of a sub-chunk, bits 2u, 2u+1
+            uint32_t word[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) fw[k] = 0.0f;
-            if (nsteps == kSub) {
+            sweep_full<R, kSubseq, kT>(cA, gA0, gA1, j0 == 0, is_origin, srcA, w12, ghost, mu, cur,
+                                       prv, ylp, fw, o0, o1, ol, kl);
+            if constexpr (kSubseq)
+                if (has_last) store_lastrow(p.lastrow + j0, kSub, ol);
 #pragma unroll
-                for (int u = 0; u < kSub; ++u) {
-                    float cu[R];
-#pragma unroll
-                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
-                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
-                                            is_origin,
-                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
-                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
-                }
-            } else {
-                // the last, partial sub-chunk
-#pragma unroll
-                for (int u = 0; u < kSub; ++u) {
-                    if (u >= nsteps) break;
-                    float cu[R];
-#pragma unroll
-                    for (int k = 0; k < R; ++k) cu[k] = c[k][u];
-                    dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
-                                        (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
-                                            is_origin,
-                                        mu, cur, prv, ylp, fw, o0[u], o1[u]);
-                    if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
-                }
-            }
-            if constexpr (kSubseq) {
-                if (has_last) {  // row La-1 of these columns
-                    float* dst = p.lastrow + js;
-                    if (nsteps == kSub) {
-                        reinterpret_cast<float4*>(dst)[0] = make_float4(ol[0], ol[1], ol[2], ol[3]);
-                        reinterpret_cast<float4*>(dst)[1] = make_float4(ol[4], ol[5], ol[6], ol[7]);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < kSub; ++u)
-                            if (u < nsteps) dst[u] = ol[u];
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], h);
+            for (int k = 0; k < R; ++k) word[k] = field_bits(fw[k], 0);
             if (to_ring && lane == kOutLane) {
-                const unsigned d0 = smem_u32(&nextring[to % kRingBlk][0][0]);
-                sts128(d0, make_float4(o0[0], o0[1], o0[2], o0[3]));
-                sts128(d0 + 16, make_float4(o0[4], o0[5], o0[6], o0[7]));
-                sts128(d0 + 32, make_float4(o1[0], o1[1], o1[2], o1[3]));
-                sts128(d0 + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
+                store_border(smem_u32(&nextring[to % kRingBlk][0][0]), o0, o1);
                 mbar_arrive(bar_at(bfull_out, to % kRingBlk));
             }
-
-        }
-        if constexpr (kT) {
+            if (two) {
 #pragma unroll
-            for (int k = 0; k < R; ++k) word[k] = transpose_fields(word[k]);
+                for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+                sweep_full<R, kSubseq, kT>(cB, gB0, gB1, false, is_origin, srcA, w12, ghost, mu, cur,
+                                           prv, ylp, fw, o0, o1, ol, kl);
+                if constexpr (kSubseq)
+                    if (has_last) store_lastrow(p.lastrow + j0 + kSub, kSub, ol);
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], 1);
+                if (to_ring && lane == kOutLane) {
+                    store_border(smem_u32(&nextring[(to + 1u) % kRingBlk][0][0]), o0, o1);
+                    mbar_arrive(bar_at(bfull_out, (to + 1u) % kRingBlk));
+                }
+            }
+            if constexpr (kT) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] = transpose_fields(word[k]);
+            }
+            store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
+                               (size_t)lane * R,
+                           word);
         }
-        store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
-                           (size_t)lane * R,
-                       word);
+        // the last, ragged word: its one or two sub-chunks one at a time
+        for (int js = jfull; js < jend; js += kSub) {
+            const int n = js / kSub;
+            const int nsteps = min(kSub, Lb - js);
+            const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
+            const unsigned t = csub + (unsigned)(n - rg.x);
+            const bool have_in = from_ring && n < rp.y;
+            const bool need_out = to_ring && ((n - rg.x) & 3) == 0;
+            const unsigned tl = to + 3u;
+            if (have_in && !mbar_wait(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                                      p.timeout_ns, 1))
+                return;
+            if (need_out && !mbar_wait(bar_at(bempty_out, tl % kRingBlk),
+                                       use_parity(tl, kRingBlk) ^ 1u, p.ctl, p.timeout_ns, 2))
+                return;
+            if (!mbar_wait(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
+                           p.timeout_ns, 7))
+                return;
+            float g0[kSub], g1[kSub], c[R][kSub];
+            load_border(have_in ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk, g0, g1);
+            load_costs<R, kRM>(cring, t, lane, c);
+            if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+            mbar_arrive(bar_at(cempty, t % kCostSlots));
+            float o0[kSub], o1[kSub], ol[kSub], fw[R];
+            (void)ol;
+#pragma unroll
+            for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+            sweep_sub<R, kSubseq, kT>(c, g0, g1, nsteps, js == 0, is_origin, srcA, w12, ghost, mu, cur,
+                                      prv, ylp, fw, o0, o1, ol, kl);
+            if constexpr (kSubseq)
+                if (has_last) store_lastrow(p.lastrow + js, nsteps, ol);
+            if (to_ring && lane == kOutLane) {
+                store_border(smem_u32(&nextring[to % kRingBlk][0][0]), o0, o1);
+                mbar_arrive(bar_at(bfull_out, to % kRingBlk));
+            }
+            // the word's fields: the first sub-chunk's are the low half
+            const int h = (js / kSub) & 1;
+            uint32_t word[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] = field_bits(fw[k], h);
+            if (h == 0) {
+                // keep the low half for the second sub-chunk, if there is one
+                if (js + kSub < jend) {
+#pragma unroll
+                    for (int k = 0; k < R; ++k) tailw[k] = word[k];
+                    continue;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] |= tailw[k];
+            }
+            if constexpr (kT) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] = transpose_fields(word[k]);
+            }
+            store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(js >> 4)) * (32 * R) +
+                               (size_t)lane * R,
+                           word);
+        }
+    } else {
+        // costs of the first sub-chunk
+        float c[R][kSub];
+        if (!mbar_wait(bar_at(cfull, csub % kCostSlots), use_parity(csub, kCostSlots), p.ctl,
+                       p.timeout_ns, 7))
+            return;
+        load_costs<R, kRM>(cring, csub, lane, c);
+        mbar_arrive(bar_at(cempty, csub % kCostSlots));
+
+        const int jend = min(rg.y * kSub, Lb);
+        for (int j0 = rg.x * kSub; j0 < jend; j0 += kColsPerWord) {
+            uint32_t word[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) word[k] = 0;
+            // the two sub-chunks of a backpointer word: not unrolled (half the
+            // code of the sweep loop; measured 4-5% faster on a long pair)
+#pragma unroll 1
+            for (int h = 0; h < kColsPerWord / kSub; ++h) {
+                const int js = j0 + h * kSub;
+                if (js >= jend) break;
+                const int n = js / kSub;
+                const int nsteps = min(kSub, Lb - js);
+                const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
+                const unsigned t = csub + (unsigned)(n - rg.x);
+
+                // The three waits of a sub-chunk -- the border rows top-2, top-1
+                // of columns js .. js+7 from the ring above (the group's top
+                // border is +inf in group 0, and so are the columns the strip
+                // above did not sweep: the +inf block inf_blk), every 4 blocks the
+                // output ring (the consumer empties it in order, so once the
+                // previous use of block to+3 is consumed so are those of to ..
+                // to+2), and the costs (the cost warp runs up to kCostSlots
+                // sub-chunks ahead, so they are normally there) -- are first
+                // tested together without blocking, so that their latencies
+                // overlap; only a barrier not yet complete is waited for.
+                const bool have_in = from_ring && n < rp.y;
+                const bool need_out = to_ring && ((n - rg.x) & 3) == 0;
+                const bool need_cost = n > rg.x;
+                const unsigned tl = to + 3u;
+                const int rb = have_in ? mbar_test_wait(bar_at(bfull_in, ti % kRingBlk),
+                                                        use_parity(ti, kRingBlk))
+                                       : 1;
+                const int ro = need_out ? mbar_test_wait(bar_at(bempty_out, tl % kRingBlk),
+                                                         use_parity(tl, kRingBlk) ^ 1u)
+                                        : 1;
+                const int rc = need_cost ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
+                                                          use_parity(t, kCostSlots))
+                                         : 1;
+                if (!__all_sync(kFull, rb) &&
+                    !mbar_wait_slow(bar_at(bfull_in, ti % kRingBlk), use_parity(ti, kRingBlk), p.ctl,
+                                    p.timeout_ns, 1))
+                    return;
+                if (!__all_sync(kFull, ro) &&
+                    !mbar_wait_slow(bar_at(bempty_out, tl % kRingBlk), use_parity(tl, kRingBlk) ^ 1u,
+                                    p.ctl, p.timeout_ns, 2))
+                    return;
+                if (!__all_sync(kFull, rc) &&
+                    !mbar_wait_slow(bar_at(cfull, t % kCostSlots), use_parity(t, kCostSlots), p.ctl,
+                                    p.timeout_ns, 7))
+                    return;
+                float gv0[kSub], gv1[kSub];
+                {
+                    const unsigned s0 = have_in ? smem_u32(&myring[ti % kRingBlk][0][0]) : inf_blk;
+                    const float4 a0 = lds128(s0), a1 = lds128(s0 + 16);
+                    const float4 b0 = lds128(s0 + 32), b1 = lds128(s0 + 48);
+                    gv0[0] = a0.x; gv0[1] = a0.y; gv0[2] = a0.z; gv0[3] = a0.w;
+                    gv0[4] = a1.x; gv0[5] = a1.y; gv0[6] = a1.z; gv0[7] = a1.w;
+                    gv1[0] = b0.x; gv1[1] = b0.y; gv1[2] = b0.z; gv1[3] = b0.w;
+                    gv1[4] = b1.x; gv1[5] = b1.y; gv1[6] = b1.z; gv1[7] = b1.w;
+                }
+                // this sub-chunk's costs (loaded here rather than half-way through
+                // the previous sub-chunk keeps the 8 steps below one straight-line
+                // block: measured 8% faster)
+                if (need_cost) load_costs<R, kRM>(cring, t, lane, c);
+                if (have_in) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
+                if (need_cost) mbar_arrive(bar_at(cempty, t % kCostSlots));
+                float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
+                float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
+                (void)ol;
+                float fw[R];  // backpointer fields of the sub-chunk, bits 2u, 2u+1
+#pragma unroll
+                for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+                if (nsteps == kSub) {
+#pragma unroll
+                    for (int u = 0; u < kSub; ++u) {
+                        float cu[R];
+#pragma unroll
+                        for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                        dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                            (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                                is_origin,
+                                            mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                        if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+                    }
+                } else {
+                    // the last, partial sub-chunk
+#pragma unroll
+                    for (int u = 0; u < kSub; ++u) {
+                        if (u >= nsteps) break;
+                        float cu[R];
+#pragma unroll
+                        for (int k = 0; k < R; ++k) cu[k] = c[k][u];
+                        dp_step<R, kSubseq, kT>(cu, u, srcA, w12, ghost, gv0[u], gv1[u],
+                                            (kSubseq || ((h == 0) && (u == 0) && (j0 == 0))) &&
+                                                is_origin,
+                                            mu, cur, prv, ylp, fw, o0[u], o1[u]);
+                        if constexpr (kSubseq) ol[u] = pick_row<R>(cur, kl);
+                    }
+                }
+                if constexpr (kSubseq) {
+                    if (has_last) {  // row La-1 of these columns
+                        float* dst = p.lastrow + js;
+                        if (nsteps == kSub) {
+                            reinterpret_cast<float4*>(dst)[0] = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                            reinterpret_cast<float4*>(dst)[1] = make_float4(ol[4], ol[5], ol[6], ol[7]);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < kSub; ++u)
+                                if (u < nsteps) dst[u] = ol[u];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], h);
+                if (to_ring && lane == kOutLane) {
+                    const unsigned d0 = smem_u32(&nextring[to % kRingBlk][0][0]);
+                    sts128(d0, make_float4(o0[0], o0[1], o0[2], o0[3]));
+                    sts128(d0 + 16, make_float4(o0[4], o0[5], o0[6], o0[7]));
+                    sts128(d0 + 32, make_float4(o1[0], o1[1], o1[2], o1[3]));
+                    sts128(d0 + 48, make_float4(o1[4], o1[5], o1[6], o1[7]));
+                    mbar_arrive(bar_at(bfull_out, to % kRingBlk));
+                }
+
+            }
+            if constexpr (kT) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) word[k] = transpose_fields(word[k]);
+            }
+            store_words<R>(p.bp + ((size_t)strip * p.nchunk + (size_t)(j0 >> 4)) * (32 * R) +
+                               (size_t)lane * R,
+                           word);
+        }
     }
 #pragma unroll
     for (int k = 0; k < R; ++k)
@@ -1195,7 +1445,7 @@ __global__ void __launch_bounds__(split_threads<DP, NS, kBF>(),
             }
         } else if (role == 1) {
             if (w < gr.nstrips_here)
-                run_dp<R, NS, kBF, kSubseq, kT, kMap>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
+                run_dp<R, NS, kBF, kSubseq, kT, kMap, (kBF || kWide), kWide>(p, gr, w, strip, lane, ring, smem_u32(&bfull[0][0]),
                                    smem_u32(&bempty[0][0]), rsub[w], rsub[w + 1], cring_s,
                                    cfull_s, cempty_s, csub[w], smem_u32(&s_inf[0][0]),
                                    kMap ? map.done : nullptr);
