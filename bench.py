@@ -199,7 +199,8 @@ class ClockSampler:
 
 
 DP_SOURCES = ("paper_2607_15478_gb300/csrc/dp_split.cuh", "paper_2607_15478_gb300/csrc/dp_split.cu",
-              "paper_2607_15478_gb300/csrc/dp_split_cl.cu", "paper_2607_15478_gb300/csrc/dp_device.cuh")
+              "paper_2607_15478_gb300/csrc/dp_split_cl.cu", "paper_2607_15478_gb300/csrc/dp_split_cl.cuh",
+              "paper_2607_15478_gb300/csrc/dp_device.cuh")
 
 
 def dp_sources_sha256():

@@ -14,6 +14,7 @@
 //                  of the band that is not the side of the matrix (the band
 //                  may then have cut off a better path: the caller falls back
 //                  to the full exact DP)
+#include <climits>
 #include "pardtw_common.cuh"
 
 namespace pardtw {
@@ -84,11 +85,45 @@ __global__ void k_band_ranges(const int32_t* __restrict__ cpath, const int* __re
 }
 
 // Widen the ranges to monotone: starts by a suffix minimum, ends by a
-// prefix maximum (one thread; a few thousand strips at most).
-__global__ void k_band_monotone(int nstrips, int2* __restrict__ ranges) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int q = nstrips - 2; q >= 0; --q) ranges[q].x = min(ranges[q].x, ranges[q + 1].x);
-    for (int q = 1; q < nstrips; ++q) ranges[q].y = max(ranges[q].y, ranges[q - 1].y);
+// prefix maximum.  One block: thread t takes a run of consecutive strips,
+// the runs' minima and maxima are scanned across the block (inclusive scans
+// in shared memory, log2(kMonoThreads) rounds), and each thread rewrites its
+// run from the carry of the runs after it (starts) and before it (ends).
+// (A single thread took 125 us for 1075 strips.)
+constexpr int kMonoThreads = 256;
+__global__ void __launch_bounds__(kMonoThreads)
+    k_band_monotone(int nstrips, int2* __restrict__ ranges) {
+    __shared__ int s_min[kMonoThreads], s_max[kMonoThreads];
+    const int t = threadIdx.x;
+    const int per = (nstrips + kMonoThreads - 1) / kMonoThreads;
+    const int lo = min(t * per, nstrips), hi = min(lo + per, nstrips);
+    int mn = INT_MAX, mx = INT_MIN;
+    for (int q = lo; q < hi; ++q) {
+        const int2 r = ranges[q];
+        mn = min(mn, r.x);
+        mx = max(mx, r.y);
+    }
+    s_min[t] = mn;
+    s_max[t] = mx;
+    __syncthreads();
+    for (int off = 1; off < kMonoThreads; off <<= 1) {
+        const int a = t >= off ? s_max[t - off] : INT_MIN;               // runs before t
+        const int b = t + off < kMonoThreads ? s_min[t + off] : INT_MAX;  // runs after t
+        __syncthreads();
+        s_max[t] = max(s_max[t], a);
+        s_min[t] = min(s_min[t], b);
+        __syncthreads();
+    }
+    int cmax = t > 0 ? s_max[t - 1] : INT_MIN;
+    int cmin = t + 1 < kMonoThreads ? s_min[t + 1] : INT_MAX;
+    for (int q = lo; q < hi; ++q) {
+        cmax = max(cmax, ranges[q].y);
+        ranges[q].y = cmax;
+    }
+    for (int q = hi - 1; q >= lo; --q) {
+        cmin = min(cmin, ranges[q].x);
+        ranges[q].x = cmin;
+    }
 }
 
 __global__ void k_band_touch(const int32_t* __restrict__ path, const int* __restrict__ plen,
@@ -120,7 +155,7 @@ cudaError_t launch_band_ranges(const int32_t* cpath, const int* clen, int ds, in
     const int blocks = (nstrips + threads - 1) / threads;
     k_band_ranges<<<blocks, threads, 0, s>>>(cpath, clen, ds, w, wrow, Lac, La, Lb, nstrips, rps,
                                              swap, ranges);
-    k_band_monotone<<<1, 32, 0, s>>>(nstrips, ranges);
+    k_band_monotone<<<1, kMonoThreads, 0, s>>>(nstrips, ranges);
     return cudaGetLastError();
 }
 
