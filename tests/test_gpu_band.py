@@ -150,3 +150,20 @@ def test_band_fallback_at_multi_wave_size(aligner):
             assert_parity(A, B, path, total, name="band-fallback-multi-wave")
             return
     pytest.fail("no fallback on three unstructured 30000 x 33000 pairs")
+
+
+
+@pytest.mark.parametrize("D,precision", [(33, 0), (64, 0), (128, 0), (12, 1), (128, 1)])
+def test_band_unsupported_features(aligner, D, precision):
+    # the banded DP runs in the narrow warp-pair kernel only: D > 32 or the
+    # BF16 cost is refused with DTW_ERR_UNSUPPORTED, and the handle still
+    # aligns the next pair
+    from paper_2607_15478_gb300 import pardtw
+    wp = synth.warped_pair(synth.rng_for(66, D), 400, 500, D, kind="gaussian", knots=8,
+                           tmin=0.7, tmax=1.4, sigma=0.1)
+    with pytest.raises(pardtw.PardtwError) as e:
+        aligner.align_banded(dev(wp.A), dev(wp.B), downsample=8, halfwidth=64,
+                             cost_precision=precision)
+    assert e.value.status == pardtw.DTW_ERR_UNSUPPORTED
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    check_path_valid(path.cpu().numpy(), 400, 500)
