@@ -13,10 +13,12 @@
 //
 // Every CTA of a cluster sits on an SM of its own (the dynamic shared
 // memory is raised so that two CTAs cannot share an SM, which would put two
-// DP warps on one SM sub-partition).  The cluster size is the largest of 8,
-// 4, 2 whose resident clusters hold every strip group of the pair at once;
-// a band with more groups runs persistent clusters of 8, a full sweep with
-// more groups no clusters.
+// DP warps on one SM sub-partition).  The cluster size is the largest of 8
+// down to 2 whose resident clusters hold every strip group of the pair at
+// once (the 20000 x 25000 pair's 135 groups: 17 clusters of 8 do not fit at
+// once, 23 of 6 do, and its DP takes 1.360 ms against 1.393 with clusters of
+// 4, a third fewer hops through global memory); a band with more groups runs
+// persistent clusters of 8, a full sweep with more groups no clusters.
 #pragma once
 #include <mutex>
 
@@ -27,7 +29,8 @@ namespace {
 
 constexpr int kClSmemFloor = 120 * 1024;  // > half an SM's shared memory: one CTA per SM
 constexpr int kClMaxDev = 64;
-constexpr int kClSizes[3] = {8, 4, 2};
+constexpr int kNClSizes = 7;
+constexpr int kClSizes[kNClSizes] = {8, 7, 6, 5, 4, 3, 2};
 
 template <int DP, bool kBF, bool kT>
 struct ClKernel {
@@ -41,7 +44,7 @@ struct ClKernel {
 
 struct ClInfo {
     bool ready = false, ok = false;
-    int max_clusters[3] = {0, 0, 0};  // resident clusters of size kClSizes[k]
+    int max_clusters[kNClSizes] = {};  // resident clusters of size kClSizes[k]
 };
 
 cudaLaunchConfig_t cl_config(dim3 grid, int threads, int smem, cudaStream_t s,
@@ -76,7 +79,7 @@ const ClInfo& cl_info(int dev) {
         (void)cudaGetLastError();
         return ci;
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kNClSizes; ++k) {
         cudaLaunchAttribute at[1];
         cudaLaunchConfig_t cfg =
             cl_config(dim3((unsigned)kClSizes[k]), K::kThreads, K::smem(), nullptr, at, kClSizes[k]);
@@ -103,7 +106,7 @@ cudaError_t launch_cl(const DpArgs& a, cudaStream_t s, bool* used) {
     if (!ci.ok) return cudaSuccess;
     int cn = 0, nclusters = 0;
     // one wave: the largest cluster size whose resident clusters hold every group
-    for (int k = 0; k < 3 && cn == 0; ++k) {
+    for (int k = 0; k < kNClSizes && cn == 0; ++k) {
         const int need = (a.ngroups + kClSizes[k] - 1) / kClSizes[k];
         if (ci.max_clusters[k] >= need) {
             cn = kClSizes[k];
