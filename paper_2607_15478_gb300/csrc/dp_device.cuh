@@ -429,7 +429,8 @@ __device__ __forceinline__ float eq_as_float(float a, float b) {
 // of exact powers of two, so the code costs two compares and no integer or
 // select instruction.
 // kSubseq: the subsequence DTW of WSDTW (Sec. II-C), weights 1, 1, 2 for
-// (1,1), (1,2), (2,1) instead of 2, 3, 3 (w12 carries the (1,2) weight).
+// (1,1), (1,2), (2,1) instead of 2, 3, 3.  (w12 is no longer read: the
+// ghost rows' zero weight became a select of the border value.)
 // kT: the pair is swept transposed (rows of the kernel = frames of B), so
 // the kernel's (1,2) candidate is the problem's (2,1) and vice versa; the
 // problem's tie order (1,1), (1,2), (2,1) is then the kernel's c0, c2, c1.
@@ -441,6 +442,7 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
                                         bool ghost, float g0, float g1, bool origin_here,
                                         float mu, float* cur, float* prv, float& ylp, float* fw,
                                         float& o0, float& o1) {
+    (void)w12;  // the (1,2) weight: 3 (1 in the subsequence DP) on every real row
     const float y1 = __shfl_sync(kFull, cur[R - 1], srcA);  // E[i0-1][j-1]
     const float y2 = __shfl_sync(kFull, cur[R - 2], srcA);  // E[i0-2][j-1]
     const float bit0 = (float)(1u << (2 * u)), bit1 = (float)(2u << (2 * u));
@@ -449,12 +451,18 @@ __device__ __forceinline__ void dp_step(const float* cost, int u, int srcA, cons
     for (int k = 0; k < R; ++k) {
         const float x1 = (k == 0) ? y1 : cur[k - 1];                       // E[i-1][j-1]
         const float x2 = (k == 0) ? y2 : ((k == 1) ? y1 : cur[k - 2]);     // E[i-2][j-1]
-        float x1p = (k == 0) ? ylp : prv[k - 1];                           // E[i-1][j-2]
-        if (k == R - 2) x1p = ghost ? g0 : x1p;
-        if (k == R - 1) x1p = ghost ? g1 : x1p;
+        const float x1p = (k == 0) ? ylp : prv[k - 1];                     // E[i-1][j-2]
         constexpr float w11 = kSubseq ? 1.0f : 2.0f, w21 = kSubseq ? 2.0f : 3.0f;
+        constexpr float w12c = kSubseq ? 1.0f : 3.0f;
         const float c0 = fmaf(w11, cost[k], x1);     // from (i-1, j-1)
-        const float c1 = fmaf(w12[k], cost[k], x1p);  // from (i-1, j-2)
+        // from (i-1, j-2); the ghost lane's two rows take the border value
+        // here (their other candidates carry the cost 1e30), the value that
+        // a weight of 0 on this candidate gave, without an FMA reading three
+        // registers (those issue at 0.64-0.83 per cycle on GB300, against
+        // 0.91 with a constant operand)
+        float c1 = fmaf(w12c, cost[k], x1p);
+        if (k == R - 2) c1 = ghost ? g0 : c1;
+        if (k == R - 1) c1 = ghost ? g1 : c1;
         const float c2 = fmaf(w21, cost[k], x2);     // from (i-2, j-1)
         float mk = min3f(c0, c1, c2);
         fw[k] = fmaf(eq_as_float(c0, mk), bit0, fw[k]);
