@@ -67,8 +67,8 @@ constexpr int kBfBlkBytes = kColsPerWord * kBfStride * 2;
 // FP32 cost for D > 32 ("wide"): -a^ of the lane's R rows no longer fits in
 // registers, so the strip's rows of A^ sit in shared memory (rows padded by 4
 // floats: the 16-byte loads of rows 3l + k of a warp fall in distinct bank
-// groups), and two cost warps share a strip, each computing 4 of the 8
-// columns of a sub-chunk.
+// groups), and two cost warps share a strip, taking alternate sub-chunks
+// (all 8 columns each).
 template <int DP, bool kBF>
 struct CostWide {
     static constexpr bool kOn = DP > 32 && !kBF;
@@ -715,11 +715,10 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             // One backpointer word per trip: sub-chunks n (even; ranges start on
             // whole words) and n + 1.
             const int n = j0 / kSub;
-            constexpr bool two = true;
             const unsigned ti = rin + (unsigned)(n - rp.x), to = rout + (unsigned)(n - rg.x);
             const unsigned t = csub + (unsigned)(n - rg.x);
             const bool in0 = from_ring && n < rp.y;
-            const bool in1 = two && from_ring && n + 1 < rp.y;
+            const bool in1 = from_ring && n + 1 < rp.y;
 
             // The waits of the word, first tested together without blocking: the
             // border blocks from the ring above (the producer publishes them in
@@ -730,7 +729,7 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             // slots (filled in order by one cost warp; with two cost warps, which
             // take alternate slots, both are tested).
             const bool need_out = to_ring && ((n - rg.x) & 3) == 0;
-            const unsigned tl = to + 3u, tb = in1 ? ti + 1u : ti, tc = two ? t + 1u : t;
+            const unsigned tl = to + 3u, tb = in1 ? ti + 1u : ti, tc = t + 1u;
             const int rb = in0 ? mbar_test_wait(bar_at(bfull_in, tb % kRingBlk),
                                                  use_parity(tb, kRingBlk))
                                : 1;
@@ -738,9 +737,9 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                                                      use_parity(tl, kRingBlk) ^ 1u)
                                     : 1;
             const int rc = mbar_test_wait(bar_at(cfull, tc % kCostSlots), use_parity(tc, kCostSlots));
-            const int rc0 = (kTwoCost && two) ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
-                                                               use_parity(t, kCostSlots))
-                                              : 1;
+            const int rc0 = kTwoCost ? mbar_test_wait(bar_at(cfull, t % kCostSlots),
+                                                      use_parity(t, kCostSlots))
+                                     : 1;
             if (!__all_sync(kFull, rb) &&
                 !mbar_wait_slow(bar_at(bfull_in, tb % kRingBlk), use_parity(tb, kRingBlk), p.ctl,
                                 p.timeout_ns, 1))
@@ -762,11 +761,11 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
             load_border(in1 ? smem_u32(&myring[(ti + 1u) % kRingBlk][0][0]) : inf_blk, gB0, gB1);
             float cA[R][kSub], cB[R][kSub];
             load_costs<R, kRM>(cring, t, lane, cA);
-            if (two) load_costs<R, kRM>(cring, t + 1u, lane, cB);
+            load_costs<R, kRM>(cring, t + 1u, lane, cB);
             if (in0) mbar_arrive(bar_at(bempty_in, ti % kRingBlk));
             if (in1) mbar_arrive(bar_at(bempty_in, (ti + 1u) % kRingBlk));
             mbar_arrive(bar_at(cempty, t % kCostSlots));
-            if (two) mbar_arrive(bar_at(cempty, (t + 1u) % kCostSlots));
+            mbar_arrive(bar_at(cempty, (t + 1u) % kCostSlots));
 
             float o0[kSub], o1[kSub];  // the strip's two bottom rows (lane 30)
             float ol[kSub];            // subsequence DP: row La-1 (lane of has_last)
@@ -785,19 +784,17 @@ __device__ __forceinline__ void run_dp(const DpArgs& p, const GroupRoles& gr, in
                 store_border(smem_u32(&nextring[to % kRingBlk][0][0]), o0, o1);
                 mbar_arrive(bar_at(bfull_out, to % kRingBlk));
             }
-            if (two) {
 #pragma unroll
-                for (int k = 0; k < R; ++k) fw[k] = 0.0f;
-                sweep_full<R, kSubseq, kT>(cB, gB0, gB1, false, is_origin, srcA, w12, ghost, mu, cur,
-                                           prv, ylp, fw, o0, o1, ol, kl);
-                if constexpr (kSubseq)
-                    if (has_last) store_lastrow(p.lastrow + j0 + kSub, kSub, ol);
+            for (int k = 0; k < R; ++k) fw[k] = 0.0f;
+            sweep_full<R, kSubseq, kT>(cB, gB0, gB1, false, is_origin, srcA, w12, ghost, mu, cur,
+                                       prv, ylp, fw, o0, o1, ol, kl);
+            if constexpr (kSubseq)
+                if (has_last) store_lastrow(p.lastrow + j0 + kSub, kSub, ol);
 #pragma unroll
-                for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], 1);
-                if (to_ring && lane == kOutLane) {
-                    store_border(smem_u32(&nextring[(to + 1u) % kRingBlk][0][0]), o0, o1);
-                    mbar_arrive(bar_at(bfull_out, (to + 1u) % kRingBlk));
-                }
+            for (int k = 0; k < R; ++k) word[k] |= field_bits(fw[k], 1);
+            if (to_ring && lane == kOutLane) {
+                store_border(smem_u32(&nextring[(to + 1u) % kRingBlk][0][0]), o0, o1);
+                mbar_arrive(bar_at(bfull_out, (to + 1u) % kRingBlk));
             }
             if constexpr (kT) {
 #pragma unroll
