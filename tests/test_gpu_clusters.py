@@ -44,10 +44,12 @@ def both(aligner, A, B, **opts):
     return p1, t1
 
 
-# rows swept / 186 = strip groups: 1, 2, 3, 9 (one cluster of 8 plus one),
-# 17 (two clusters plus one), 108 and 135 (one wave of clusters)
-@pytest.mark.parametrize("La,Lb", [(150, 160), (300, 350), (500, 620), (1700, 1500),
-                                   (3100, 3500), (20000, 16000), (25000, 20000)])
+# rows swept / 186 = strip groups: 1, 2, 3, 5, 7 (one cluster of 8, its
+# ranks past the last group idle), 9 (two clusters of 8, the second with one
+# group), 17 (three of 8), 108 (14 of 8) and 135 (23 of 6: 17 clusters of 8
+# do not fit at once)
+@pytest.mark.parametrize("La,Lb", [(150, 160), (300, 350), (500, 620), (900, 1000), (1300, 1400),
+                                   (1700, 1500), (3100, 3500), (20000, 16000), (25000, 20000)])
 def test_clusters_bit_identical_and_oracle(aligner, La, Lb):
     from paper_2607_15478_gb300 import pardtw
     wp = synth.warped_pair(synth.rng_for(110, La), La, Lb, 12, knots=16, tmin=0.5, tmax=2.0)
