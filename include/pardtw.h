@@ -152,9 +152,9 @@ int dtw_set_stream(dtw_handle* h, void* cuda_stream);
  * bytes plus 3% padding at 3 rows per lane (7% at 1); plus the tagged
  * border rows between strip groups, 16 bytes per column and group of two
  * 93-row strips (La*Lb/11.6 bytes; La*Lb/7.5 at 1 row per lane); plus the
- * parallel backtrace's band maps, 12 bytes per column and 128 rows
- * (La*Lb/10.7 bytes); plus O((La+Lb)*D)).  About 0.44 bytes per cell with
- * the default options.  Errors: DTW_ERR_INVALID, DTW_ERR_UNSUPPORTED. */
+ * parallel backtrace's band maps, 14 bytes per column and 128 rows
+ * (La*Lb/9.1 bytes: each band's exits, and the maps two and four bands up);
+ * plus O((La+Lb)*D)).  About 0.46 bytes per cell with the default options.  Errors: DTW_ERR_INVALID, DTW_ERR_UNSUPPORTED. */
 int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes);
 
 /* ---- cost matrix (Sec. IV cosine distance; Sec. VI-B explicit matrix) ---- */
@@ -383,8 +383,8 @@ int dtw_band_cells(dtw_handle* h, long long* cells);
  *       *path_len = -status
  * Sizes whose scratch (backpointers La*Lb/4 bytes plus padding, border rows,
  * the backtrace's band maps, normalised features) exceeds the array return
- * DTW_ERR_SCRATCH_LIMIT before any work is queued; about 1.45e8 cells fit
- * (2.2 cells per byte at D = 12, e.g. 12000 x 12000).
+ * DTW_ERR_SCRATCH_LIMIT before any work is queued; about 1.44e8 cells fit
+ * (2.15 cells per byte at D = 12, e.g. 12000 x 12000).
  * The first call on a device looks up the array's device address (a one-time
  * set-up per device, made with that device current); make that first call
  * before any stream capture.  Every call shares the array and leaves its

@@ -19,9 +19,10 @@
 //      Only the entries of each band's last two rows are stored, and the
 //      end cell's entry.
 //   2. k_bt_compose composes the maps of bands b and b-1 (every other band),
-//      and k_bt_chain (one thread) follows the entries from the end cell up
-//      to band 0, two bands per dependent load: the path's last cell in
-//      every other band.
+//      k_bt_compose4 those of b and b-2 (every fourth band), and k_bt_chain
+//      (one thread) follows the entries from the end cell up to band 0, four
+//      bands per dependent load (with the two-band map of the same cell
+//      loaded beside it): the path's last cell in every other band.
 //   3. k_bt_walk (one warp per band): each band's piece of the path is
 //      walked back from that cell (one lookup away for the bands the chain
 //      stepped over) to the band's top, in parallel.
@@ -90,10 +91,40 @@ __global__ void __launch_bounds__(256) k_bt_compose(const BtArgs one,
     sc.exits2[(size_t)m * Lb + j] = make_int2(hop(x.x), hop(x.y));
 }
 
+// Four-band exit map: for band b = nbands-2-4m (m = blockIdx.y < n4) and
+// column j, the entries of the cells of band b's last two rows four bands
+// up, composed from the two-band maps of bands b and b-2.  Same columns as
+// k_bt_compose.
+template <bool kMany>
+__global__ void __launch_bounds__(256) k_bt_compose4(const BtArgs one,
+                                                     const BtArgs* __restrict__ many) {
+    const BtArgs& a = kMany ? many[blockIdx.z] : one;
+    const int La = a.La, Lb = a.Lb;
+    const BtScratch sc = bt_scratch(a.scratch, La, Lb);
+    const int m = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= sc.n4 || j >= Lb) return;
+    const int b = sc.nbands - 2 - 4 * m;
+    const int r1 = (b + 1) * kBand;
+    const int lo = max((r1 - 1) / 2, Lb - 1 - 2 * (La - 1 - (r1 - 2)));
+    const int hi = min(2 * (r1 - 1), Lb - 1);
+    if (j < lo || j > hi) return;
+    const int2* __restrict__ exits2 = sc.exits2;
+    const int2 x = exits2[(size_t)(2 * m) * Lb + j];  // into band b-2's last two rows
+    auto hop = [&](int e) -> int {
+        if (e < 0) return kNoPath;
+        const int2 c = entry_cell(e, b - 1);
+        if (c.y < 0 || c.y >= Lb) return kNoPath;
+        return pick_exit(exits2[(size_t)(2 * m + 1) * Lb + c.y], c.x, (b - 1) * kBand - 1);
+    };
+    sc.exits4[(size_t)m * Lb + j] = make_int2(hop(x.x), hop(x.y));
+}
+
 // One thread: the path's last cell in bands nbands-1, nbands-2, nbands-4,
-// ... (two bands per dependent load, through the two-band exit map) and in
-// band 0; the walks find the others.  cross[b] = (i, j) of that cell;
-// status on failure.
+// ... and in band 0; the walks find the others.  Four bands per dependent
+// load through the four-band exit map, the two-band map's entry of the same
+// cell loaded beside it (it names the crossing in between); two at the end.
+// cross[b] = (i, j) of that cell; status on failure.
 template <bool kMany>
 __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
     if (threadIdx.x != 0) return;
@@ -120,6 +151,26 @@ __global__ void k_bt_chain(const BtArgs one, const BtArgs* __restrict__ many) {
     if (b >= 1) {
         ok = take(b);
         if (ok) cross[--b] = c;
+    }
+    const int2* __restrict__ exits4 = sc.exits4;
+    while (ok && b >= 4) {  // four bands at a time (b = nbands-2-4m, m < n4)
+        const int m = (nbands - 2 - b) / 4;
+        const int last = (b + 1) * band - 1;
+        const int2 x2 = exits2[(size_t)(2 * m) * Lb + c.y];
+        const int2 x4 = exits4[(size_t)m * Lb + c.y];
+        const int e2 = pick_exit(x2, c.x, last), e4 = pick_exit(x4, c.x, last);
+        e = e2;
+        ok = take(b - 1);
+        const int2 c2 = c;
+        if (ok) {
+            e = e4;
+            ok = take(b - 3);
+        }
+        if (ok) {
+            cross[b - 2] = c2;
+            b -= 4;
+            cross[b] = c;
+        }
     }
     while (ok && b >= 2) {  // two bands at a time
         const int m = (nbands - 2 - b) / 2;
@@ -285,8 +336,10 @@ int bandmap_band_rows() { return kBand; }
 size_t bandmap_scratch_bytes(int La, int Lb) {
     const int nbands = (La + kBand - 1) / kBand;
     const int n2 = nbands >= 4 ? (nbands - 2) / 2 : 0;
+    const int n4 = nbands >= 6 ? (nbands - 6) / 4 + 1 : 0;
     return (size_t)nbands * Lb * sizeof(int2)        // exits
            + (size_t)n2 * Lb * sizeof(int2)           // exits2
+           + (size_t)n4 * Lb * sizeof(int2)           // exits4
            + (size_t)nbands * sizeof(int2)            // cross
            + (size_t)nbands * kBand * sizeof(int2)    // seg
            + (size_t)nbands * sizeof(int) + 64;       // count, end entry
@@ -312,6 +365,10 @@ cudaError_t launch_backtrace_bands(const BtArgs& a, cudaStream_t s, bool with_ma
     if (n2 > 0)
         k_bt_compose<false><<<dim3((unsigned)((a.Lb + 255) / 256), (unsigned)n2, 1), 256, 0, s>>>(
             a, nullptr);
+    const int n4 = nbands >= 6 ? (nbands - 6) / 4 + 1 : 0;
+    if (n4 > 0)
+        k_bt_compose4<false><<<dim3((unsigned)((a.Lb + 255) / 256), (unsigned)n4, 1), 256, 0, s>>>(
+            a, nullptr);
     k_bt_chain<false><<<1, 32, 0, s>>>(a, nullptr);
     k_bt_walk<false><<<(nbands + 3) / 4, 128, 0, s>>>(a, nullptr);
     k_bt_emit<false><<<dim3((unsigned)nbands, 1), kBand, 0, s>>>(a, nullptr);
@@ -329,6 +386,10 @@ cudaError_t launch_backtrace_bands_many(const BtArgs* many, int n, int maxLa, in
     if (n2 > 0)
         k_bt_compose<true><<<dim3((unsigned)((maxLb + 255) / 256), (unsigned)n2, (unsigned)n),
                              256, 0, s>>>(BtArgs{}, many);
+    const int n4 = nbands >= 6 ? (nbands - 6) / 4 + 1 : 0;
+    if (n4 > 0)
+        k_bt_compose4<true><<<dim3((unsigned)((maxLb + 255) / 256), (unsigned)n4, (unsigned)n),
+                              256, 0, s>>>(BtArgs{}, many);
     k_bt_chain<true><<<n, 32, 0, s>>>(BtArgs{}, many);
     k_bt_walk<true><<<dim3((unsigned)((nbands + 3) / 4), (unsigned)n), 128, 0, s>>>(BtArgs{},
                                                                                      many);

@@ -19,21 +19,26 @@ struct BtScratch {
     int2* exits;     // nbands x Lb: entries of each band's last two rows
     int2* exits2;    // n2 x Lb: for band b = nbands-2-2m (m < n2, b >= 2), the entries two
                      // bands up (into band b-2's last two rows) of band b's last two rows
+    int2* exits4;    // n4 x Lb: for band b = nbands-2-4m (m < n4, b >= 4), the entries four
+                     // bands up (into band b-4's last two rows)
     int2* cross;     // nbands: the path's last cell in each band
     int2* seg;       // nbands x band: each band's piece of the path, descending
     int* count;      // nbands: cells in each piece
     int* end_entry;  // the end cell's entry
-    int nbands, n2;
+    int nbands, n2, n4;
 };
 __host__ __device__ inline BtScratch bt_scratch(void* scratch, int La, int Lb) {
     BtScratch r;
     r.nbands = (La + kBand - 1) / kBand;
     r.n2 = r.nbands >= 4 ? (r.nbands - 2) / 2 : 0;
+    r.n4 = r.nbands >= 6 ? (r.nbands - 6) / 4 + 1 : 0;
     char* p = static_cast<char*>(scratch);
     r.exits = reinterpret_cast<int2*>(p);
     p += (size_t)r.nbands * Lb * sizeof(int2);
     r.exits2 = reinterpret_cast<int2*>(p);
     p += (size_t)r.n2 * Lb * sizeof(int2);
+    r.exits4 = reinterpret_cast<int2*>(p);
+    p += (size_t)r.n4 * Lb * sizeof(int2);
     r.cross = reinterpret_cast<int2*>(p);
     p += (size_t)r.nbands * sizeof(int2);
     r.seg = reinterpret_cast<int2*>(p);

@@ -2,14 +2,16 @@
 over the oracle's step codes, and the serial walk's path over random step
 codes (CPU).
 
-The CUDA backtrace (band map, two-band map, chain of crossings, band walks)
+The CUDA backtrace (band map, two- and four-band maps, chain of crossings,
+band walks)
 is checked against the oracle on the GPU.  This test checks the scheme
 itself, independently of its kernels, on many shapes and band counts: bands
 of `BAND` rows; in every band, row by row over the columns a path can reach
 (lo(r0) .. hi(r1-1)), the entry of each cell = the entry of its step's
 predecessor, or the predecessor itself (2 * column + last-row bit) when that
-lies in the band above; the crossings from the end cell up, two bands per
-lookup through the composed map of every other band; the walks, each from
+lies in the band above; the crossings from the end cell up, four bands per
+lookup through the composed map of every fourth band from the top, then two
+per lookup through the map of every other band; the walks, each from
 its band's crossing (or one lookup away) down to where the path leaves the
 band, which must be the cell its first cell's entry names."""
 import numpy as np
@@ -85,12 +87,31 @@ def scheme_path(code):
                 if 0 <= cj < Lb:
                     comp[j, r] = pick(exits[b - 1][cj], ci, b * BAND - 1)
         ex2[b] = comp
+    # the four-band map of bands nb-2, nb-6, ... (>= 4): the two-band map of b
+    # names a cell in band b-2's last rows, whose two-band map goes on to b-4
+    ex4 = {}
+    for b in range(nb - 2, 3, -4):
+        comp = np.full((Lb, 2), NOPATH, dtype=np.int64)
+        for j in range(Lb):
+            for r in range(2):
+                e = int(ex2[b][j, r])
+                if e < 0:
+                    continue
+                ci, cj = entry_cell(e, b - 1)
+                if 0 <= cj < Lb:
+                    comp[j, r] = pick(ex2[b - 2][cj], ci, (b - 1) * BAND - 1)
+        ex4[b] = comp
     # the chain
     cross = {nb - 1: (La - 1, Lb - 1)}
     e, b = end_entry, nb - 1
     if b >= 1:
         cross[b - 1] = entry_cell(e, b)
         b -= 1
+    while b >= 4:
+        ci, cj = cross[b]
+        cross[b - 2] = entry_cell(pick(ex2[b][cj], ci, last_row[b]), b - 1)
+        cross[b - 4] = entry_cell(pick(ex4[b][cj], ci, last_row[b]), b - 3)
+        b -= 4
     while b >= 2:
         ci, cj = cross[b]
         e = pick(ex2[b][cj], ci, last_row[b])
