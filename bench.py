@@ -433,6 +433,8 @@ def run_ours(args):
             ex["al"].close()
             line["bf16"], ex = measure_bf16(dev, k, args.warmup, flush)
             ex["al"].close()
+            line["cost_matrix"], ex = measure_cost(dev, k, args.warmup)
+            ex["al"].close()
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -440,6 +442,50 @@ def run_ours(args):
 
 def _rank0_line(line):
     print(json.dumps(line), flush=True)
+
+
+def measure_cost(dev, steps, warmup):
+    """The explicit cost matrix of the 20000x12 vs 25000x12 pair through
+    dtw_cost (an inspection surface: the aligner never stores it): 4 bytes
+    written a cell, so HBM-bound.  2.0 GB, larger than L2: no flush needed."""
+    import torch
+    from paper_2607_15478_gb300 import pardtw, synth
+    wp = synth.config_pair(1)
+    La, Lb, D = wp.A.shape[0], wp.B.shape[0], wp.A.shape[1]
+    stream = torch.cuda.Stream(device=dev)
+    al = pardtw.Aligner(dev.index, stream)
+    A = torch.from_numpy(wp.A).to(dev)
+    B = torch.from_numpy(wp.B).to(dev)
+    C = torch.empty((La, Lb), dtype=torch.float32, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def step():
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            pardtw.dtw_cost(al.h, A, B, C)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(warmup):
+        step()
+    ms = [step() for _ in range(steps)]
+    med = statistics.median(ms)
+    written = La * Lb * 4
+    peaks, basis = measured_peaks()
+    gbs = written / med / 1e6
+    block = {
+        "workload": workload_name(La, Lb) + ", La x Lb float32 matrix",
+        "ms": med, "step_ms": step_stats(ms), "gcups": La * Lb / med / 1e6,
+        "bytes_written": written, "gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+        "frac_of_hbm": gbs / peaks["hbm_gbs"],
+        "peak_basis": f"HBM copy bandwidth ({basis})",
+        "kernels": "k_normalise + k_cost (4 x 4 cells a thread, b^ of its 4 columns in registers over its row tiles, one 16-byte store per row of 4)",
+        "timing": "CUDA events on the aligner's stream, device buffers",
+    }
+    del C
+    return block, {"al": al}
 
 
 def measure_band(dev, steps, warmup, flush, exact_runs=3):

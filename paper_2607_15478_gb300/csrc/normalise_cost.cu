@@ -147,32 +147,128 @@ cudaError_t launch_normalise_many(const NormArgs* many, int n, int max_frames, i
 
 // C[i][j] = 1 - sum_d a^_i[d] b^_j[d], accumulated as fma(-a, b, acc) from 1
 // in feature order -- bit-identical to the cost the DP kernel uses.
-// Block: 256 threads = 8 rows x 32 column lanes; each lane writes 4 columns
-// of its row per pass.
-__global__ void k_cost(const float* __restrict__ Ahat, int La, const float* __restrict__ Bt,
-                       int Lb, int dp, float* __restrict__ C) {
-    const int lane = threadIdx.x & 31;
-    for (int i = blockIdx.y * 8 + (threadIdx.x >> 5); i < La; i += gridDim.y * 8) {
-        const float* a = Ahat + (size_t)i * dp;
-        for (int j0 = blockIdx.x * 128 + lane; j0 < Lb; j0 += gridDim.x * 128) {
+// Writing the matrix is the whole cost of this kernel (4 bytes a cell against
+// (La + Lb) * D * 4 bytes read), so it is laid out for the HBM write: a block
+// of 256 threads covers kCostCols columns and takes tiles of kCostRows rows
+// (about 8192 blocks, each over several tiles); thread (tx, ty) makes the 4 x 4
+// cells of columns 4 tx .. 4 tx + 3 and rows 4 ty .. 4 ty + 3 of each tile.
+// b^ comes as one 16-byte word per feature (bt_index puts 16 consecutive frames
+// of a feature side by side), a^ as 16-byte broadcast loads (a warp holds one
+// ty), and each row of 4 results is one 16-byte store when the rows are
+// 16-byte aligned (Lb % 4 == 0), else four 4-byte stores.  Loading b^ per tile
+// from the chunk layout costs ~8 L1 wavefronts per warp load (a warp's 128
+// columns span 8 chunks): that, not HBM, bounded the first form of this kernel
+// (3.3 TB/s against 7.6 for a plain write), hence the registers below.
+constexpr int kCostRows = 16, kCostCols = 256, kCostMaxDp = 128;
+
+// The rows i0 .. i0+3 of a thread's tile against its 4 columns, features
+// d0 .. d0+3 (b[u]: the 4 columns' values of feature d0 + u).
+__device__ __forceinline__ void cost_fma4(float (&acc)[4][4], const float4 (&a)[4],
+                                          const float4 (&b)[4]) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + 32 * q;
-                if (j >= Lb) break;
-                float acc = 1.0f;
-                for (int d = 0; d < dp; ++d) acc = fmaf(-a[d], Bt[bt_index(j, d, dp)], acc);
-                C[(size_t)i * Lb + j] = acc;
+    for (int r = 0; r < 4; ++r) {
+        const float av[4] = {a[r].x, a[r].y, a[r].z, a[r].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc[r][0] = fmaf(-av[u], b[u].x, acc[r][0]);
+            acc[r][1] = fmaf(-av[u], b[u].y, acc[r][1]);
+            acc[r][2] = fmaf(-av[u], b[u].z, acc[r][2]);
+            acc[r][3] = fmaf(-av[u], b[u].w, acc[r][3]);
+        }
+    }
+}
+
+__device__ __forceinline__ void cost_store4(const float (&acc)[4][4], int i0, int La, int j,
+                                            int Lb, float* __restrict__ C, int vec) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + r;
+        if (i >= La) continue;
+        float* out = C + (size_t)i * Lb + j;
+        if (vec && j + 3 < Lb) {
+            __stcs(reinterpret_cast<float4*>(out),
+                   make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (j + c < Lb) __stcs(out + c, acc[r][c]);
+        }
+    }
+}
+
+// DP <= 16: the thread's 4 columns of b^ stay in registers over all its row
+// tiles (DP float4 words), so a tile costs only the 4 rows' values of a^ (one
+// broadcast load per 4 features and row) and the stores.  Other widths load
+// b^ per tile (L1 hits).
+template <int DP>
+__global__ void __launch_bounds__(256) k_cost(const float* __restrict__ Ahat, int La,
+                                              const float* __restrict__ Bt, int Lb, int dp,
+                                              float* __restrict__ C, int vec) {
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int j = blockIdx.x * kCostCols + 4 * tx;
+    if (j >= Lb) return;  // Bt holds whole chunks of 16 frames: j .. j+3 exist
+    if (DP > 0) dp = DP;
+    const float* bcol = Bt + bt_index(j, 0, dp);  // feature d at bcol + 16 d
+    constexpr int kRegD = DP > 0 ? DP : 4;
+    float4 breg[kRegD];
+    if constexpr (DP > 0) {
+#pragma unroll
+        for (int d = 0; d < DP; ++d)
+            breg[d] = __ldg(reinterpret_cast<const float4*>(bcol + (size_t)d * 16));
+    }
+    for (int i0 = blockIdx.y * kCostRows + 4 * ty; i0 < La; i0 += gridDim.y * kCostRows) {
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 1.0f;
+        const float* arow[4];  // rows beyond La read row La - 1 (never stored)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) arow[r] = Ahat + (size_t)min(i0 + r, La - 1) * dp;
+        if constexpr (DP > 0) {
+#pragma unroll
+            for (int d0 = 0; d0 < DP; d0 += 4) {
+                float4 a[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    a[r] = __ldg(reinterpret_cast<const float4*>(arow[r] + d0));
+                const float4 b[4] = {breg[d0], breg[d0 + 1], breg[d0 + 2], breg[d0 + 3]};
+                cost_fma4(acc, a, b);
+            }
+        } else {
+            for (int d0 = 0; d0 < dp; d0 += 4) {
+                float4 a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    b[u] = __ldg(reinterpret_cast<const float4*>(bcol + (size_t)(d0 + u) * 16));
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    a[r] = __ldg(reinterpret_cast<const float4*>(arow[r] + d0));
+                cost_fma4(acc, a, b);
             }
         }
+        cost_store4(acc, i0, La, j, Lb, C, vec);
     }
 }
 
 cudaError_t launch_cost(const float* Ahat, int La, const float* Bt, int Lb, int dp, float* C,
                         cudaStream_t s) {
-    const int gx = (Lb + 127) / 128 < 64 ? (Lb + 127) / 128 : 64;
-    const int gy = (La + 7) / 8 < 32768 ? (La + 7) / 8 : 32768;
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    k_cost<<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C);
+    if (dp > kCostMaxDp || dp % 4 != 0) return cudaErrorInvalidValue;
+    const int gx = (Lb + kCostCols - 1) / kCostCols;
+    const int ty = (La + kCostRows - 1) / kCostRows;
+    // about 8192 blocks: each takes several row tiles, reusing its columns
+    int gy = (8192 + gx - 1) / gx;
+    if (gy > ty) gy = ty;
+    if (gy > 65535) gy = 65535;
+    const dim3 grid((unsigned)gx, (unsigned)gy);
+    const int vec = (Lb % 4 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0) ? 1 : 0;
+    switch (dp) {
+        case 4: k_cost<4><<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C, vec); break;
+        case 8: k_cost<8><<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C, vec); break;
+        case 12: k_cost<12><<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C, vec); break;
+        case 16: k_cost<16><<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C, vec); break;
+        default: k_cost<0><<<grid, 256, 0, s>>>(Ahat, La, Bt, Lb, dp, C, vec); break;
+    }
     return cudaGetLastError();
 }
 

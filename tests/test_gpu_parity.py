@@ -152,11 +152,79 @@ def test_host_buffers_roundtrip(aligner):
     assert_parity(wp.A, wp.B, path[:n].numpy(), float(tot[0]))
 
 
-def test_cost_matrix(aligner):
-    wp = synth.warped_pair(synth.rng_for(54, 0), 150, 170, 12, knots=3)
+def cost_tolerance(D):
+    # FP32 against the FP64 matrix, u = 2^-24: the sums of squares (D FMAs)
+    # and the reciprocal square root leave each normalised feature within
+    # (D/2 + 2) u relative, which moves the dot product (|a^ . b^| <= 1) by at
+    # most (D + 4) u; the D FMAs from 1 round partial sums of magnitude <= 2,
+    # at most 2 D u more
+    return (3 * D + 8) * 2.0 ** -24
+
+
+# k_cost's tiles are 16 rows x 256 columns, 4 x 4 cells a thread: ragged row
+# and column tiles, rows of a length that is not a multiple of 4 (4-byte
+# stores) and of one that is (16-byte stores), every padded feature width
+# (4, 8, 12, 16 with b^ in registers; 64, 128 loaded per tile)
+COST_CASES = [(1, 1, 3), (150, 170, 12), (37, 517, 4), (45, 520, 12), (70, 300, 8),
+              (90, 263, 16), (260, 1030, 33), (300, 777, 100), (64, 256, 128)]
+
+
+@pytest.mark.parametrize("La,Lb,D", COST_CASES)
+def test_cost_matrix(aligner, La, Lb, D):
+    rng = synth.rng_for(55, La * 7 + Lb * 3 + D)
+    A = rng.standard_normal((La, D)).astype(np.float32)
+    B = rng.standard_normal((Lb, D)).astype(np.float32)
+    A[La // 2] = 0.0  # a zero frame costs 1 against anything
+    B[Lb // 3] = 0.0
+    C = aligner.cost(dev(A), dev(B)).cpu().numpy()
+    Co = oracle.cost_matrix(A, B)
+    assert np.max(np.abs(C - Co)) <= cost_tolerance(D)
+    assert np.all(C[La // 2] == 1.0) and np.all(C[:, Lb // 3] == 1.0)
+
+
+def test_cost_matrix_host_buffers_and_many_row_tiles(aligner):
+    from paper_2607_15478_gb300 import pardtw
+    # host inputs and output (staged through the workspace) give the same bits
+    rng = synth.rng_for(56, 0)
+    A = rng.standard_normal((45, 12)).astype(np.float32)
+    B = rng.standard_normal((521, 12)).astype(np.float32)
+    Ch = torch.empty((45, 521), dtype=torch.float32)
+    pardtw.dtw_cost(aligner.h, torch.from_numpy(A), torch.from_numpy(B), Ch)
+    Cd = aligner.cost(dev(A), dev(B)).cpu()
+    assert torch.equal(Ch, Cd)
+    # ~66000 tiles of 16 rows for one column of blocks (the grid holds about
+    # 8192 blocks, so each takes ~8 tiles), the last one ragged
+    La = 65535 * 16 + 4000
+    A = rng.standard_normal((La, 4)).astype(np.float32)
+    B = rng.standard_normal((9, 4)).astype(np.float32)
+    C = aligner.cost(dev(A), dev(B)).cpu().numpy()
+    assert np.max(np.abs(C - oracle.cost_matrix(A, B))) <= cost_tolerance(4)
+
+
+def _fma_f32(w, c, t):
+    """float32(w * c + t) with one rounding: w * c (a float32 times 2 or 3) is
+    exact in FP64, and the FP64 sum is checked to be exact (TwoSum), so the
+    rounding to float32 is the only one."""
+    p, t = w * float(c), float(t)
+    s = p + t
+    bb = s - p
+    assert (p - (s - bb)) + (t - bb) == 0.0
+    return np.float32(s)
+
+
+@pytest.mark.parametrize("La,Lb", [(600, 700), (700, 600)])
+def test_cost_matrix_is_the_dp_cost(aligner, La, Lb):
+    # the explicit matrix holds the DP's own costs bit for bit: the aligner's
+    # FP32 total equals D(0,0) = C(0,0), D = fma(w, C, D) along its path over
+    # dtw_cost's matrix (both sweep directions)
+    wp = synth.config_pair(0, La=La, Lb=Lb)
     C = aligner.cost(dev(wp.A), dev(wp.B)).cpu().numpy()
-    Co = oracle.cost_matrix(wp.A, wp.B)
-    assert np.max(np.abs(C - Co)) < 2e-6
+    path, total = aligner.align(dev(wp.A), dev(wp.B))
+    p = path.cpu().numpy() if hasattr(path, "cpu") else np.asarray(path)
+    t = np.float32(C[0, 0])
+    for (i0, j0), (i1, j1) in zip(p[:-1], p[1:]):
+        t = _fma_f32(2.0 if (i1 - i0, j1 - j0) == (1, 1) else 3.0, C[i1, j1], t)
+    assert float(t) == float(total)
 
 
 def test_unreachable_and_invalid(aligner):
