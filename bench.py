@@ -42,10 +42,23 @@ METRIC = "exact DTW GCUPS on 1 GB300; learned-band speedup at <=1-frame path err
 UNIT = "GCUPS"
 WORKLOAD = "pair-20000x12-vs-25000x12 chroma-like, warped (64 knots, tempo 0.7-1.4), cosine cost"
 L2_FLUSH_BYTES = 512 << 20
-KERNELS_PER_STEP = 7  # normalise, DP, band map, two-band map, band chain, band walks, emit
-# learned band: 2 x (pool, 3 convolutions, heads), coarse alignment (7), band
-# ranges (2), banded alignment (7), band-side test (1)
-KERNELS_PER_LEARNED_STEP = 10 + 7 + 2 + 7 + 1
+
+
+def backtrace_kernels(rows):
+    """Launches of the parallel backtrace of a sweep with `rows` rows: band
+    map, two-band map (at least 4 bands of 128 rows), four-band map (at least
+    6), chain, walks, emission.  Every workload here has at least 768 frames on
+    each side, so both sweep directions give the same count."""
+    nb = -(-rows // 128)
+    return 4 + (nb >= 4) + (nb >= 6)
+
+
+# normalise, DP, backtrace
+KERNELS_PER_STEP = 2 + backtrace_kernels(20000)
+# learned band: 2 x (pool, 3 convolutions, heads), coarse alignment of the
+# 8x pooled sequences (normalise, DP, backtrace), band ranges (2), banded
+# alignment (normalise, DP, backtrace), band-side test (1)
+KERNELS_PER_LEARNED_STEP = 10 + (2 + backtrace_kernels(100000 // 8)) + 2 + (2 + backtrace_kernels(100000)) + 1
 # WSDTW: batched normalisation, subsequence DP, segment DP (one cooperative
 # launch while every column tile's CTA fits on the GPU at once, as at this
 # size; else a tile pass and a fix-up pass per fragment), fragment
@@ -841,8 +854,9 @@ def run_batch(args):
             "cpu_baseline": cpu,
             "e2e": {"value": sum(cells_all) * args.steps / t_e2e / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": ex["h2d"], "d2h_bytes_per_step": ex["d2h"]},
-            # epoch bump, normalisation, DP, band map, two-band map, chain, walks, emit
-            "gpu_launches": 8 * args.steps,
+            # epoch bump, normalisation, DP, backtrace (bands over the longest A)
+            "gpu_launches": (3 + backtrace_kernels(max((p.A.shape[0] for p in pairs), default=0)))
+                            * args.steps,
             "clocks": ex["clocks"],
         })
     ex["plan"].close()
@@ -901,8 +915,8 @@ def run_precision(args):
         "cpu_baseline": None,
         "e2e": {"value": cells * args.steps / t_e2e / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (La + Lb) * D * 4, "d2h_bytes_per_step": cap * 8 + 8},
-        # normalisation, bf16 packing of B, DP, band map, two-band map, chain, walks, emit
-        "gpu_launches": 8 * args.steps,
+        # normalisation, bf16 packing of B, DP, backtrace
+        "gpu_launches": (3 + backtrace_kernels(min(La, Lb))) * args.steps,
         "clocks": ex["clocks"],
     })
     al.close()
