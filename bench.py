@@ -3,15 +3,16 @@
 
 One step = one exact alignment of the 20000x12 vs 25000x12 chroma-like pair
 (normalise, column-sweep DP with on-the-fly cosine cost, band entry map,
-two-band map, band chain, band walks, path emit: 7 kernels), with the inputs
+two- and four-band maps, band chain, band walks, path emit: 8 kernels), with the inputs
 already resident in HBM.  GCUPS = La*Lb / t / 1e9.
 
 The same JSON line carries the second half of the metric and the project's
 other forms, each measured in this run on this GPU: a `band` block (the
 100000 x 126231 pair in the learned band against the full exact DP: speedup,
 fallbacks, path deviation), a `batch` block (256 uneven pairs as one CUDA
-graph) and a `bf16` block (the 40000x128 vs 48000x128 pair, BF16 cost on the
-tensor cores against the FP32 cost).
+graph), a `bf16` block (the 40000x128 vs 48000x128 pair, BF16 cost on the
+tensor cores against the FP32 cost) and a `cost_matrix` block (the explicit
+cost matrix of the default pair through dtw_cost: GB/s written).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config 1..5] [--no-extras]
