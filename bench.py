@@ -335,7 +335,7 @@ def run_ours(args):
     if n_ok <= 0:
         raise RuntimeError(f"alignment failed on rank {rank}: {pardtw.status_string(-n_ok)}")
 
-    step_ms, dp_ms = [], []
+    step_ms, dp_ms, stages = [], [], []
     with ClockSampler(dev.index) as clk:  # sampling starts before the barrier
         if ws > 1:
             dist.barrier()
@@ -345,7 +345,9 @@ def run_ours(args):
             step()
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            dp_ms.append(al.stage_times()[1])
+            st = al.stage_times()
+            stages.append(st)
+            dp_ms.append(st[1])
         torch.cuda.synchronize(dev)
         clk.mark_end()
         if ws > 1:
@@ -434,6 +436,12 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "stage_ms": {
+                "normalise": statistics.median(x[0] for x in stages),
+                "dp": statistics.median(x[1] for x in stages),
+                "backtrace": statistics.median(x[2] for x in stages),
+                "timing": "CUDA events around each stage on the aligner's stream; medians "
+                          "over the timed steps"},
             "clocks": clk.summary(),
         }
         if ws == 1 and not args.no_extras:
