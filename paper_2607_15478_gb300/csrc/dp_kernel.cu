@@ -327,16 +327,11 @@ template <int DP>
 cudaError_t launch_dp_t(const DpArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NW = kWarpsPerGroup;
     const int smem = NW * BStage<DP>::kWarpBytes;
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_dp<DP, NW>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dp<DP, NW>, NW * 32,
-                                                          smem);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    static DeviceSlots occupancy;
+    int blocks_per_sm = 0;
+    const cudaError_t e = blocks_per_sm_once(k_dp<DP, NW>, NW * 32, smem, occupancy,
+                                             &blocks_per_sm);
+    if (e != cudaSuccess) return e;
     int grid = blocks_per_sm * num_sms;
     if (grid > a.ngroups) grid = a.ngroups;
     k_dp<DP, NW><<<grid, NW * 32, smem, s>>>(a);

@@ -1508,15 +1508,10 @@ cudaError_t launch_t(const DpArgs& a, const DpArgs* many, const int* item0, int 
     constexpr int kThreads = split_threads<DP, NS, kBF>();
     const int smem = NS * SplitSmem<DP, R, kBF>::kStripBytes;
     auto* kern = k_dp_split<DP, R, NS, kMany, kBF, kSubseq, kT, kMap>;
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    static DeviceSlots occupancy;
+    int blocks_per_sm = 0;
+    const cudaError_t e = blocks_per_sm_once(kern, kThreads, smem, occupancy, &blocks_per_sm);
+    if (e != cudaSuccess) return e;
     int grid = blocks_per_sm * num_sms;
     if (kMap) {
         if (!map || !map->done || map->nbm <= 0) return cudaErrorInvalidValue;

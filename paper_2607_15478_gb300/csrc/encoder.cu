@@ -471,14 +471,10 @@ template <bool kBwd, bool kBF16>
 cudaError_t conv_t(const float* X, const float* mask, int L, int Cin, const float* W,
                    const float* b, int relu, float* Y, cudaStream_t s) {
     const int smem = (Cin * kK * kC + (kTL + 2 * kPad) * Cin) * (int)sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv<kBwd, kBF16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (kC * kK * kC + (kTL + 2 * kPad) * kC) * 4);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static DeviceSlots raised;
+    const cudaError_t e = raise_smem_once(k_conv<kBwd, kBF16>,
+                                          (kC * kK * kC + (kTL + 2 * kPad) * kC) * 4, raised);
+    if (e != cudaSuccess) return e;
     k_conv<kBwd, kBF16><<<(L + kTL - 1) / kTL, kConvThreads, smem, s>>>(X, mask, L, Cin, W, b,
                                                                        relu, Y);
     return cudaGetLastError();
@@ -488,14 +484,10 @@ template <int kCPT>
 cudaError_t wgrad_t(const float* X, int L, int Cin, const float* dY, const float* Yout, float* dW,
                     float* db, cudaStream_t s) {
     const int smem = (kTW * kC + (kTW + 2 * kPad) * Cin) * (int)sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad<kCPT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (kTW * kC + (kTW + 2 * kPad) * kC) * 4);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static DeviceSlots raised;
+    const cudaError_t e = raise_smem_once(k_conv_wgrad<kCPT>,
+                                          (kTW * kC + (kTW + 2 * kPad) * kC) * 4, raised);
+    if (e != cudaSuccess) return e;
     k_conv_wgrad<kCPT><<<(L + kTW - 1) / kTW, kConvThreads, smem, s>>>(X, L, Cin, dY, Yout, dW,
                                                                       db);
     return cudaGetLastError();

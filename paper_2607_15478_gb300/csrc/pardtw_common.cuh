@@ -5,9 +5,62 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "pardtw.h"
 
 namespace pardtw {
+
+// Launch facts of a kernel that are per device: its dynamic shared memory
+// limit (cudaFuncSetAttribute applies to the current device) and the CTAs of
+// it resident per SM.  Each launcher keeps one DeviceSlots per kernel
+// instantiation (static storage: zero-initialised, 0 = not looked up yet).
+constexpr int kMaxDevices = 64;
+struct DeviceSlots {
+    std::atomic<int> v[kMaxDevices];
+};
+
+// Raise `kern`'s dynamic shared memory limit to `smem` bytes on the current
+// device, once per device.
+template <class K>
+cudaError_t raise_smem_once(K* kern, int smem, DeviceSlots& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    if (slot && done.v[dev].load(std::memory_order_acquire) != 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (slot) done.v[dev].store(1, std::memory_order_release);
+    return cudaSuccess;
+}
+
+// CTAs of `kern` (threads a CTA, smem bytes of dynamic shared memory)
+// resident per SM of the current device, at least 1; raises the kernel's
+// shared memory limit there first.  Looked up once per device.
+template <class K>
+cudaError_t blocks_per_sm_once(K* kern, int threads, int smem, DeviceSlots& cache, int* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    if (slot) {
+        const int n = cache.v[dev].load(std::memory_order_acquire);
+        if (n > 0) {
+            *out = n;
+            return cudaSuccess;
+        }
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (n < 1) n = 1;
+    if (slot) cache.v[dev].store(n, std::memory_order_release);
+    *out = n;
+    return cudaSuccess;
+}
 
 constexpr int kWarp = 32;
 constexpr long long kDefaultTimeoutNs = 2000000000LL;  // bounded device waits: 2 s
