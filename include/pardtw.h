@@ -154,7 +154,8 @@ int dtw_set_stream(dtw_handle* h, void* cuda_stream);
  * 93-row strips (La*Lb/11.6 bytes; La*Lb/7.5 at 1 row per lane); plus the
  * parallel backtrace's band maps, 14 bytes per column and 128 rows
  * (La*Lb/9.1 bytes: each band's exits, and the maps two and four bands up);
- * plus O((La+Lb)*D)).  About 0.46 bytes per cell with the default options.  Errors: DTW_ERR_INVALID, DTW_ERR_UNSUPPORTED. */
+ * plus O((La+Lb)*D)).  About 0.46 bytes per cell with the default options.
+ * Errors: DTW_ERR_INVALID, DTW_ERR_UNSUPPORTED. */
 int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* bytes);
 
 /* ---- cost matrix (Sec. IV cosine distance; Sec. VI-B explicit matrix) ---- */
@@ -162,7 +163,11 @@ int dtw_workspace_size(int La, int Lb, int D, const dtw_options* opt, size_t* by
  * A, B: La x D and Lb x D float32 (device or host).  C: La*Lb float32,
  * caller-owned (device or host).  The exact aligner never materialises
  * this matrix (Sec. II-D); this entry point exists for inspection and tests.
- * Errors: DTW_ERR_INVALID, DTW_ERR_OOM, DTW_ERR_CUDA. */
+ * Every value is the FP32 cost the aligner's DP uses for that cell, bit for
+ * bit (one FMA per feature in feature order, from 1).  Host buffers are
+ * staged through the workspace and the call then synchronises.
+ * Errors: DTW_ERR_INVALID (NULL pointer, La, Lb or D < 1), DTW_ERR_UNSUPPORTED
+ * (D > 128), DTW_ERR_OOM, DTW_ERR_CUDA. */
 int dtw_cost(dtw_handle* h, const float* A, int La, const float* B, int Lb, int D, float* C);
 
 /* ---- exact alignment of one pair (Sec. II-D ParDTW, Sec. III-B) ----------- */
